@@ -1,0 +1,214 @@
+"""Seeded synthetic workloads shared by the CUDA path and the CPU oracle.
+
+This module describes *what* is simulated -- grid, spacings, switches,
+parameter values and seeded initial fields -- and holds none of the method's
+arithmetic: no reference state, thermodynamics, stencil or solver.  Both sides
+convert a :class:`Case` into their own parameter structure.
+
+Random numbers come from one counter-based generator: the SplitMix64 output
+function (Steele, Lea and Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014) applied to ``seed * golden + (stream << 40) + index``,
+top 53 bits mapped to [0, 1).  Every draw is made here on the host; the GPU
+never generates randomness.
+
+Workloads (stand-ins for the paper's DYCOMS RF01 setup, Sec. 4, which needs
+no external data beyond the printed parameters):
+
+* ``tgv``   -- dry, triply periodic Taylor-Green box with unit reference
+  density (the 32^3 FP64 parity case and its 1536x1536x256 tiling),
+* ``cbl``   -- moist capped boundary layer: mixed layer of theta_l = 289 K,
+  q_t = 9 g/kg (Sec. 4) below a seeded inversion height, seeded jumps above,
+  +-0.1 K noise below, geostrophic wind, radiation, subsidence, surface
+  fluxes and sponge.
+"""
+from __future__ import annotations
+
+import dataclasses
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+_GOLD = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+#: physics switch names understood by both sides
+PHYSICS = ("adv", "sgs", "const_nu", "moist", "buoy", "coriolis", "sponge",
+           "rad", "subs", "sfc", "fb")
+
+# stream ids of the generator
+STREAM_U, STREAM_V, STREAM_W, STREAM_TH, STREAM_QT, STREAM_P = 0, 1, 2, 3, 4, 5
+STREAM_CASE = 16
+
+
+def uniform01(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
+    """n uniform doubles in [0, 1) from counter indices offset .. offset+n-1."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(offset, offset + n, dtype=np.uint64)
+        x = np.uint64(seed) * _GOLD + (np.uint64(stream) << np.uint64(40)) + idx
+        z = x + _GOLD
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def uniform(seed: int, stream: int, n: int, lo: float, hi: float) -> np.ndarray:
+    return lo + (hi - lo) * uniform01(seed, stream, n)
+
+
+@dataclass
+class Case:
+    """A workload: grid, numerics switches, parameters and a seed."""
+
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    dz: float
+    walls: bool = False
+    precision: int = 64
+    dt: float = 0.0            # 0: Courant-number step from the initial field
+    cfl: float = 0.3
+    K: int = 3                 # sub-iterations per step
+    solver: str = "cg"         # "cg" | "jacobi"
+    op: str = "compact"        # "compact" (L_c + App. A term) | "wide" (D rho0 G)
+    warm: str = "zero"         # "zero" | "prev" | "learned"
+    tol: float = 1e-10
+    maxit: int = 5000
+    omega: float = 2.0 / 3.0
+    physics: tuple = ("adv", "sgs")
+    cs: float = 0.18
+    pr: float = 0.4
+    sc: float = 0.4
+    nu_const: float = 0.0
+    f_cor: float = 7.62e-5
+    ug: float = 0.0
+    vg: float = 0.0
+    sponge_frac: float = 0.05
+    sponge_rate: float = 0.25
+    subs_div: float = 0.0
+    shf: float = 0.0
+    lhf: float = 0.0
+    rad_f0: float = 0.0
+    rad_f1: float = 0.0
+    rad_kappa: float = 0.0
+    theta0: float = 290.0
+    p00: float = 1.0e5
+    sat_tol: float = 1e-10
+    sat_maxit: int = 20
+    rho0_const: Optional[float] = None   # constant reference density override
+    seed: int = 1
+    init: str = "tgv"          # "tgv" | "cbl" | "zero"
+    init_args: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def shape(self) -> tuple:
+        return (self.nz, self.ny, self.nx)
+
+    def replace(self, **kw) -> "Case":
+        return dataclasses.replace(self, **kw)
+
+    def rho0_profile(self) -> Optional[np.ndarray]:
+        if self.rho0_const is None:
+            return None
+        return np.full(self.nz, float(self.rho0_const))
+
+
+# ----------------------------------------------------------------------------
+# case builders
+
+
+def tgv(n: int = 32, nxyz: Optional[tuple] = None, seed: int = 1, precision: int = 64,
+        cs: float = 0.17, amp: float = 1.0, noise: float = 1e-3, steps_tol: float = 1e-10,
+        **kw) -> Case:
+    """Dry triply periodic Taylor-Green box, dx = dy = dz = 1/n, rho0 = 1."""
+    nx, ny, nz = nxyz if nxyz is not None else (n, n, n)
+    h = 1.0 / n
+    c = Case(name=f"tgv{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, dx=h, dy=h, dz=h,
+             walls=False, precision=precision, cfl=0.3, K=3, tol=steps_tol,
+             physics=("adv", "sgs"), cs=cs, rho0_const=1.0, seed=seed,
+             init="tgv", init_args={"amp": amp, "noise": noise, "theta": 300.0})
+    return c.replace(**kw) if kw else c
+
+
+def cbl(nx: int = 128, ny: int = 128, nz: int = 96, dx: float = 35.0, dz: float = 10.0,
+        seed: int = 1, precision: int = 32, **kw) -> Case:
+    """Moist capped boundary layer (DYCOMS RF01-like stand-in)."""
+    c = Case(name=f"cbl{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, dx=dx, dy=dx, dz=dz,
+             walls=True, precision=precision, dt=0.5, K=3, tol=1e-6, maxit=5000,
+             physics=("adv", "sgs", "fb", "moist", "buoy", "coriolis", "sponge",
+                      "rad", "subs", "sfc"),
+             cs=0.18, pr=0.4, sc=0.4, f_cor=7.62e-5, ug=7.0, vg=-5.5,
+             sponge_frac=0.05, sponge_rate=0.25, subs_div=3.75e-6,
+             shf=15.0, lhf=115.0, rad_f0=70.0, rad_f1=22.0, rad_kappa=85.0,
+             theta0=290.0, p00=1.0e5, sat_tol=1e-10 if precision == 64 else 1e-4,
+             seed=seed, init="cbl",
+             init_args={"theta_ml": 289.0, "qt_ml": 9.0e-3, "zi": (700.0, 900.0),
+                        "dtheta": (5.0, 10.0), "dqt": (-8.0e-3, -5.0e-3),
+                        "noise": 0.1})
+    return c.replace(**kw) if kw else c
+
+
+# ----------------------------------------------------------------------------
+# initial fields
+
+
+def cbl_draws(case: Case) -> dict:
+    """The seeded scalars of a capped-boundary-layer member."""
+    a = case.init_args
+    r = uniform01(case.seed, STREAM_CASE, 3)
+    zi = a["zi"][0] + (a["zi"][1] - a["zi"][0]) * r[0]
+    dth = a["dtheta"][0] + (a["dtheta"][1] - a["dtheta"][0]) * r[1]
+    dq = a["dqt"][0] + (a["dqt"][1] - a["dqt"][0]) * r[2]
+    return {"zi": float(zi), "dtheta": float(dth), "dqt": float(dq)}
+
+
+def initial_state(case: Case) -> dict:
+    """Seeded initial fields u, v, w, p, theta_l, q_t as float64 (nz, ny, nx)."""
+    nz, ny, nx = case.shape
+    n = case.n
+    out = {}
+    if case.init == "tgv":
+        a = case.init_args
+        x = (np.arange(nx) + 0.5) * case.dx
+        y = (np.arange(ny) + 0.5) * case.dy
+        z = (np.arange(nz) + 0.5) * case.dz
+        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+        tp = 2.0 * np.pi
+        amp, eps = a.get("amp", 1.0), a.get("noise", 1e-3)
+        u = amp * np.sin(tp * X) * np.cos(tp * Y) * np.cos(tp * Z)
+        v = -amp * np.cos(tp * X) * np.sin(tp * Y) * np.cos(tp * Z)
+        w = np.zeros_like(u)
+        out["u"] = u + uniform(case.seed, STREAM_U, n, -eps, eps).reshape(case.shape)
+        out["v"] = v + uniform(case.seed, STREAM_V, n, -eps, eps).reshape(case.shape)
+        out["w"] = w + uniform(case.seed, STREAM_W, n, -eps, eps).reshape(case.shape)
+        out["theta_l"] = np.full(case.shape, a.get("theta", 300.0))
+        out["q_t"] = np.zeros(case.shape)
+    elif case.init == "cbl":
+        a = case.init_args
+        d = cbl_draws(case)
+        z = (np.arange(nz) + 0.5) * case.dz
+        below = (z < d["zi"])[:, None, None] * np.ones(case.shape, dtype=bool)
+        th = np.where(below, a["theta_ml"], a["theta_ml"] + d["dtheta"])
+        qt = np.where(below, a["qt_ml"], a["qt_ml"] + d["dqt"])
+        noise = uniform(case.seed, STREAM_TH, n, -a["noise"], a["noise"]).reshape(case.shape)
+        out["theta_l"] = th + np.where(below, noise, 0.0)
+        out["q_t"] = qt.astype(np.float64)
+        out["u"] = np.full(case.shape, case.ug)
+        out["v"] = np.full(case.shape, case.vg)
+        out["w"] = np.zeros(case.shape)
+    elif case.init == "zero":
+        for k in ("u", "v", "w", "theta_l", "q_t"):
+            out[k] = np.zeros(case.shape)
+    else:
+        raise ValueError(f"unknown init {case.init!r}")
+    out["p"] = np.zeros(case.shape)
+    return out
