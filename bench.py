@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""LES cell-steps/s on one GB300 (arXiv 2301.04698 hot path), as one JSON line.
+
+A step is one full time step of the iterative predictor-corrector scheme:
+thermodynamics, K = 3 sub-iterations of (scalar predictor, momentum predictor
+and Poisson right side, Poisson solve, correction).  Default workload: the
+moist capped boundary layer on 128 x 128 x 96 nodes, dx = 35 m, dz = 10 m,
+FP32 fields with FP64 reductions, CG to 1e-6 relative residual.
+
+Legs of one run:
+  value    device time of exactly --steps steps (CUDA events on the library's
+           stream; L2 flushed by a 256 MiB write before every timed step,
+           outside the events), inputs resident in HBM;
+  e2e      the same steps through the C ABI with host buffers: every step
+           uploads the state from pinned host memory and reads the FP64
+           diagnostics back;
+  roofline the kernel with the largest share of device time in a profiled
+           pass of the same steps (event pair around every launch):
+           algorithmic bytes per launch / mean launch time vs measured HBM peak;
+  cpu_baseline (rank 0, N = 1) the FP64 oracle on a bounded sample.
+--impl reference times the oracle alone (the reference arm of this build).
+Under torchrun each rank runs an independent replica (different seed): weak
+scaling with no collective on the data path; timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LES cell-steps/s on 1 GB300; Poisson ms/step at fixed residual, learned vs plain"
+UNIT = "cell-steps/s"
+
+
+def workload(name: str, seed: int):
+    from paper_2301_04698_gb300 import inputs
+    if name == "cbl128":
+        return inputs.cbl(128, 128, 96, seed=seed, precision=32)
+    if name == "tgv32":
+        return inputs.tgv(32, seed=seed)
+    if name == "tgv_large":
+        return inputs.tgv(32, nxyz=(1536, 1536, 256), seed=seed, precision=32, steps_tol=1e-6)
+    raise SystemExit(f"unknown workload {name}")
+
+
+WORKLOAD_DESC = {
+    "cbl128": "moist capped boundary layer 128x128x96, dx=35 m, dz=10 m, FP32 (FP64 reductions), "
+              "K=3, CG to 1e-6",
+    "tgv32": "dry triply periodic Taylor-Green 32^3, FP64, K=3, CG to 1e-10",
+    "tgv_large": "dry triply periodic Taylor-Green 1536x1536x256, FP32 (FP64 reductions), K=3, CG to 1e-6",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="cbl128", choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", default="auto", help="oracle sample: auto | full | NXxNY")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_setup(n):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                 f".clocks_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        mx = max(r[1] for r in rows)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_2301_04698_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(cs, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "les.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str, workload_name: str):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    ent = d.get(f"{workload_name}:{kernel}")
+    if not ent or ent.get("src") != src_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(case, args):
+    """A bounded sample of the workload for the FP64 oracle: the same physics
+    on the full column height over a horizontal sub-domain."""
+    if args.cpu_sample == "full":
+        return case, "full domain"
+    if args.cpu_sample not in ("auto",):
+        sx, sy = (int(v) for v in args.cpu_sample.lower().split("x"))
+    else:
+        budget = 2.0e6 if case.precision == 32 else 4.0e6
+        sx = sy = case.nx
+        while sx * sy * case.nz > budget and sx > 16:
+            sx //= 2
+            sy //= 2
+    if sx == case.nx and sy == case.ny:
+        return case, "full domain"
+    sub = case.replace(nx=sx, ny=sy, name=case.name + f"_sub{sx}x{sy}")
+    return sub, f"{sx}x{sy}x{case.nz} horizontal sub-domain of the same workload"
+
+
+def time_oracle(case, steps: int, warm: int):
+    from oracle import Oracle
+    from paper_2301_04698_gb300 import inputs
+    o = Oracle(case, inputs.initial_state(case))
+    if warm:
+        o.step(warm)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return case.n * steps / dt, dt
+
+
+def cores():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    case = workload(args.workload, 1)
+    sample, desc = oracle_sample(case, args)
+    val, secs = time_oracle(sample, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC[args.workload], "sample": desc},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores(), "kind": "oracle", "sample": desc},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        rc = reference_arm(args, rank, world)
+        barrier(world)
+        return rc
+
+    import numpy as np
+    import torch
+
+    from paper_2301_04698_gb300 import build as B
+    from paper_2301_04698_gb300 import inputs, les
+    if rank == 0:
+        B.build()
+    barrier(world)
+    les.load_library()
+
+    case = workload(args.workload, seed=1 + rank)
+    st0 = inputs.initial_state(case)
+    sim = les.Simulation(case)
+    sim.set_state(st0)
+    stream = sim.stream
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+
+    # warm-up (also fixes dt when it comes from the Courant number)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            sim.step(1, allow_not_converged=True)
+    torch.cuda.synchronize()
+    names = ("u", "v", "w", "p", "theta_l", "q_t")
+    snap = {k: sim.view(k).clone() for k in names}
+
+    # ---- timed region: exactly --steps steps ------------------------------
+    launches0 = sim.launch_count()
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters = 0
+    nc = 0
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            r = sim.step(1, allow_not_converged=True)
+            ev[s][1].record(stream)
+            iters += r["iters_total"]
+            nc += r["not_converged"]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(world)
+    clk = clocks.stop()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    dev_ms = allmax(world, dev_ms)
+    launches = sim.launch_count() - launches0
+    value = world * case.n * args.steps / (dev_ms / 1e3)
+
+    # ---- stage breakdown (Poisson ms / step) -------------------------------
+    for k in names:
+        sim.view(k).copy_(snap[k])
+    stage_ms = {"begin": 0.0, "scalar": 0.0, "momentum": 0.0, "solve": 0.0, "correct": 0.0}
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.zero_()
+            for stg in ["begin"] + ["scalar", "momentum", "solve", "correct"] * case.K + ["end"]:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sim.stage(stg, allow_not_converged=True)
+                b.record(stream)
+                b.synchronize()
+                if stg in stage_ms:
+                    stage_ms[stg] += a.elapsed_time(b)
+    stage_ms = {k: v / args.steps for k, v in stage_ms.items()}
+
+    # ---- per-kernel profile of the same steps -------------------------------
+    for k in names:
+        sim.view(k).copy_(snap[k])
+    sim.profile_reset()
+    sim.profile(True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.zero_()
+            sim.step(1, allow_not_converged=True)
+    kstats = sim.profile_read()
+    sim.profile(False)
+    total_k = sum(k["total_ms"] for k in kstats) or 1.0
+    top = max(kstats, key=lambda k: k["total_ms"])
+    hbm, peak_kind = peaks()
+    mean_ms = top["total_ms"] / max(top["timed"], 1)
+    achieved = top["bytes_per_launch"] / (mean_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic_for(top["name"], args.workload), "kernel": top["name"],
+                "share": top["total_ms"] / total_k, "mean_launch_us": mean_ms * 1e3,
+                "bytes_per_launch": top["bytes_per_launch"], "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "frac_of_8tbs": achieved / 8000.0}
+    kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 4),
+                           "share": round(k["total_ms"] / total_k, 4),
+                           "gbs": round(k["bytes_per_launch"] / (k["total_ms"] / max(k["timed"], 1) / 1e3) / 1e9, 1)
+                           if k["total_ms"] > 0 else None} for k in kstats}
+
+    # ---- end to end through the C ABI with host buffers ----------------------
+    host = {k: snap[k].cpu().pin_memory() for k in names}
+    h2d = sum(h.numel() * h.element_size() for h in host.values())
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        for k in names:
+            sim.set_from_host(k, host[k])
+        sim.step(1, allow_not_converged=True)
+        sim.diagnostics()
+    torch.cuda.synchronize()
+    e2e_s = allmax(world, time.perf_counter() - t0)
+    e2e = {"value": world * case.n * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": les.NDIAG * 8}
+
+    # ---- CPU oracle baseline ---------------------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample, desc = oracle_sample(case, args)
+        val, secs = time_oracle(sample, 1, 0)
+        cpu = {"value": val, "unit": UNIT, "cores": cores(), "kind": "oracle",
+               "sample": f"1 step of the {desc} (FP64, {secs:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if case.precision == 32 else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC[args.workload], "grid": [case.nx, case.ny, case.nz],
+                       "cells": case.n, "K": case.K, "solver": case.solver, "tol": case.tol,
+                       "warm_start": case.warm, "l2": "flushed (256 MiB write) before every timed step",
+                       "replicas": world, "seed": 1},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "poisson": {"ms_per_step": stage_ms["solve"], "iters_per_step": iters / args.steps,
+                        "not_converged": nc, "warm_start": case.warm, "tol": case.tol},
+            "stage_ms_per_step": stage_ms,
+            "kernels": kernels,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    barrier(world)
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

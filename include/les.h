@@ -1,0 +1,253 @@
+/*
+ * les.h -- C ABI of the GB300 LES time-step library (libles.so).
+ *
+ * One time step of the anelastic moist large-eddy simulation of Chammas et al.,
+ * "Accelerating large-eddy simulations of clouds with Tensor Processing Units"
+ * (arXiv 2301.04698): the explicit QUICK / Smagorinsky / thermodynamics stencil
+ * updates and the pressure-correction Poisson solve of the iterative
+ * predictor-corrector scheme (Sec. 2.1-2.4, Appendix A), on one CUDA device.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Grid: nx * ny * nz collocated nodes, node (i,j,k) at ((i+1/2)dx, (j+1/2)dy,
+ *   (k+1/2)dz).  Every field is one contiguous array of nx*ny*nz values in the
+ *   handle's precision (float for precision 32, double for 64), x fastest:
+ *   element (i,j,k) is at offset (k*ny + j)*nx + i.  Periodic in x and y;
+ *   periodic in z or bounded by a surface (k = -1/2) and a lid (k = nz - 1/2).
+ * - Memory: the library allocates no device memory.  The caller supplies one
+ *   device workspace of les_workspace_bytes() bytes (e.g. a torch uint8 tensor)
+ *   that the handle borrows until les_destroy(); every field, solver vector and
+ *   reduction scratch lives in it.  Host buffers passed to get/set are
+ *   borrowed only for the duration of the call.
+ * - Streams: all device work is issued on the handle's stream (cudaStream_t
+ *   given as void*; NULL = legacy default stream).  Calls return when the work
+ *   is enqueued, except where a result must come back to the host (solver
+ *   status, diagnostics, host copies), which synchronise the stream.
+ * - Errors: every call returns a status (LES_OK = 0).  No exception or abort
+ *   crosses the ABI; les_last_error() gives a message for the handle.
+ * - Threads: a handle must not be used from two threads at once.
+ */
+#ifndef LES_H
+#define LES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LES_ABI_VERSION 1
+
+/* ---- status codes -------------------------------------------------------- */
+#define LES_OK                 0
+#define LES_ERR_INVALID_ARG    1  /* bad pointer, size, id or configuration  */
+#define LES_ERR_CUDA           2  /* a CUDA runtime call or launch failed     */
+#define LES_ERR_NOT_CONVERGED  3  /* Poisson solve hit maxit; state is valid  */
+#define LES_ERR_NONFINITE      4  /* NaN / Inf detected in the state          */
+#define LES_ERR_TIMEOUT        5  /* a bounded device wait gave up            */
+#define LES_ERR_STATE          6  /* call out of order (e.g. stage sequence)  */
+#define LES_ERR_NO_MODEL       7  /* learned warm start requested, none set   */
+
+/* ---- physics switches (les_config.physics) -------------------------------- */
+#define LES_PHYS_ADV       (1u << 0)  /* QUICK advection, Sec. 2.4             */
+#define LES_PHYS_SGS       (1u << 1)  /* Smagorinsky-Lilly nu_t, Sec. 2.3      */
+#define LES_PHYS_CONST_NU  (1u << 2)  /* constant viscosity const_nu instead   */
+#define LES_PHYS_MOIST     (1u << 3)  /* saturation adjustment, Sec. 2.2       */
+#define LES_PHYS_BUOY      (1u << 4)  /* rho0 b k in Eq. (momentum)            */
+#define LES_PHYS_CORIOLIS  (1u << 5)  /* -f k x rho0 (u - u_g)                 */
+#define LES_PHYS_SPONGE    (1u << 6)  /* Rayleigh sponge near the lid, Sec 2.3 */
+#define LES_PHYS_RAD       (1u << 7)  /* longwave flux divergence (theta_l)    */
+#define LES_PHYS_SUBS      (1u << 8)  /* large-scale subsidence                */
+#define LES_PHYS_SFC       (1u << 9)  /* surface fluxes of theta_l and q_t     */
+#define LES_PHYS_FB        (1u << 10) /* stratification factor f_B in nu_t    */
+
+/* ---- enumerations -------------------------------------------------------- */
+#define LES_BC_PERIODIC    0
+#define LES_BC_WALLS       1          /* free-slip surface, no-slip lid (Sec 4) */
+#define LES_SOLVER_CG      0          /* conjugate gradient, FP64 dot products  */
+#define LES_SOLVER_JACOBI  1          /* weighted Jacobi, the paper's solver    */
+#define LES_OP_COMPACT     0          /* L_c psi = rhs - C(psi^k), App. A       */
+#define LES_OP_WIDE        1          /* D(rho0 G psi) = D(rho0 u^)/dt          */
+#define LES_WARM_ZERO      0
+#define LES_WARM_PREV      1          /* previous step's solve, same sub-iter   */
+#define LES_WARM_LEARNED   2          /* learned network (les_set_warm_model)   */
+
+/* field ids for get / set / offset */
+enum les_field {
+  LES_U = 0, LES_V, LES_W,        /* velocity (u^{n+1} between steps)          */
+  LES_P,                          /* perturbation pressure p'                  */
+  LES_THETA_L, LES_QT,            /* liquid potential temperature, total water */
+  LES_UN, LES_VN, LES_WN,         /* u^n during a step                         */
+  LES_THETA_L_HALF, LES_QT_HALF,  /* phi^{n+1/2} during a step                 */
+  LES_UHAT, LES_VHAT, LES_WHAT,   /* predicted velocity (rho0 u)^ / rho0       */
+  LES_RHS,                        /* Poisson right-hand side                   */
+  LES_PSI,                        /* alpha0 * dp, the Poisson unknown          */
+  LES_B, LES_QL, LES_T,           /* buoyancy, liquid water, temperature       */
+  LES_SRAD,                       /* radiative source of rho0 theta_l          */
+  LES_NFIELD
+};
+
+/* stages of one step, for les_stage(): BEGIN, then n_subiter times
+ * (SCALAR, MOMENTUM, SOLVE, CORRECT), then END (Sec. 2.4) */
+enum les_stage_id {
+  LES_STAGE_BEGIN = 0,   /* dt (if 0), phi^{n+1/2} thermodynamics -> T, q_l, b,
+                            radiative source; u^n, phi^{n+1/2} saved; dp = 0   */
+  LES_STAGE_SCALAR,      /* Eq. (scalar_prediction_step) -> phi^{k+1}          */
+  LES_STAGE_MOMENTUM,    /* Eq. (momentum_prediction_step) -> u^, and the
+                            Poisson right side (Eq. pressure_correction, App. A) */
+  LES_STAGE_SOLVE,       /* Poisson solve for psi = alpha0 dp                  */
+  LES_STAGE_CORRECT,     /* (rho0 u)^{k+1} = (rho0 u)^ - dt rho0 G psi,
+                            p^{k+1} = p^k + rho0 psi                           */
+  LES_STAGE_END
+};
+
+/* Configuration.  Readings of points the paper leaves open are documented
+ * with the library; defaults come from les_config_default(). */
+typedef struct les_config {
+  uint32_t struct_size;      /* sizeof(les_config), ABI check               */
+  int32_t  precision;        /* 32 or 64                                    */
+  int32_t  nx, ny, nz;       /* >= 3, >= 3, >= 2                            */
+  int32_t  bc_z;             /* LES_BC_PERIODIC | LES_BC_WALLS              */
+  double   dx, dy, dz;       /* spacings (m)                                */
+  double   dt;               /* > 0 fixed; 0 = cfl / max(|u|/dx+|v|/dy+|w|/dz)
+                                from the state at the first step, then held */
+  double   cfl;
+  int32_t  n_subiter;        /* K sub-iterations per step (>= 1)             */
+  int32_t  solver;           /* LES_SOLVER_*                                */
+  int32_t  poisson_op;       /* LES_OP_*                                    */
+  int32_t  warm_start;       /* LES_WARM_*                                  */
+  double   poisson_tol;      /* ||b - A x||_2 <= tol ||b||_2                */
+  int32_t  poisson_maxit;
+  uint32_t physics;          /* LES_PHYS_* bits                             */
+  double   jacobi_omega;
+  double   cs, pr, sc;       /* Smagorinsky constant, Prandtl, Schmidt      */
+  double   const_nu;         /* viscosity with LES_PHYS_CONST_NU (m^2/s)    */
+  double   f_cor, ug, vg;    /* Coriolis parameter, geostrophic wind        */
+  double   sponge_frac;      /* sponge occupies the top fraction            */
+  double   sponge_rate;      /* Rayleigh rate at the lid (1/s)              */
+  double   subs_div;         /* D in the subsidence speed D z (1/s)         */
+  double   shf, lhf;         /* surface sensible / latent heat flux (W/m^2) */
+  double   rad_f0, rad_f1;   /* longwave flux amplitudes (W/m^2)            */
+  double   rad_kappa;        /* absorption coefficient (m^2/kg)             */
+  double   theta0, p00;      /* reference potential temperature, pressure   */
+  double   sat_tol;          /* secant stop |theta_l* - theta_l| (K)        */
+  int32_t  sat_maxit;
+  int32_t  reserved0;
+  double   reserved[4];
+} les_config;
+
+typedef struct les_step_stats {
+  int32_t steps;             /* steps completed by the call                 */
+  int32_t solves;            /* Poisson solves                              */
+  int32_t iters_total;       /* solver iterations summed over the solves    */
+  int32_t iters_max;         /* most iterations in one solve                */
+  int32_t not_converged;     /* solves that stopped at maxit                */
+  int32_t reserved0;
+  double  res_max;           /* largest final relative residual             */
+  double  dt;                /* the step size in use                        */
+} les_step_stats;
+
+#define LES_NDIAG 10
+/* les_diagnostics() output, all accumulated in FP64 on the device:
+ * [0] sum rho0 theta_l dV   [1] sum rho0 q_t dV    [2..4] sum rho0 u_c dV
+ * [5] 1/2 sum rho0 |u|^2 dV [6] max Courant number [7] max |D(rho0 u)|
+ * [8] number of non-finite values in u, v, w, p, theta_l, q_t
+ * [9] sum rho0 q_l dV */
+
+typedef struct les_handle les_handle;
+
+/* Fill *cfg with the paper's Table 1 constants and library defaults for an
+ * nx*ny*nz grid.  Never fails. */
+void les_config_default(les_config *cfg, int32_t nx, int32_t ny, int32_t nz);
+
+/* Bytes of device workspace that les_init needs for *cfg (256-B aligned
+ * sub-buffers).  Returns LES_ERR_INVALID_ARG for an invalid configuration. */
+int les_workspace_bytes(const les_config *cfg, size_t *bytes);
+
+/* Create a handle.  rho0_z: optional host array of nz reference densities
+ * (NULL = the hydrostatic adiabatic profile of Sec. 2.1, Eqs. 2-4).
+ * workspace: device pointer (>= 256-B aligned) of at least
+ * les_workspace_bytes() bytes, borrowed until les_destroy.  stream: a
+ * cudaStream_t or NULL.  The state starts at zero. */
+int les_init(const les_config *cfg, const double *rho0_z, void *workspace,
+             size_t workspace_bytes, void *stream, les_handle **out);
+
+/* Release the handle (not the workspace).  NULL is accepted. */
+void les_destroy(les_handle *h);
+
+/* Re-target all later work to another stream. */
+int les_set_stream(les_handle *h, void *stream);
+
+/* Copy nx*ny*nz values of the handle's precision into / out of a field.
+ * on_device != 0: src / dst is a device pointer (stream-ordered copy);
+ * otherwise a host pointer (the call synchronises the stream). */
+int les_set_state(les_handle *h, int32_t field, const void *src, int32_t on_device);
+int les_get_state(les_handle *h, int32_t field, void *dst, int32_t on_device);
+
+/* Byte offset of a field's current buffer inside the workspace (buffers of
+ * the scalars and u^n rotate between steps and sub-iterations). */
+int les_field_offset(les_handle *h, int32_t field, size_t *offset);
+
+/* Advance nsteps time steps (Sec. 2.4).  stats may be NULL.  Returns
+ * LES_ERR_NOT_CONVERGED if any solve stopped at maxit (the state is still
+ * advanced), LES_ERR_INVALID_ARG if dt = 0 and the fluid is at rest. */
+int les_step(les_handle *h, int32_t nsteps, les_step_stats *stats);
+
+/* Run one stage of the step (enum les_stage_id) in the documented order;
+ * returns LES_ERR_STATE when called out of order.  stats may be NULL. */
+int les_stage(les_handle *h, int32_t stage, les_step_stats *stats);
+
+/* Solve A x = b with the handle's operator, boundary conditions and solver:
+ * A = L_c (LES_OP_COMPACT) or D(rho0 G .) (LES_OP_WIDE).  b's mean is
+ * removed first and x is returned with zero mean.  d_rhs, d_x: device arrays
+ * of nx*ny*nz values, distinct from the handle's fields; x holds the initial
+ * guess on entry.  rtol > 0, maxit >= 0.  iters / rel_res may be NULL.
+ * Synchronises the stream.  LES_ERR_NOT_CONVERGED if maxit was reached. */
+int les_poisson_solve(les_handle *h, const void *d_rhs, void *d_x, double rtol,
+                      int32_t maxit, int32_t *iters, double *rel_res);
+
+/* y = A x for op = LES_OP_COMPACT or LES_OP_WIDE (device arrays). */
+int les_apply_poisson(les_handle *h, int32_t op, const void *d_x, void *d_y);
+
+/* FP64 diagnostics of the current state (layout above); out: host array of
+ * LES_NDIAG doubles.  Synchronises the stream. */
+int les_diagnostics(les_handle *h, double *out);
+
+/* ---- launch accounting and event profiling -------------------------------- */
+#define LES_MAX_KERNELS 32
+typedef struct les_kernel_stat {
+  char    name[24];          /* kernel class, e.g. "cg_matvec"                     */
+  int32_t fields_per_cell;   /* algorithmic fields read + written per launch/cell  */
+  int32_t reserved0;
+  int64_t launches;          /* launches since the last reset                      */
+  int64_t timed;             /* launches bracketed by events (profiling enabled)   */
+  double  total_ms;          /* summed event time of the timed launches            */
+  double  bytes_per_launch;  /* fields_per_cell * nx*ny*nz * sizeof(element)       */
+} les_kernel_stat;
+
+/* Enable (1) / disable (0) CUDA-event timing of every kernel launch on the
+ * handle's stream (adds two event records per launch).  Launches are always
+ * counted. */
+int les_profile_enable(les_handle *h, int32_t enable);
+/* Copy up to max_entries kernel classes with at least one launch into out
+ * (host array); *count receives the number written.  Synchronises on the
+ * last recorded event. */
+int les_profile_read(les_handle *h, les_kernel_stat *out, int32_t max_entries, int32_t *count);
+/* Zero the launch counts and timings. */
+int les_profile_reset(les_handle *h);
+/* Total kernel launches issued by the handle since creation or reset. */
+int64_t les_launch_count(const les_handle *h);
+
+/* The step size (0 until fixed by the first step when cfg.dt == 0). */
+double les_get_dt(const les_handle *h);
+int    les_set_dt(les_handle *h, double dt);
+
+/* Message of the last failed call on h (static string if h is NULL). */
+const char *les_last_error(const les_handle *h);
+const char *les_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LES_H */

@@ -1,0 +1,230 @@
+// les_internal.h -- host-side declarations shared by the translation units of
+// libles.so (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "les.h"
+#include "les_common.cuh"
+
+namespace les {
+
+// Physical constants of Table 1 (and the reading of the saturation vapour
+// pressure: Clausius-Clapeyron with constant L_v0 from the triple point).
+constexpr double kRd = 287.0;
+constexpr double kRv = 461.89;
+constexpr double kCpd = 1004.5;
+constexpr double kCpv = 1859.5;
+constexpr double kCl = 4181.0;
+constexpr double kLv0 = 2.47e6;
+constexpr double kGrav = 9.81;
+constexpr double kTtr = 273.16;
+constexpr double kEtr = 611.657;
+
+// Per-launch physics parameters (passed by value).
+template <typename T>
+struct Phys {
+  uint32_t flags;
+  T dt;
+  T cs2d2;            // (c_s Delta)^2
+  T inv_pr, inv_sc;
+  T nu_const;
+  T f_cor, ug, vg;
+  T sponge_rate, sponge_zs, sponge_h;
+  T subs_div;
+  T sflux_th, sflux_qt;  // rho0 (w' phi')_s: SHF / c_pd, LHF / L_v0
+  T rad_f0, rad_f1, rad_kappa;
+  T p00;
+  T sat_tol;
+  int sat_maxit;
+  const T* rho0;      // nz
+  const T* alpha0;    // nz
+  const T* p0;        // nz
+};
+
+// Device-side solver control block (lives in the workspace).
+struct SolverCtl {
+  double sum;       // result of the last mean reduction
+  double bn2;       // ||b - mean(b)||^2
+  double rr;        // r.r
+  double pq;        // p.Ap
+  double alpha, beta;
+  double rel;       // current relative residual
+  double tol;
+  int iter, maxit;
+  int done;         // 0 running, 1 converged, 2 maxit, 3 breakdown, 4 zero rhs
+  int first;        // next CG iteration is the first one
+  int answer;       // Jacobi: buffer holding the answer (0 = x, 1 = scratch)
+  int pad;
+  double scal;      // misc scalar (CFL max)
+  unsigned tickets[8];
+};
+
+enum Ticket { TK_SUM = 0, TK_INIT, TK_MATVEC, TK_UPDATE, TK_JACOBI, TK_DIAG, TK_MAX, TK_SPARE };
+
+struct LaunchCfg {
+  dim3 grid, block;
+};
+
+// Kernel classes for launch counting and the optional event profiler.
+enum KernelId : int {
+  KI_THERMO = 0, KI_RADIATION, KI_NU, KI_NU_HALF, KI_SCALAR, KI_MOMENTUM, KI_RHS, KI_CORRECT,
+  KI_DIAG, KI_CFL, KI_APPLY, KI_SUM, KI_CG_INIT, KI_CG_MATVEC, KI_CG_UPDATE, KI_JACOBI, KI_FINISH,
+  KI_CTL, KI_COUNT
+};
+extern const char* const kKernelNames[KI_COUNT];
+
+// Counts every launch; when enabled, brackets each launch with a pair of
+// CUDA events on the launching stream and accumulates the elapsed times.
+struct Profiler {
+  bool on = false;
+  long long launches[KI_COUNT] = {};
+  long long timed[KI_COUNT] = {};
+  double ms[KI_COUNT] = {};
+  struct Rec {
+    int id;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+
+  cudaEvent_t take() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void begin(int id, cudaStream_t st) {
+    launches[id] += 1;
+    if (!on) return;
+    Rec r{id, take(), take()};
+    cudaEventRecord(r.a, st);
+    pending.push_back(r);
+  }
+  void end(cudaStream_t st) {
+    if (!on || pending.empty()) return;
+    cudaEventRecord(pending.back().b, st);
+  }
+  // fold the finished records into the totals (synchronises on the last one)
+  cudaError_t collect() {
+    if (pending.empty()) return cudaSuccess;
+    cudaError_t e = cudaEventSynchronize(pending.back().b);
+    if (e != cudaSuccess) return e;
+    for (auto& r : pending) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+        ms[r.id] += t;
+        timed[r.id] += 1;
+      }
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    pending.clear();
+    return cudaSuccess;
+  }
+  void reset() {
+    collect();
+    for (int i = 0; i < KI_COUNT; ++i) launches[i] = timed[i] = 0, ms[i] = 0.0;
+  }
+  ~Profiler() {
+    for (auto& r : pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+// launch bracket: counts (and optionally times) one kernel launch
+struct ProfScope {
+  Profiler* p;
+  cudaStream_t st;
+  ProfScope(Profiler* prof, int id, cudaStream_t s) : p(prof), st(s) {
+    if (p) p->begin(id, st);
+  }
+  ~ProfScope() {
+    if (p) p->end(st);
+  }
+};
+
+template <typename T>
+Grid<T> make_grid(const les_config& c, int zc);
+
+template <typename T>
+LaunchCfg tile_launch(const Grid<T>& g, int max_blocks);
+
+// ---- stencil stage launchers (les_stencil.cu) ------------------------------
+template <typename T>
+struct StageArgs {
+  Grid<T> g;
+  Phys<T> ph;
+  LaunchCfg lc;
+  cudaStream_t st;
+  Profiler* prof;
+};
+
+template <typename T>
+cudaError_t launch_thermo(const StageArgs<T>& a, const T* th, const T* qt, T* temp, T* ql, T* b,
+                          T* srad);
+template <typename T>
+cudaError_t launch_nu(const StageArgs<T>& a, const T* u, const T* v, const T* w, const T* un,
+                      const T* vn, const T* wn, const T* b, T* uh, T* vh, T* wh, T* nu);
+template <typename T>
+cudaError_t launch_scalar(const StageArgs<T>& a, const T* u, const T* v, const T* w, const T* nu,
+                          const T* thk, const T* qtk, const T* thh, const T* qth, const T* srad,
+                          T* th_out, T* qt_out);
+template <typename T>
+cudaError_t launch_momentum(const StageArgs<T>& a, const T* uh, const T* vh, const T* wh,
+                            const T* un, const T* vn, const T* wn, const T* nu, const T* p,
+                            const T* b, T* ou, T* ov, T* ow);
+template <typename T>
+cudaError_t launch_rhs(const StageArgs<T>& a, int op, const T* ou, const T* ov, const T* ow,
+                       const T* psi, T* rhs);
+template <typename T>
+cudaError_t launch_correct(const StageArgs<T>& a, const T* ou, const T* ov, const T* ow,
+                           const T* psi, T* u, T* v, T* w, T* p);
+template <typename T>
+cudaError_t launch_diag(const StageArgs<T>& a, const T* u, const T* v, const T* w, const T* p,
+                        const T* th, const T* qt, const T* ql, double* partials, SolverCtl* ctl,
+                        double* out_dev /* LES_NDIAG */);
+template <typename T>
+cudaError_t launch_cfl_max(const StageArgs<T>& a, const T* u, const T* v, const T* w,
+                           double* partials, SolverCtl* ctl);
+
+// ---- Poisson solver (les_solver.cu) ----------------------------------------
+template <typename T>
+struct SolverArgs {
+  Grid<T> g;
+  LaunchCfg lc;
+  cudaStream_t st;
+  int op;            // LES_OP_*
+  int solver;        // LES_SOLVER_*
+  double omega;
+  const T* rho0;
+  SolverCtl* ctl;    // device
+  SolverCtl* ctl_host;  // pinned host mirror
+  double* partials;  // device
+  T* r;              // work vectors (n each)
+  T* p0;
+  T* p1;
+  T* q;
+  Profiler* prof;
+};
+
+template <typename T>
+cudaError_t launch_apply(const SolverArgs<T>& a, int op, const T* x, T* y);
+
+// Solve A x = b; returns LES_OK / LES_ERR_NOT_CONVERGED / LES_ERR_CUDA.
+template <typename T>
+int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxit, int* iters,
+                  double* rel, std::string* err);
+
+}  // namespace les

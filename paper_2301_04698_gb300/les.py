@@ -1,0 +1,328 @@
+"""Thin Python binding of libles.so (include/les.h): argument marshalling only.
+
+Every step of the time step runs in the library's CUDA kernels; this module
+allocates the device workspace as a torch tensor, passes raw pointers, sizes
+and the current torch stream across the C ABI, and converts status codes into
+exceptions.  If libles.so is missing it raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libles.so")
+
+# ---- mirrors of include/les.h -----------------------------------------------
+LES_OK, LES_ERR_INVALID_ARG, LES_ERR_CUDA, LES_ERR_NOT_CONVERGED = 0, 1, 2, 3
+LES_ERR_NONFINITE, LES_ERR_TIMEOUT, LES_ERR_STATE, LES_ERR_NO_MODEL = 4, 5, 6, 7
+
+PHYS_BITS = {"adv": 1 << 0, "sgs": 1 << 1, "const_nu": 1 << 2, "moist": 1 << 3, "buoy": 1 << 4,
+             "coriolis": 1 << 5, "sponge": 1 << 6, "rad": 1 << 7, "subs": 1 << 8, "sfc": 1 << 9,
+             "fb": 1 << 10}
+FIELDS = {"u": 0, "v": 1, "w": 2, "p": 3, "theta_l": 4, "q_t": 5, "u_n": 6, "v_n": 7, "w_n": 8,
+          "theta_l_half": 9, "q_t_half": 10, "u_hat": 11, "v_hat": 12, "w_hat": 13, "rhs": 14,
+          "psi": 15, "b": 16, "q_l": 17, "T": 18, "s_rad": 19}
+STAGES = {"begin": 0, "scalar": 1, "momentum": 2, "solve": 3, "correct": 4, "end": 5}
+SOLVERS = {"cg": 0, "jacobi": 1}
+OPS = {"compact": 0, "wide": 1}
+WARM = {"zero": 0, "prev": 1, "learned": 2}
+NDIAG = 10
+DIAG_NAMES = ("sum_rho_theta", "sum_rho_qt", "sum_rho_u", "sum_rho_v", "sum_rho_w",
+              "kinetic_energy", "max_cfl", "max_div", "nonfinite", "sum_rho_ql")
+
+#: every symbol declared in include/les.h
+EXPORTED = ("les_config_default", "les_workspace_bytes", "les_init", "les_destroy", "les_set_stream",
+            "les_set_state", "les_get_state", "les_field_offset", "les_step", "les_stage",
+            "les_poisson_solve", "les_apply_poisson", "les_diagnostics", "les_get_dt", "les_set_dt",
+            "les_last_error", "les_status_string", "les_profile_enable", "les_profile_read",
+            "les_profile_reset", "les_launch_count")
+
+
+class LesConfig(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_uint32), ("precision", C.c_int32),
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("bc_z", C.c_int32),
+        ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+        ("dt", C.c_double), ("cfl", C.c_double),
+        ("n_subiter", C.c_int32), ("solver", C.c_int32), ("poisson_op", C.c_int32),
+        ("warm_start", C.c_int32),
+        ("poisson_tol", C.c_double), ("poisson_maxit", C.c_int32), ("physics", C.c_uint32),
+        ("jacobi_omega", C.c_double), ("cs", C.c_double), ("pr", C.c_double), ("sc", C.c_double),
+        ("const_nu", C.c_double), ("f_cor", C.c_double), ("ug", C.c_double), ("vg", C.c_double),
+        ("sponge_frac", C.c_double), ("sponge_rate", C.c_double), ("subs_div", C.c_double),
+        ("shf", C.c_double), ("lhf", C.c_double), ("rad_f0", C.c_double), ("rad_f1", C.c_double),
+        ("rad_kappa", C.c_double), ("theta0", C.c_double), ("p00", C.c_double),
+        ("sat_tol", C.c_double), ("sat_maxit", C.c_int32), ("reserved0", C.c_int32),
+        ("reserved", C.c_double * 4),
+    ]
+
+
+class LesStepStats(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("solves", C.c_int32), ("iters_total", C.c_int32),
+                ("iters_max", C.c_int32), ("not_converged", C.c_int32), ("reserved0", C.c_int32),
+                ("res_max", C.c_double), ("dt", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+class LesKernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("fields_per_cell", C.c_int32), ("reserved0", C.c_int32),
+                ("launches", C.c_int64), ("timed", C.c_int64), ("total_ms", C.c_double),
+                ("bytes_per_launch", C.c_double)]
+
+
+class LesError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libles.so.  Raises if it has not been built -- never falls back."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2301_04698_gb300.build.build() "
+                           "(the LES path has no CPU fallback)")
+    lib = C.CDLL(path)
+    vp, i32, dbl, sz = C.c_void_p, C.c_int32, C.c_double, C.c_size_t
+    cfgp = C.POINTER(LesConfig)
+    statp = C.POINTER(LesStepStats)
+    lib.les_config_default.restype = None
+    lib.les_config_default.argtypes = [cfgp, i32, i32, i32]
+    lib.les_workspace_bytes.restype = C.c_int
+    lib.les_workspace_bytes.argtypes = [cfgp, C.POINTER(sz)]
+    lib.les_init.restype = C.c_int
+    lib.les_init.argtypes = [cfgp, C.POINTER(dbl), vp, sz, vp, C.POINTER(vp)]
+    lib.les_destroy.restype = None
+    lib.les_destroy.argtypes = [vp]
+    lib.les_set_stream.restype = C.c_int
+    lib.les_set_stream.argtypes = [vp, vp]
+    lib.les_set_state.restype = C.c_int
+    lib.les_set_state.argtypes = [vp, i32, vp, i32]
+    lib.les_get_state.restype = C.c_int
+    lib.les_get_state.argtypes = [vp, i32, vp, i32]
+    lib.les_field_offset.restype = C.c_int
+    lib.les_field_offset.argtypes = [vp, i32, C.POINTER(sz)]
+    lib.les_step.restype = C.c_int
+    lib.les_step.argtypes = [vp, i32, statp]
+    lib.les_stage.restype = C.c_int
+    lib.les_stage.argtypes = [vp, i32, statp]
+    lib.les_poisson_solve.restype = C.c_int
+    lib.les_poisson_solve.argtypes = [vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl)]
+    lib.les_apply_poisson.restype = C.c_int
+    lib.les_apply_poisson.argtypes = [vp, i32, vp, vp]
+    lib.les_diagnostics.restype = C.c_int
+    lib.les_diagnostics.argtypes = [vp, C.POINTER(dbl)]
+    lib.les_get_dt.restype = dbl
+    lib.les_get_dt.argtypes = [vp]
+    lib.les_set_dt.restype = C.c_int
+    lib.les_set_dt.argtypes = [vp, dbl]
+    lib.les_last_error.restype = C.c_char_p
+    lib.les_last_error.argtypes = [vp]
+    lib.les_status_string.restype = C.c_char_p
+    lib.les_status_string.argtypes = [C.c_int]
+    lib.les_profile_enable.restype = C.c_int
+    lib.les_profile_enable.argtypes = [vp, i32]
+    lib.les_profile_read.restype = C.c_int
+    lib.les_profile_read.argtypes = [vp, C.POINTER(LesKernelStat), i32, C.POINTER(i32)]
+    lib.les_profile_reset.restype = C.c_int
+    lib.les_profile_reset.argtypes = [vp]
+    lib.les_launch_count.restype = C.c_int64
+    lib.les_launch_count.argtypes = [vp]
+    _lib = lib
+    return lib
+
+
+def config_from_case(case) -> LesConfig:
+    """les_config for a workload description (attributes as in inputs.Case)."""
+    lib = load_library()
+    c = LesConfig()
+    lib.les_config_default(C.byref(c), case.nx, case.ny, case.nz)
+    c.precision = int(case.precision)
+    c.bc_z = 1 if case.walls else 0
+    c.dx, c.dy, c.dz = float(case.dx), float(case.dy), float(case.dz)
+    c.dt, c.cfl = float(case.dt), float(case.cfl)
+    c.n_subiter = int(case.K)
+    c.solver = SOLVERS[case.solver]
+    c.poisson_op = OPS[case.op]
+    c.warm_start = WARM[case.warm]
+    c.poisson_tol, c.poisson_maxit = float(case.tol), int(case.maxit)
+    phys = 0
+    for name in case.physics:
+        phys |= PHYS_BITS[name]
+    c.physics = phys
+    c.jacobi_omega = float(case.omega)
+    for k in ("cs", "pr", "sc", "f_cor", "ug", "vg", "sponge_frac", "sponge_rate", "subs_div", "shf",
+              "lhf", "rad_f0", "rad_f1", "rad_kappa", "theta0", "p00", "sat_tol"):
+        setattr(c, k, float(getattr(case, k)))
+    c.const_nu = float(case.nu_const)
+    c.sat_maxit = int(case.sat_maxit)
+    return c
+
+
+def _check(lib, h, rc, what, allow=(LES_OK,)):
+    if rc in allow:
+        return rc
+    msg = lib.les_last_error(h).decode() if h else lib.les_status_string(rc).decode()
+    raise LesError(rc, f"{what}: {lib.les_status_string(rc).decode()}: {msg}")
+
+
+class Simulation:
+    """One LES on the current CUDA device, behind the C ABI."""
+
+    def __init__(self, case, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = lib = load_library()
+        self.case = case
+        self.cfg = config_from_case(case)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.dtype = torch.float64 if case.precision == 64 else torch.float32
+        self.np_dtype = np.float64 if case.precision == 64 else np.float32
+        self.shape = (case.nz, case.ny, case.nx)
+        self.n = case.nx * case.ny * case.nz
+        self.esize = 8 if case.precision == 64 else 4
+        nbytes = C.c_size_t(0)
+        _check(lib, None, lib.les_workspace_bytes(C.byref(self.cfg), C.byref(nbytes)), "les_workspace_bytes")
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        rho = case.rho0_profile() if hasattr(case, "rho0_profile") else None
+        self._rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+        h = C.c_void_p()
+        rc = lib.les_init(C.byref(self.cfg),
+                          self._rho.ctypes.data_as(C.POINTER(C.c_double)) if self._rho is not None else None,
+                          C.c_void_p(self.workspace.data_ptr()), nbytes, C.c_void_p(self.stream.cuda_stream),
+                          C.byref(h))
+        _check(lib, None, rc, "les_init")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.les_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- fields ---------------------------------------------------------------
+    def view(self, name: str):
+        """Zero-copy torch view of a field's current buffer (shape nz, ny, nx)."""
+        off = C.c_size_t(0)
+        _check(self.lib, self.h, self.lib.les_field_offset(self.h, FIELDS[name], C.byref(off)), "offset")
+        raw = self.workspace[off.value: off.value + self.n * self.esize]
+        return raw.view(self.dtype).view(self.shape)
+
+    def set(self, name: str, value) -> None:
+        t = self.torch
+        if isinstance(value, np.ndarray):
+            src = t.from_numpy(np.ascontiguousarray(value.reshape(self.shape), dtype=self.np_dtype))
+            src = src.to(self.device, non_blocking=False)
+        else:
+            src = value.reshape(self.shape).to(device=self.device, dtype=self.dtype).contiguous()
+        with t.cuda.stream(self.stream):
+            rc = self.lib.les_set_state(self.h, FIELDS[name], C.c_void_p(src.data_ptr()), 1)
+        _check(self.lib, self.h, rc, f"set {name}")
+        self.stream.synchronize()
+
+    def set_state(self, state: dict) -> None:
+        for k in ("u", "v", "w", "p", "theta_l", "q_t"):
+            if k in state:
+                self.set(k, state[k])
+
+    def set_from_host(self, name: str, host) -> None:
+        """Host-buffer transfer through the ABI (host pointer, synchronous)."""
+        rc = self.lib.les_set_state(self.h, FIELDS[name], C.c_void_p(host.data_ptr()), 0)
+        _check(self.lib, self.h, rc, f"set {name} (host)")
+
+    def get_to_host(self, name: str, host) -> None:
+        rc = self.lib.les_get_state(self.h, FIELDS[name], C.c_void_p(host.data_ptr()), 0)
+        _check(self.lib, self.h, rc, f"get {name} (host)")
+
+    def get(self, name: str) -> np.ndarray:
+        out = np.empty(self.shape, dtype=self.np_dtype)
+        rc = self.lib.les_get_state(self.h, FIELDS[name], C.c_void_p(out.ctypes.data), 0)
+        _check(self.lib, self.h, rc, f"get {name}")
+        return out
+
+    # -- stepping -------------------------------------------------------------
+    def step(self, nsteps: int = 1, allow_not_converged: bool = False) -> dict:
+        st = LesStepStats()
+        allow = (LES_OK, LES_ERR_NOT_CONVERGED) if allow_not_converged else (LES_OK,)
+        rc = self.lib.les_step(self.h, int(nsteps), C.byref(st))
+        _check(self.lib, self.h, rc, "les_step", allow)
+        d = st.as_dict()
+        d["status"] = rc
+        return d
+
+    def stage(self, name: str, allow_not_converged: bool = False) -> dict:
+        st = LesStepStats()
+        allow = (LES_OK, LES_ERR_NOT_CONVERGED) if allow_not_converged else (LES_OK,)
+        rc = self.lib.les_stage(self.h, STAGES[name], C.byref(st))
+        _check(self.lib, self.h, rc, f"les_stage({name})", allow)
+        d = st.as_dict()
+        d["status"] = rc
+        return d
+
+    @property
+    def dt(self) -> float:
+        return self.lib.les_get_dt(self.h)
+
+    @dt.setter
+    def dt(self, v: float) -> None:
+        _check(self.lib, self.h, self.lib.les_set_dt(self.h, float(v)), "les_set_dt")
+
+    # -- solver ---------------------------------------------------------------
+    def poisson_solve(self, rhs, x, tol: float, maxit: int, allow_not_converged: bool = False):
+        it = C.c_int32(0)
+        rel = C.c_double(0.0)
+        rc = self.lib.les_poisson_solve(self.h, C.c_void_p(rhs.data_ptr()), C.c_void_p(x.data_ptr()),
+                                        float(tol), int(maxit), C.byref(it), C.byref(rel))
+        allow = (LES_OK, LES_ERR_NOT_CONVERGED) if allow_not_converged else (LES_OK,)
+        _check(self.lib, self.h, rc, "les_poisson_solve", allow)
+        return rc, it.value, rel.value
+
+    def apply_poisson(self, x, op: str = "compact"):
+        y = self.torch.empty_like(x)
+        rc = self.lib.les_apply_poisson(self.h, OPS[op], C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()))
+        _check(self.lib, self.h, rc, "les_apply_poisson")
+        return y
+
+    # -- profiling ------------------------------------------------------------
+    def profile(self, enable: bool) -> None:
+        _check(self.lib, self.h, self.lib.les_profile_enable(self.h, int(bool(enable))), "profile")
+
+    def profile_reset(self) -> None:
+        _check(self.lib, self.h, self.lib.les_profile_reset(self.h), "profile reset")
+
+    def profile_read(self) -> list:
+        arr = (LesKernelStat * 32)()
+        cnt = C.c_int32(0)
+        _check(self.lib, self.h, self.lib.les_profile_read(self.h, arr, 32, C.byref(cnt)), "profile read")
+        out = []
+        for k in arr[:cnt.value]:
+            out.append({"name": k.name.decode(), "fields_per_cell": k.fields_per_cell,
+                        "launches": k.launches, "timed": k.timed, "total_ms": k.total_ms,
+                        "bytes_per_launch": k.bytes_per_launch})
+        return out
+
+    def launch_count(self) -> int:
+        return int(self.lib.les_launch_count(self.h))
+
+    def diagnostics(self) -> dict:
+        out = (C.c_double * NDIAG)()
+        rc = self.lib.les_diagnostics(self.h, out)
+        _check(self.lib, self.h, rc, "les_diagnostics", (LES_OK, LES_ERR_NONFINITE))
+        return dict(zip(DIAG_NAMES, list(out)))

@@ -1,0 +1,289 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element,
+on the same seeded inputs.
+
+Tolerances: FP64 runs agree to rounding amplified by the solver tolerance --
+each Poisson solve stops at a relative residual tol, so the two solutions
+differ by at most about cond(L) * tol; the 100-step Taylor-Green case uses the
+stated bar of 1e-5 relative L2 per field.  FP32 runs are compared with the
+FP64 oracle over a short horizon with per-field bounds derived from float
+rounding (2^-24 ~ 6e-8 per operation, amplified by the stencil sums).
+"""
+import numpy as np
+import pytest
+
+from paper_2301_04698_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def les_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2301_04698_gb300 import build, les
+    build.build()
+    les.load_library()
+    return les
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def demean(a):
+    return a - a.mean()
+
+
+def pair(les_mod, case, state=None):
+    from oracle import Oracle
+    st = state if state is not None else inputs.initial_state(case)
+    sim = les_mod.Simulation(case)
+    sim.set_state(st)
+    ref = Oracle(case, st)
+    return sim, ref, st
+
+
+def random_state(case, seed=3, amp=1.0, th=(289.0, 4.0), qt=(8e-3, 3e-3)):
+    n, s = case.n, case.shape
+    st = {k: amp * inputs.uniform(seed, i, n, -1, 1).reshape(s) for i, k in enumerate(("u", "v", "w"))}
+    st["theta_l"] = th[0] + th[1] * inputs.uniform(seed, 3, n, -1, 1).reshape(s)
+    st["q_t"] = qt[0] + qt[1] * inputs.uniform(seed, 4, n, -1, 1).reshape(s)
+    st["p"] = 10.0 * inputs.uniform(seed, 5, n, -1, 1).reshape(s)
+    return st
+
+
+# --------------------------------------------------------------------------
+# Poisson operator and solver
+
+
+@pytest.mark.parametrize("walls", [False, True])
+@pytest.mark.parametrize("op", ["compact", "wide"])
+def test_poisson_operator(les_mod, walls, op):
+    from oracle import Oracle
+    case = inputs.Case(name="op", nx=37, ny=11, nz=10, dx=0.3, dy=0.2, dz=0.1, walls=walls,
+                       precision=64, init="zero", physics=())
+    if walls:
+        case = case.replace(dz=25.0, dx=40.0, dy=45.0)
+    sim = les_mod.Simulation(case)
+    ref = Oracle(case)
+    x = inputs.uniform(5, 0, case.n, -1, 1).reshape(case.shape)
+    y = sim.apply_poisson(torch.from_numpy(x).cuda(), op).cpu().numpy()
+    yr = ref.apply_poisson(x, op)
+    assert rel(y, yr) < 1e-14
+
+
+@pytest.mark.parametrize("walls", [False, True])
+@pytest.mark.parametrize("solver", ["cg", "jacobi"])
+def test_poisson_solve(les_mod, walls, solver):
+    from oracle import Oracle
+    case = inputs.Case(name="ps", nx=12, ny=10, nz=9, dx=0.3, dy=0.25, dz=0.1, walls=walls,
+                       precision=64, init="zero", physics=(), solver=solver)
+    sim = les_mod.Simulation(case)
+    ref = Oracle(case)
+    b = inputs.uniform(7, 0, case.n, -1, 1).reshape(case.shape) + 0.3
+    tol = 1e-12 if solver == "cg" else 1e-8
+    maxit = 5000 if solver == "cg" else 200000
+    xr, st, itr, resr = ref.poisson(b, solver=solver, tol=tol, maxit=maxit)
+    bt = torch.from_numpy(b).cuda()
+    xt = torch.zeros_like(bt)
+    rc, it, res = sim.poisson_solve(bt, xt, tol, maxit)
+    x = xt.cpu().numpy()
+    assert res <= tol and st == 0
+    assert abs(x.mean()) < 1e-13
+    assert rel(x, xr) < (1e-9 if solver == "cg" else 1e-5)
+    if solver == "cg":
+        assert abs(it - itr) <= 2
+    else:
+        assert it == itr
+
+
+def test_poisson_not_converged_and_zero_rhs(les_mod):
+    case = inputs.Case(name="ps", nx=16, ny=16, nz=16, dx=1.0, dy=1.0, dz=1.0, precision=64,
+                       init="zero", physics=())
+    sim = les_mod.Simulation(case)
+    b = torch.from_numpy(inputs.uniform(2, 0, case.n, -1, 1).reshape(case.shape)).cuda()
+    x = torch.zeros_like(b)
+    rc, it, res = sim.poisson_solve(b, x, 1e-12, 3, allow_not_converged=True)
+    assert rc == les_mod.LES_ERR_NOT_CONVERGED and it == 3 and res > 1e-12
+    x = torch.ones_like(b)
+    rc, it, res = sim.poisson_solve(torch.zeros_like(b), x, 1e-10, 100)
+    assert rc == 0 and it == 0 and float(x.abs().max()) == 0.0
+
+
+def test_poisson_fp32(les_mod):
+    from oracle import Oracle
+    case = inputs.Case(name="ps", nx=40, ny=36, nz=20, dx=35.0, dy=35.0, dz=10.0, walls=True,
+                       precision=32, init="zero", physics=())
+    sim = les_mod.Simulation(case)
+    ref = Oracle(case.replace(precision=64))
+    b = inputs.uniform(9, 0, case.n, -1, 1).reshape(case.shape)
+    xr, *_ = ref.poisson(b, tol=1e-12)
+    bt = torch.from_numpy(b.astype(np.float32)).cuda()
+    xt = torch.zeros_like(bt)
+    rc, it, res = sim.poisson_solve(bt, xt, 1e-6, 5000)
+    assert rc == 0 and res <= 1e-6
+    # recursive-residual CG in FP32 with FP64 dots: the error is the solver
+    # tolerance amplified by the condition number, plus float rounding
+    assert rel(xt.cpu().numpy(), xr) < 5e-4
+
+
+# --------------------------------------------------------------------------
+# stage-by-stage parity, FP64, all physics, ragged sizes
+
+
+def _moist_case(nx=37, ny=11, nz=12, **kw):
+    c = inputs.cbl(nx, ny, nz, dz=70.0, precision=64, tol=1e-13, maxit=5000, sat_tol=1e-10)
+    return c.replace(**kw)
+
+
+@pytest.mark.parametrize("walls", [True, False])
+def test_stages_fp64(les_mod, walls):
+    case = _moist_case()
+    if not walls:
+        case = case.replace(walls=False, physics=("adv", "sgs", "fb", "moist", "buoy", "coriolis"))
+    st = inputs.initial_state(case)
+    pert = random_state(case, seed=8)
+    for k in ("u", "v", "w"):
+        st[k] = st[k] + pert[k]
+    st["p"] = pert["p"]
+    sim, ref, _ = pair(les_mod, case, st)
+    sim.stage("begin")
+    ref.begin_step()
+    assert abs(sim.dt - ref.dt) == 0.0
+    for f in ("T", "q_l", "b", "s_rad"):
+        a, b = sim.get(f), ref.get(f)
+        scale = max(np.abs(b).max(), 1e-30)
+        assert np.max(np.abs(a - b)) <= 1e-12 * scale + 1e-300, f
+    assert ref.get("q_l").max() > 0     # the cloud exists
+    for k in range(case.K):
+        sim.stage("scalar")
+        ref.scalar_stage()
+        for f in ("theta_l", "q_t"):
+            assert rel(sim.get(f), ref.get(f)) < 1e-13, (k, f)
+        sim.stage("momentum")
+        ref.momentum_stage()
+        for f in ("u_hat", "v_hat", "w_hat"):
+            assert rel(sim.get(f), ref.get(f)) < 1e-12, (k, f)
+        assert rel(sim.get("rhs"), ref.get("rhs")) < 1e-10, k
+        sim.stage("solve")
+        ref.solve_stage()
+        assert rel(sim.get("psi"), ref.get("psi")) < 1e-9, k
+        sim.stage("correct")
+        ref.correct_stage()
+        for f in ("u", "v", "w"):
+            assert rel(sim.get(f), ref.get(f)) < 1e-9, (k, f)
+        assert rel(demean(sim.get("p")), demean(ref.get("p"))) < 1e-9, k
+    sim.stage("end")
+    ref.end_step()
+
+
+def test_stage_order_is_enforced(les_mod):
+    case = inputs.tgv(8)
+    sim = les_mod.Simulation(case)
+    sim.set_state(inputs.initial_state(case))
+    with pytest.raises(les_mod.LesError) as e:
+        sim.stage("scalar")
+    assert e.value.status == les_mod.LES_ERR_STATE
+
+
+def test_fluid_at_rest_needs_dt(les_mod):
+    case = inputs.tgv(8, init="zero")
+    sim = les_mod.Simulation(case)
+    with pytest.raises(les_mod.LesError) as e:
+        sim.step(1)
+    assert e.value.status == les_mod.LES_ERR_INVALID_ARG
+
+
+# --------------------------------------------------------------------------
+# whole steps
+
+
+def test_tgv32_fp64_100_steps(les_mod):
+    """Config: 32^3 triply periodic Taylor-Green + seeded noise, FP64, Smagorinsky
+    0.17, dt from CFL 0.3, K = 3, CG to 1e-10 -- 100 steps, 1e-5 relative L2."""
+    case = inputs.tgv(32)
+    sim, ref, _ = pair(les_mod, case)
+    stats = sim.step(100)
+    ref.step(100)
+    assert stats["steps"] == 100 and stats["not_converged"] == 0
+    assert sim.dt == ref.dt
+    for f in ("u", "v", "w", "theta_l"):
+        assert rel(sim.get(f), ref.get(f)) < 1e-5, f
+    assert rel(demean(sim.get("p")), demean(ref.get("p"))) < 1e-5
+    d, dr = sim.diagnostics(), ref.diagnostics()
+    assert abs(d["kinetic_energy"] - dr["kinetic_energy"]) < 1e-8 * dr["kinetic_energy"]
+
+
+def test_moist_walls_fp64_steps(les_mod):
+    case = _moist_case(nx=24, ny=20, nz=16, dt=1.0)
+    sim, ref, _ = pair(les_mod, case)
+    sim.step(3)
+    ref.step(3)
+    for f in ("u", "v", "w", "theta_l", "q_t"):
+        assert rel(sim.get(f), ref.get(f)) < 1e-9, f
+    assert rel(demean(sim.get("p")), demean(ref.get("p"))) < 1e-8
+
+
+def test_conservation_gpu_fp64(les_mod):
+    case = _moist_case(nx=20, ny=18, nz=12, physics=("adv", "sgs", "fb", "moist", "buoy", "coriolis"),
+                       dt=1.0)
+    sim, ref, _ = pair(les_mod, case)
+    d0 = sim.diagnostics()
+    sim.step(5)
+    d1 = sim.diagnostics()
+    assert abs(d1["sum_rho_theta"] - d0["sum_rho_theta"]) <= 1e-13 * d0["sum_rho_theta"]
+    assert abs(d1["sum_rho_qt"] - d0["sum_rho_qt"]) <= 1e-13 * d0["sum_rho_qt"]
+
+
+def test_cbl_fp32_against_fp64_oracle(les_mod):
+    """FP32 stencils and sweeps (FP64 reductions) against the FP64 oracle over a
+    short horizon; errors stated per field."""
+    case = inputs.cbl(40, 36, 96, precision=32, dt=0.5)
+    sim, ref, _ = pair(les_mod, case)
+    sim.step(5)
+    ref.step(5)
+    errs = {f: rel(sim.get(f), ref.get(f)) for f in ("u", "v", "w", "theta_l", "q_t")}
+    errs["p"] = rel(demean(sim.get("p")), demean(ref.get("p")))
+    print("fp32 vs fp64 relative L2 after 5 steps:", errs)
+    assert errs["theta_l"] < 1e-6 and errs["q_t"] < 1e-5
+    assert errs["u"] < 1e-5 and errs["v"] < 1e-5
+    assert errs["w"] < 5e-2 and errs["p"] < 5e-2
+
+
+def test_deterministic(les_mod):
+    case = _moist_case(nx=20, ny=12, nz=10, dt=1.0, precision=32, tol=1e-6, sat_tol=1e-4)
+    outs = []
+    for _ in range(2):
+        sim = les_mod.Simulation(case)
+        sim.set_state(inputs.initial_state(case))
+        sim.step(2)
+        outs.append({f: sim.get(f) for f in ("u", "w", "theta_l", "p")})
+        sim.close()
+    for f in outs[0]:
+        assert np.array_equal(outs[0][f], outs[1][f]), f
+
+
+def test_nonfinite_is_reported(les_mod):
+    case = inputs.tgv(8)
+    st = inputs.initial_state(case)
+    st["theta_l"] = st["theta_l"].copy()
+    st["theta_l"][3, 2, 1] = np.nan
+    sim = les_mod.Simulation(case)
+    sim.set_state(st)
+    d = sim.diagnostics()
+    assert d["nonfinite"] == 1.0
+
+
+@pytest.mark.parametrize("shape", [(3, 3, 2), (33, 9, 17), (64, 8, 3)])
+def test_ragged_and_minimum_grids(les_mod, shape):
+    nx, ny, nz = shape
+    case = inputs.tgv(16, nxyz=shape, steps_tol=1e-12).replace(dx=1 / nx, dy=1 / ny, dz=1 / max(nz, 2))
+    sim, ref, _ = pair(les_mod, case)
+    sim.step(2)
+    ref.step(2)
+    for f in ("u", "v", "w"):
+        assert rel(sim.get(f), ref.get(f)) < 1e-9, f
