@@ -214,6 +214,37 @@ int les_apply_poisson(les_handle *h, int32_t op, const void *d_x, void *d_y);
  * LES_NDIAG doubles.  Synchronises the stream. */
 int les_diagnostics(les_handle *h, double *out);
 
+/* ---- allocation-free Poisson solve --------------------------------------------
+ * For callers that cannot allocate device memory, and so cannot provide the
+ * workspace a handle needs: a plug-in whose host application owns all device
+ * memory through its own pool allocator, or a latency-bound loop that must not
+ * call cudaMalloc / cudaFree because they can synchronise the whole device.
+ * The paper has no counterpart; the solve is the same as les_poisson_solve()
+ * (same operator, boundary conditions, solver, mean removal and stop test),
+ * configured by *cfg alone (no handle).
+ *
+ * Scratch: one file-scope __device__ array of 16 MiB + 256.25 KiB inside
+ * libles.so, held by every GPU that loads the library until the process
+ * exits.  Limit: nx*ny*nz <= 524288 cells at precision 64, <= 1048576 at
+ * precision 32 (four work vectors of 16 MiB in total); larger grids are
+ * rejected with LES_ERR_INVALID_ARG and a message in err.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  Every call on a device shares the one array,
+ * which keeps the previous call's contents (the call clears the control
+ * block it needs zeroed): calls that overlap on the GPU race, so issue them
+ * on one stream or serialise them.
+ * d_rho0: device array of nz reference densities in the field precision,
+ * needed only for LES_OP_WIDE (may be NULL otherwise).  d_rhs, d_x: device
+ * arrays of nx*ny*nz values, x holds the initial guess on entry.  stream: a
+ * cudaStream_t or NULL.  err: optional host buffer of err_len bytes for a
+ * message.  Synchronises the stream.  Returns LES_OK, LES_ERR_NOT_CONVERGED,
+ * LES_ERR_INVALID_ARG or LES_ERR_CUDA. */
+int les_poisson_solve_static(const les_config *cfg, const void *d_rho0, const void *d_rhs, void *d_x,
+                             double rtol, int32_t maxit, void *stream, int32_t *iters,
+                             double *rel_res, char *err, size_t err_len);
+
 /* ---- launch accounting and event profiling -------------------------------- */
 #define LES_MAX_KERNELS 32
 typedef struct les_kernel_stat {

@@ -39,7 +39,7 @@ EXPORTED = ("les_config_default", "les_workspace_bytes", "les_init", "les_destro
             "les_set_state", "les_get_state", "les_field_offset", "les_step", "les_stage",
             "les_poisson_solve", "les_apply_poisson", "les_diagnostics", "les_get_dt", "les_set_dt",
             "les_last_error", "les_status_string", "les_profile_enable", "les_profile_read",
-            "les_profile_reset", "les_launch_count")
+            "les_profile_reset", "les_launch_count", "les_poisson_solve_static")
 
 
 class LesConfig(C.Structure):
@@ -139,6 +139,9 @@ def load_library(path: str = LIB_PATH):
     lib.les_profile_reset.argtypes = [vp]
     lib.les_launch_count.restype = C.c_int64
     lib.les_launch_count.argtypes = [vp]
+    lib.les_poisson_solve_static.restype = C.c_int
+    lib.les_poisson_solve_static.argtypes = [cfgp, vp, vp, vp, dbl, i32, vp, C.POINTER(i32), C.POINTER(dbl),
+                                             C.c_char_p, sz]
     _lib = lib
     return lib
 
