@@ -133,7 +133,11 @@ typedef struct les_config {
   double   theta0, p00;      /* reference potential temperature, pressure   */
   double   sat_tol;          /* secant stop |theta_l* - theta_l| (K)        */
   int32_t  sat_maxit;
-  int32_t  reserved0;
+  int32_t  solver_path;      /* 0: one persistent cooperative launch per CG
+                                solve when eligible (compact operator, nx a
+                                multiple of 128 floats / 64 doubles, ny a
+                                multiple of the tile rows), else 1;
+                                1: one launch per CG phase               */
   double   reserved[4];
 } les_config;
 
@@ -244,6 +248,28 @@ int les_diagnostics(les_handle *h, double *out);
 int les_poisson_solve_static(const les_config *cfg, const void *d_rho0, const void *d_rhs, void *d_x,
                              double rtol, int32_t maxit, void *stream, int32_t *iters,
                              double *rel_res, char *err, size_t err_len);
+
+/* ---- tuning of the persistent CG solve ---------------------------------------
+ * The CG solve runs as one persistent cooperative launch when solver_path = 0
+ * and the grid is eligible.  A thread block of 32 x cg_tile_rows threads owns
+ * a tile of (32 * 16 B of cells) x cg_tile_rows x cg_tile_planes nodes; the
+ * grid is capped by occupancy and cg_max_blocks.  Each grid-barrier wait ends
+ * after barrier_timeout_ms; the solve then returns LES_ERR_TIMEOUT and the
+ * device stays usable.  fault_missing_arrivals is a failure-detection test
+ * hook: the barrier then waits for that many blocks that never arrive, so
+ * every wait runs out; it must be 0 otherwise.  A zero field in a set call
+ * keeps the current value (except fault_missing_arrivals). */
+typedef struct les_tuning {
+  uint32_t struct_size;            /* sizeof(les_tuning)                   */
+  int32_t  cg_tile_rows;           /* 1, 2, 4 or 8                          */
+  int32_t  cg_tile_planes;         /* >= 1                                  */
+  int32_t  cg_max_blocks;          /* >= 1                                  */
+  double   barrier_timeout_ms;     /* > 0                                   */
+  int32_t  fault_missing_arrivals; /* 0 in production                      */
+  int32_t  reserved0;
+} les_tuning;
+int les_get_tuning(les_handle *h, les_tuning *out);
+int les_set_tuning(les_handle *h, const les_tuning *in);
 
 /* ---- launch accounting and event profiling -------------------------------- */
 #define LES_MAX_KERNELS 32

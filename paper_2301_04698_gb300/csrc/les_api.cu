@@ -37,7 +37,7 @@ struct Layout {
   size_t field_bytes = 0;
   size_t off_fixed[B_NFIXED] = {};
   std::vector<size_t> off_prev;
-  size_t off_prof = 0, off_ctl = 0, off_partials = 0, off_diag = 0;
+  size_t off_prof = 0, off_ctl = 0, off_partials = 0, off_diag = 0, off_bar = 0;
   size_t total = 0;
   int max_blocks = 0;
 };
@@ -65,6 +65,7 @@ int validate(const les_config* c, std::string* why) {
   if (!(c->dt >= 0)) return bad("dt must be >= 0");
   if (c->dt == 0 && !(c->cfl > 0)) return bad("dt = 0 needs cfl > 0");
   if (c->sat_maxit < 0 || c->sat_maxit > 1000) return bad("sat_maxit out of range");
+  if (c->solver_path != 0 && c->solver_path != 1) return bad("solver_path must be 0 or 1");
   return LES_OK;
 }
 
@@ -93,6 +94,8 @@ Layout make_layout(const les_config& c, int nsm) {
   off += align_up((size_t)16 * L.max_blocks * sizeof(double));
   L.off_diag = off;
   off += align_up(LES_NDIAG * sizeof(double));
+  L.off_bar = off;
+  off += align_up(sizeof(FusedBar));
   L.total = off;
   return L;
 }
@@ -120,6 +123,8 @@ struct les_handle {
   SolverCtl ctl_host{};
   double* partials = nullptr;
   double* diag = nullptr;
+  FusedBar* bar = nullptr;
+  FusedCfg fused;
   int cur = 0;           // scalar ping-pong: 0 -> A holds phi^k, 1 -> B
   int next_stage = LES_STAGE_BEGIN;
   int sub = 0;
@@ -228,6 +233,8 @@ SolverArgs<T> solver_args(les_handle* h) {
   s.p1 = (T*)h->fixed[B_PB];
   s.q = (T*)h->fixed[B_Q];
   s.prof = &h->prof;
+  s.bar = h->bar;
+  s.fused = h->cfg.solver_path == 0 ? &h->fused : nullptr;
   return s;
 }
 
@@ -252,6 +259,7 @@ int fields_per_cell(const les_config& c, int id) {
     case KI_CG_UPDATE: return 6;
     case KI_JACOBI: return 3;
     case KI_FINISH: return 2;
+    case KI_CG_FUSED: return 0;  // varies with the iteration count
     default: return 0;
   }
 }
@@ -425,7 +433,7 @@ namespace les {
 
 const char* const kKernelNames[KI_COUNT] = {
     "thermo", "radiation", "nu", "nu_half", "scalar", "momentum", "rhs", "correct", "diag",
-    "cfl", "apply", "sum", "cg_init", "cg_matvec", "cg_update", "jacobi", "finish", "ctl"};
+    "cfl", "apply", "sum", "cg_init", "cg_matvec", "cg_update", "jacobi", "finish", "ctl", "cg_fused"};
 
 template <typename T>
 Grid<T> make_grid(const les_config& c, int zc) {
@@ -542,6 +550,17 @@ int les_init(const les_config* cfg, const double* rho0_z, void* workspace, size_
   h->ctl = (SolverCtl*)(h->ws + L.off_ctl);
   h->partials = (double*)(h->ws + L.off_partials);
   h->diag = (double*)(h->ws + L.off_diag);
+  h->bar = (FusedBar*)(h->ws + L.off_bar);
+  // tile shape of the persistent solver: short z runs on mid-size grids (more
+  // tiles than SM slots), longer runs once the grid is large
+  {
+    const double cells = (double)cfg->nx * cfg->ny * cfg->nz;
+    h->fused.ty = (cfg->ny % 8 == 0 && cells > 2.0e7) ? 8 : 4;
+    h->fused.zc = cells > 2.0e7 ? 16 : 4;
+    int dev = 0, khz = 2000000;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    h->fused.spin_cycles = (long long)(h->fused.timeout_ms * (double)khz);
+  }
   h->dt = cfg->dt;
   // reference profiles, in the field precision
   std::vector<double> rho0, p0;
@@ -680,6 +699,40 @@ int les_diagnostics(les_handle* h, double* out) {
   return out[8] > 0 ? LES_ERR_NONFINITE : LES_OK;
 }
 
+int les_get_tuning(les_handle* h, les_tuning* out) {
+  if (!h || !out) return LES_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->struct_size = sizeof(les_tuning);
+  out->cg_tile_rows = h->fused.ty;
+  out->cg_tile_planes = h->fused.zc;
+  out->cg_max_blocks = h->fused.max_blocks;
+  out->barrier_timeout_ms = h->fused.timeout_ms;
+  out->fault_missing_arrivals = h->fused.missing;
+  return LES_OK;
+}
+
+int les_set_tuning(les_handle* h, const les_tuning* in) {
+  if (!h || !in) return LES_ERR_INVALID_ARG;
+  if (in->struct_size != sizeof(les_tuning)) return h->fail(LES_ERR_INVALID_ARG, "les_tuning.struct_size mismatch");
+  const int ty = in->cg_tile_rows;
+  if (ty != 0 && ty != 1 && ty != 2 && ty != 4 && ty != 8)
+    return h->fail(LES_ERR_INVALID_ARG, "cg_tile_rows must be 1, 2, 4 or 8");
+  if (in->cg_tile_planes < 0 || in->cg_max_blocks < 0 || in->barrier_timeout_ms < 0 ||
+      in->fault_missing_arrivals < 0)
+    return h->fail(LES_ERR_INVALID_ARG, "negative tuning value");
+  if (ty) h->fused.ty = ty;
+  if (in->cg_tile_planes) h->fused.zc = in->cg_tile_planes;
+  if (in->cg_max_blocks) h->fused.max_blocks = in->cg_max_blocks;
+  if (in->barrier_timeout_ms > 0) {
+    int dev = 0, khz = 2000000;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    h->fused.timeout_ms = in->barrier_timeout_ms;
+    h->fused.spin_cycles = (long long)(in->barrier_timeout_ms * (double)khz);
+  }
+  h->fused.missing = in->fault_missing_arrivals;
+  return LES_OK;
+}
+
 int les_profile_enable(les_handle* h, int32_t enable) {
   if (!h) return LES_ERR_INVALID_ARG;
   h->prof.collect();
@@ -701,7 +754,8 @@ int les_profile_read(les_handle* h, les_kernel_stat* out, int32_t max_entries, i
     k.launches = h->prof.launches[id];
     k.timed = h->prof.timed[id];
     k.total_ms = h->prof.ms[id];
-    k.bytes_per_launch = (double)k.fields_per_cell * (double)h->n * (double)h->es;
+    k.bytes_per_launch = h->prof.bytes[id] > 0 ? h->prof.bytes[id] / (double)k.launches
+                                               : (double)k.fields_per_cell * (double)h->n * (double)h->es;
   }
   *count = c;
   return LES_OK;

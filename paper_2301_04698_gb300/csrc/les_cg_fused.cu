@@ -1,0 +1,484 @@
+// les_cg_fused.cu -- the whole conjugate-gradient Poisson solve in one
+// persistent cooperative launch (Sec. 2.4: L_c psi = b, compact 7-point
+// Laplacian, periodic in x, y, mirror or periodic in z; mean of b removed,
+// psi returned with zero mean).
+//
+// Why: on a mid-size grid every CG iteration is two short memory-bound passes
+// separated by global reductions; as separate launches with host polling, the
+// launch gaps and 4-byte-per-thread loads left the passes at a small fraction
+// of memory bandwidth.  Here the grid stays resident for the whole solve:
+//   phase A  p = r + beta p_old evaluated on the fly, q = L_c p, p.q
+//            -- 2.5-D march: a 32 x TY thread block owns a (32 VW) x TY x zc
+//            tile, keeps plane k in shared memory (with x / y halos) and
+//            planes k-1, k+1 in registers, prefetching plane k+1 while
+//            computing plane k; each thread handles VW = 16 B of cells;
+//   phase B  x += alpha p, r -= alpha q, r.r -- 16-byte vector streaming;
+// each followed by a grid-wide FP64 sum: every block posts its partial, the
+// last block to arrive folds the partials in block order (deterministic) and
+// publishes the total with the barrier generation.  All blocks then compute
+// the same alpha, beta and stop decision.  Data written by other blocks is
+// read with ld.global.cg (L2), never through the non-coherent L1 path.
+// Every barrier wait is bounded in time; on expiry the kernel records a
+// timeout in the control block and returns.
+#include <algorithm>
+#include <string>
+
+#include "les_internal.h"
+
+namespace les {
+namespace {
+
+template <typename T>
+struct VT {
+  static constexpr int VW = 16 / sizeof(T);  // cells per 16-byte vector
+  static constexpr int W = 32 * VW;          // tile width in x
+};
+
+__device__ __forceinline__ void ldv(float (&o)[4], const float* p) {
+  const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ldv(double (&o)[2], const double* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  o[0] = v.x; o[1] = v.y;
+}
+__device__ __forceinline__ void stv(float* p, const float (&o)[4]) {
+  __stcg(reinterpret_cast<float4*>(p), make_float4(o[0], o[1], o[2], o[3]));
+}
+__device__ __forceinline__ void stv(double* p, const double (&o)[2]) {
+  __stcg(reinterpret_cast<double2*>(p), make_double2(o[0], o[1]));
+}
+// FP64 sum of VW products; float products are formed in FP32 and the 16-byte
+// group is added to the FP64 accumulator (the global reduction is FP64).
+__device__ __forceinline__ double vdot(const float (&a)[4], const float (&b)[4]) {
+  return (double)(a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3]);
+}
+__device__ __forceinline__ double vdot(const double (&a)[2], const double (&b)[2]) {
+  return a[0] * b[0] + a[1] * b[1];
+}
+
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
+  return *reinterpret_cast<const volatile unsigned*>(p);
+}
+
+template <typename T>
+struct FusedArgs {
+  int nx, ny, nz, walls;
+  T cx, cy, cz;  // 1/dx^2, 1/dy^2, 1/dz^2
+  int zc, ntx, nty, ntz;
+  long long ntiles;
+  long long n, nv;
+  const T* b;
+  T* x;
+  T* r;
+  T* p0;
+  T* p1;
+  T* q;
+  double* partials;  // [4][gridDim.x]
+  FusedBar* bar;
+  SolverCtl* ctl;
+  double tol;
+  int maxit;
+  long long spin_cycles;
+  unsigned expected;  // arrivals per barrier: gridDim.x (+ the test hook's missing ones)
+};
+
+__device__ __forceinline__ int zmap(int k, int nz, int walls) {
+  if (walls) return k < 0 ? -1 - k : (k >= nz ? 2 * nz - 1 - k : k);
+  return k < 0 ? k + nz : (k >= nz ? k - nz : k);
+}
+
+// Grid-wide FP64 sum of NV values (block partials in thread 0 after the block
+// reduce).  Returns false (in every thread) if the barrier wait timed out.
+template <int NV>
+__device__ bool grid_sum(double (&v)[NV], FusedBar* bar, double* partials, long long spin_cycles,
+                         unsigned expected) {
+  __shared__ double sh[32];
+  __shared__ unsigned s_last, s_gen;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  const unsigned G = gridDim.x;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    const double bv = block_reduce<false>(v[q], sh);
+    if (tid == 0) partials[(size_t)q * G + blockIdx.x] = bv;
+  }
+  if (tid == 0) {
+    s_gen = ld_volatile(&bar->gen);
+    __threadfence();
+    const unsigned a = atomicAdd(&bar->count, 1u);
+    s_last = (a == expected - 1);
+    s_fail = 0;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double acc = 0.0;
+      for (unsigned b = tid; b < G; b += nthr) acc += __ldcg(partials + (size_t)q * G + b);
+      const double tot = block_reduce<false>(acc, sh);
+      if (tid == 0) bar->value[q] = tot;
+    }
+    if (tid == 0) {
+      bar->count = 0;
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    }
+  } else if (tid == 0) {
+    const long long t0 = clock64();
+    while (ld_volatile(&bar->gen) == s_gen) {
+      if (ld_volatile(reinterpret_cast<const unsigned*>(&bar->fail)) != 0u || clock64() - t0 > spin_cycles) {
+        atomicExch(&bar->fail, 1);
+        s_fail = 1;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  if (s_fail) return false;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = __ldcg(&bar->value[q]);
+  return true;
+}
+
+// One 2.5-D sweep of the compact Laplacian over this block's tiles.
+// loadP(o, m): the VW operand values at linear index m; emit(m, P, q).
+template <typename T, typename LoadP, typename LoadP1, typename Emit>
+__device__ __forceinline__ void stencil_sweep(const FusedArgs<T>& f, T* sm, const LoadP& loadP,
+                                              const LoadP1& loadP1, const Emit& emit) {
+  constexpr int VW = VT<T>::VW, W = VT<T>::W;
+  const int tx = threadIdx.x, ty = threadIdx.y, TY = blockDim.y;
+  const int SW = W + 2;
+  for (long long t = blockIdx.x; t < f.ntiles; t += gridDim.x) {
+    const int ti = (int)(t % f.ntx);
+    const long long rr = t / f.ntx;
+    const int tj = (int)(rr % f.nty);
+    const int tk = (int)(rr / f.nty);
+    const int x0 = ti * W, y0 = tj * TY, k0 = tk * f.zc, k1 = min(k0 + f.zc, f.nz);
+    const int xs = x0 + tx * VW, y = y0 + ty;
+    const int yd = y0 == 0 ? f.ny - 1 : y0 - 1;
+    const int yu = y0 + TY == f.ny ? 0 : y0 + TY;
+    const int xl = x0 == 0 ? f.nx - 1 : x0 - 1;
+    const int xr = x0 + W == f.nx ? 0 : x0 + W;
+    auto lin = [&](int xx, int yy, int kk) -> size_t { return ((size_t)kk * f.ny + yy) * f.nx + xx; };
+    T Pm[VW], Pc[VW], Pp[VW], Pn[VW], hd[VW], hu[VW];
+    T hl = T(0), hr = T(0);
+    loadP(Pm, lin(xs, y, zmap(k0 - 1, f.nz, f.walls)));
+    loadP(Pc, lin(xs, y, k0));
+    loadP(Pp, lin(xs, y, zmap(k0 + 1, f.nz, f.walls)));
+    if (ty == 0) loadP(hd, lin(xs, yd, k0));
+    if (ty == TY - 1) loadP(hu, lin(xs, yu, k0));
+    if (tx == 0) hl = loadP1(lin(xl, y, k0));
+    if (tx == 31) hr = loadP1(lin(xr, y, k0));
+    T* row = sm + (1 + ty) * SW + 1 + tx * VW;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      row[e] = Pc[e];
+      if (ty == 0) row[e - SW] = hd[e];
+      if (ty == TY - 1) row[e + SW] = hu[e];
+    }
+    if (tx == 0) row[-1] = hl;
+    if (tx == 31) row[VW] = hr;
+    __syncthreads();
+    for (int k = k0; k < k1; ++k) {
+      const bool more = k + 1 < k1;
+      if (more) {
+        // prefetch plane k+2 (window) and the halos of plane k+1
+        loadP(Pn, lin(xs, y, zmap(k + 2, f.nz, f.walls)));
+        if (ty == 0) loadP(hd, lin(xs, yd, k + 1));
+        if (ty == TY - 1) loadP(hu, lin(xs, yu, k + 1));
+        if (tx == 0) hl = loadP1(lin(xl, y, k + 1));
+        if (tx == 31) hr = loadP1(lin(xr, y, k + 1));
+      }
+      T qv[VW];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        const T c = Pc[e];
+        qv[e] = (row[e - 1] + row[e + 1] - T(2) * c) * f.cx + (row[e - SW] + row[e + SW] - T(2) * c) * f.cy +
+                (Pm[e] + Pp[e] - T(2) * c) * f.cz;
+      }
+      emit(lin(xs, y, k), Pc, qv);
+      __syncthreads();
+      if (more) {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          Pm[e] = Pc[e];
+          Pc[e] = Pp[e];
+          Pp[e] = Pn[e];
+          row[e] = Pc[e];
+          if (ty == 0) row[e - SW] = hd[e];
+          if (ty == TY - 1) row[e + SW] = hu[e];
+        }
+        if (tx == 0) row[-1] = hl;
+        if (tx == 31) row[VW] = hr;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_fused(FusedArgs<T> f) {
+  constexpr int VW = VT<T>::VW;
+  extern __shared__ unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const long long gstride = (long long)gridDim.x * blockDim.x * blockDim.y;
+  const long long gtid = (long long)blockIdx.x * blockDim.x * blockDim.y + tid;
+  int status = 0;  // 0 running, 1 converged, 2 maxit, 3 breakdown, 4 zero rhs, 5 timeout
+
+  // mean of b
+  double s1[1] = {0.0};
+  for (long long v = gtid; v < f.nv; v += gstride) {
+    T bv[VW];
+    ldv(bv, f.b + v * VW);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) s1[0] += (double)bv[e];
+  }
+  if (!grid_sum<1>(s1, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+  const T mean = (T)(s1[0] / (double)f.n);
+
+  // r = (b - mean) - L_c x0;  r.r and |b - mean|^2
+  double s2[2] = {0.0, 0.0};
+  if (!status) {
+    auto loadX = [&](T (&o)[VW], size_t m) { ldv(o, f.x + m); };
+    auto loadX1 = [&](size_t m) { return __ldcg(f.x + m); };
+    auto emitR = [&](size_t m, const T (&P)[VW], const T (&qv)[VW]) {
+      T bv[VW], rv[VW];
+      ldv(bv, f.b + m);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        bv[e] -= mean;
+        rv[e] = bv[e] - qv[e];
+      }
+      stv(f.r + m, rv);
+      s2[0] += vdot(rv, rv);
+      s2[1] += vdot(bv, bv);
+    };
+    stencil_sweep(f, sm, loadX, loadX1, emitR);
+    if (!grid_sum<2>(s2, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+  }
+  double rr = s2[0];
+  const double bb = s2[1];
+  double rel = 0.0;
+  if (!status) {
+    if (bb == 0.0) status = 4;
+    else {
+      rel = sqrt(rr / bb);
+      if (rel <= f.tol) status = 1;
+      else if (f.maxit <= 0) status = 2;
+    }
+  }
+
+  int iter = 0;
+  double beta = 0.0;
+  bool first = true;
+  T* pold = f.p0;
+  T* pnew = f.p1;
+  while (!status) {
+    // phase A: p = r + beta p_old, q = L_c p, p.q
+    double sa[1] = {0.0};
+    const T tb = (T)beta;
+    const T* r = f.r;
+    const T* po = pold;
+    T* pn = pnew;
+    auto loadP = [&](T (&o)[VW], size_t m) {
+      ldv(o, r + m);
+      if (!first) {
+        T pv[VW];
+        ldv(pv, po + m);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) o[e] += tb * pv[e];
+      }
+    };
+    auto loadP1 = [&](size_t m) { return first ? __ldcg(r + m) : __ldcg(r + m) + tb * __ldcg(po + m); };
+    auto emitQ = [&](size_t m, const T (&P)[VW], const T (&qv)[VW]) {
+      stv(pn + m, P);
+      stv(f.q + m, qv);
+      sa[0] += vdot(P, qv);
+    };
+    stencil_sweep(f, sm, loadP, loadP1, emitQ);
+    if (!grid_sum<1>(sa, f.bar, f.partials, f.spin_cycles, f.expected)) {
+      status = 5;
+      break;
+    }
+    const double pq = sa[0];
+    if (pq == 0.0 || !isfinite(pq)) {
+      status = 3;
+      break;
+    }
+    const double alpha = rr / pq;
+    const T ta = (T)alpha;
+    // phase B: x += alpha p, r -= alpha q, r.r
+    double sb[1] = {0.0};
+    for (long long v = gtid; v < f.nv; v += gstride) {
+      const size_t m = (size_t)v * VW;
+      T xv[VW], pv[VW], rv[VW], qv[VW];
+      ldv(xv, f.x + m);
+      ldv(pv, pn + m);
+      ldv(rv, f.r + m);
+      ldv(qv, f.q + m);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        xv[e] += ta * pv[e];
+        rv[e] -= ta * qv[e];
+      }
+      stv(f.x + m, xv);
+      stv(f.r + m, rv);
+      sb[0] += vdot(rv, rv);
+    }
+    if (!grid_sum<1>(sb, f.bar, f.partials, f.spin_cycles, f.expected)) {
+      status = 5;
+      break;
+    }
+    const double rr_new = sb[0];
+    iter += 1;
+    rel = sqrt(rr_new / bb);
+    beta = rr_new / rr;
+    rr = rr_new;
+    first = false;
+    T* tmp = pold;
+    pold = pnew;
+    pnew = tmp;
+    if (rel <= f.tol) status = 1;
+    else if (iter >= f.maxit) status = 2;
+    else if (!isfinite(rr_new)) status = 3;
+  }
+
+  // zero-mean gauge (or zero for a zero right side)
+  if (status != 5) {
+    double sx[1] = {0.0};
+    for (long long v = gtid; v < f.nv; v += gstride) {
+      T xv[VW];
+      ldv(xv, f.x + v * VW);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) sx[0] += (double)xv[e];
+    }
+    if (!grid_sum<1>(sx, f.bar, f.partials, f.spin_cycles, f.expected)) {
+      status = 5;
+    } else {
+      const T mx = (T)(sx[0] / (double)f.n);
+      for (long long v = gtid; v < f.nv; v += gstride) {
+        T xv[VW];
+        ldv(xv, f.x + v * VW);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) xv[e] = status == 4 ? T(0) : xv[e] - mx;
+        stv(f.x + v * VW, xv);
+      }
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    f.ctl->iter = iter;
+    f.ctl->rel = rel;
+    f.ctl->done = status;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+bool fused_cg_eligible(const Grid<T>& g, int op, int solver, int ty) {
+  constexpr int W = VT<T>::W;
+  return op == LES_OP_COMPACT && solver == LES_SOLVER_CG && g.nx % W == 0 && ty > 0 && g.ny % ty == 0 &&
+         g.nz >= 2;
+}
+
+template <typename T>
+int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
+                        int* iters, double* rel, std::string* err) {
+  constexpr int W = VT<T>::W;
+  FusedArgs<T> f;
+  f.nx = a.g.nx;
+  f.ny = a.g.ny;
+  f.nz = a.g.nz;
+  f.walls = a.g.walls;
+  f.cx = a.g.idx * a.g.idx;
+  f.cy = a.g.idy * a.g.idy;
+  f.cz = a.g.idz * a.g.idz;
+  f.zc = std::max(1, std::min(fc.zc, f.nz));
+  f.ntx = f.nx / W;
+  f.nty = f.ny / fc.ty;
+  f.ntz = (f.nz + f.zc - 1) / f.zc;
+  f.ntiles = (long long)f.ntx * f.nty * f.ntz;
+  f.n = (long long)f.nx * f.ny * f.nz;
+  f.nv = f.n / VT<T>::VW;
+  f.b = b;
+  f.x = x;
+  f.r = a.r;
+  f.p0 = a.p0;
+  f.p1 = a.p1;
+  f.q = a.q;
+  f.partials = a.partials;
+  f.bar = a.bar;
+  f.ctl = a.ctl;
+  f.tol = tol;
+  f.maxit = maxit;
+  f.spin_cycles = fc.spin_cycles;
+  const dim3 block(32, fc.ty);
+  const size_t smem = (size_t)(fc.ty + 2) * (W + 2) * sizeof(T);
+  int per_sm = 0, dev = 0, nsm = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_fused<T>, 32 * fc.ty, smem)) !=
+          cudaSuccess) {
+    if (err) *err = std::string("fused CG occupancy: ") + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  long long G = (long long)per_sm * nsm;
+  G = std::min<long long>(G, fc.max_blocks);
+  G = std::max<long long>(1, std::min<long long>(G, std::max<long long>(f.ntiles, nsm)));
+  f.expected = (unsigned)G + (unsigned)std::max(0, fc.missing);
+  if ((e = cudaMemsetAsync(a.bar, 0, sizeof(FusedBar), a.st)) != cudaSuccess) {
+    if (err) *err = std::string("fused CG barrier reset: ") + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  void* args[] = {&f};
+  {
+    ProfScope ps(a.prof, KI_CG_FUSED, a.st);
+    e = cudaLaunchCooperativeKernel((const void*)k_cg_fused<T>, dim3((unsigned)G), block, args, smem, a.st);
+  }
+  if (e != cudaSuccess) {
+    if (err) *err = std::string("fused CG launch: ") + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  if ((e = cudaMemcpyAsync(a.ctl_host, a.ctl, sizeof(SolverCtl), cudaMemcpyDeviceToHost, a.st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(a.st)) != cudaSuccess) {
+    if (err) *err = std::string("fused CG: ") + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  const SolverCtl& c = *a.ctl_host;
+  if (iters) *iters = c.iter;
+  if (rel) *rel = c.rel;
+  // algorithmic traffic of the solve, each field touched once per pass:
+  // mean of b (1), r = b - L_c x0 (b, x in, r out: 3), per iteration phase A
+  // (r, p_old in, p, q out: 4) + phase B (x, p, r, q in, x, r out: 6), and
+  // the gauge (x twice in, x out: 3)
+  if (a.prof) a.prof->bytes[KI_CG_FUSED] += (7.0 + 10.0 * c.iter) * (double)f.n * sizeof(T);
+  switch (c.done) {
+    case 1:
+    case 4: return LES_OK;
+    case 2: return LES_ERR_NOT_CONVERGED;
+    case 3:
+      if (err) *err = "poisson: breakdown (zero or non-finite p.Ap / residual)";
+      return LES_ERR_NONFINITE;
+    case 5:
+      if (err) *err = "poisson: a grid barrier wait timed out";
+      return LES_ERR_TIMEOUT;
+    default:
+      if (err) *err = "poisson: fused solver returned no status";
+      return LES_ERR_CUDA;
+  }
+}
+
+template bool fused_cg_eligible<float>(const Grid<float>&, int, int, int);
+template bool fused_cg_eligible<double>(const Grid<double>&, int, int, int);
+template int poisson_solve_fused<float>(const SolverArgs<float>&, const FusedCfg&, const float*, float*, double,
+                                        int, int*, double*, std::string*);
+template int poisson_solve_fused<double>(const SolverArgs<double>&, const FusedCfg&, const double*, double*,
+                                         double, int, int*, double*, std::string*);
+
+}  // namespace les

@@ -66,6 +66,26 @@ struct SolverCtl {
 
 enum Ticket { TK_SUM = 0, TK_INIT, TK_MATVEC, TK_UPDATE, TK_JACOBI, TK_DIAG, TK_MAX, TK_SPARE };
 
+// Grid barrier of the persistent solver (lives in the workspace, cleared
+// before every launch).
+struct FusedBar {
+  unsigned count;   // blocks arrived at the current barrier
+  unsigned gen;     // barrier generation
+  int fail;         // a wait timed out
+  int pad;
+  double value[4];  // totals published by the last block to arrive
+};
+
+// Tile shape and limits of the persistent solver.
+struct FusedCfg {
+  int ty = 4;                           // thread rows per block (block = 32 x ty)
+  int zc = 4;                           // z-planes per tile
+  int max_blocks = 1 << 30;             // cap on the cooperative grid
+  long long spin_cycles = 4000000000LL; // barrier wait limit (~2 s at 2 GHz)
+  double timeout_ms = 2000.0;
+  int missing = 0;                      // test hook: arrivals that never come
+};
+
 struct LaunchCfg {
   dim3 grid, block;
 };
@@ -74,7 +94,7 @@ struct LaunchCfg {
 enum KernelId : int {
   KI_THERMO = 0, KI_RADIATION, KI_NU, KI_NU_HALF, KI_SCALAR, KI_MOMENTUM, KI_RHS, KI_CORRECT,
   KI_DIAG, KI_CFL, KI_APPLY, KI_SUM, KI_CG_INIT, KI_CG_MATVEC, KI_CG_UPDATE, KI_JACOBI, KI_FINISH,
-  KI_CTL, KI_COUNT
+  KI_CTL, KI_CG_FUSED, KI_COUNT
 };
 extern const char* const kKernelNames[KI_COUNT];
 
@@ -85,6 +105,7 @@ struct Profiler {
   long long launches[KI_COUNT] = {};
   long long timed[KI_COUNT] = {};
   double ms[KI_COUNT] = {};
+  double bytes[KI_COUNT] = {};  // algorithmic bytes of launches whose size varies
   struct Rec {
     int id;
     cudaEvent_t a, b;
@@ -132,7 +153,7 @@ struct Profiler {
   }
   void reset() {
     collect();
-    for (int i = 0; i < KI_COUNT; ++i) launches[i] = timed[i] = 0, ms[i] = 0.0;
+    for (int i = 0; i < KI_COUNT; ++i) launches[i] = timed[i] = 0, ms[i] = bytes[i] = 0.0;
   }
   ~Profiler() {
     for (auto& r : pending) {
@@ -217,10 +238,21 @@ struct SolverArgs {
   T* p1;
   T* q;
   Profiler* prof;
+  FusedBar* bar = nullptr;          // persistent-solver barrier (workspace)
+  const FusedCfg* fused = nullptr;  // enables the persistent CG when eligible
 };
 
 template <typename T>
 cudaError_t launch_apply(const SolverArgs<T>& a, int op, const T* x, T* y);
+
+// Persistent single-launch CG (les_cg_fused.cu): compact operator, nx a
+// multiple of the 16-byte tile width (128 floats / 64 doubles), ny a multiple
+// of cfg.ty.
+template <typename T>
+bool fused_cg_eligible(const Grid<T>& g, int op, int solver, int ty);
+template <typename T>
+int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
+                        int* iters, double* rel, std::string* err);
 
 // Solve A x = b; returns LES_OK / LES_ERR_NOT_CONVERGED / LES_ERR_CUDA.
 template <typename T>

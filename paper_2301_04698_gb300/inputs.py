@@ -80,6 +80,7 @@ class Case:
     tol: float = 1e-10
     maxit: int = 5000
     omega: float = 2.0 / 3.0
+    solver_path: int = 0       # 0: persistent CG launch when eligible, 1: per-phase launches
     physics: tuple = ("adv", "sgs")
     cs: float = 0.18
     pr: float = 0.4

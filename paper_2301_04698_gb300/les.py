@@ -39,7 +39,8 @@ EXPORTED = ("les_config_default", "les_workspace_bytes", "les_init", "les_destro
             "les_set_state", "les_get_state", "les_field_offset", "les_step", "les_stage",
             "les_poisson_solve", "les_apply_poisson", "les_diagnostics", "les_get_dt", "les_set_dt",
             "les_last_error", "les_status_string", "les_profile_enable", "les_profile_read",
-            "les_profile_reset", "les_launch_count", "les_poisson_solve_static")
+            "les_profile_reset", "les_launch_count", "les_poisson_solve_static", "les_get_tuning",
+            "les_set_tuning")
 
 
 class LesConfig(C.Structure):
@@ -56,7 +57,7 @@ class LesConfig(C.Structure):
         ("sponge_frac", C.c_double), ("sponge_rate", C.c_double), ("subs_div", C.c_double),
         ("shf", C.c_double), ("lhf", C.c_double), ("rad_f0", C.c_double), ("rad_f1", C.c_double),
         ("rad_kappa", C.c_double), ("theta0", C.c_double), ("p00", C.c_double),
-        ("sat_tol", C.c_double), ("sat_maxit", C.c_int32), ("reserved0", C.c_int32),
+        ("sat_tol", C.c_double), ("sat_maxit", C.c_int32), ("solver_path", C.c_int32),
         ("reserved", C.c_double * 4),
     ]
 
@@ -74,6 +75,12 @@ class LesKernelStat(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("fields_per_cell", C.c_int32), ("reserved0", C.c_int32),
                 ("launches", C.c_int64), ("timed", C.c_int64), ("total_ms", C.c_double),
                 ("bytes_per_launch", C.c_double)]
+
+
+class LesTuning(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("cg_tile_rows", C.c_int32), ("cg_tile_planes", C.c_int32),
+                ("cg_max_blocks", C.c_int32), ("barrier_timeout_ms", C.c_double),
+                ("fault_missing_arrivals", C.c_int32), ("reserved0", C.c_int32)]
 
 
 class LesError(RuntimeError):
@@ -139,6 +146,10 @@ def load_library(path: str = LIB_PATH):
     lib.les_profile_reset.argtypes = [vp]
     lib.les_launch_count.restype = C.c_int64
     lib.les_launch_count.argtypes = [vp]
+    lib.les_get_tuning.restype = C.c_int
+    lib.les_get_tuning.argtypes = [vp, C.POINTER(LesTuning)]
+    lib.les_set_tuning.restype = C.c_int
+    lib.les_set_tuning.argtypes = [vp, C.POINTER(LesTuning)]
     lib.les_poisson_solve_static.restype = C.c_int
     lib.les_poisson_solve_static.argtypes = [cfgp, vp, vp, vp, dbl, i32, vp, C.POINTER(i32), C.POINTER(dbl),
                                              C.c_char_p, sz]
@@ -170,6 +181,7 @@ def config_from_case(case) -> LesConfig:
         setattr(c, k, float(getattr(case, k)))
     c.const_nu = float(case.nu_const)
     c.sat_maxit = int(case.sat_maxit)
+    c.solver_path = int(getattr(case, "solver_path", 0))
     return c
 
 
@@ -320,6 +332,18 @@ class Simulation:
                         "launches": k.launches, "timed": k.timed, "total_ms": k.total_ms,
                         "bytes_per_launch": k.bytes_per_launch})
         return out
+
+    def tuning(self) -> dict:
+        t = LesTuning()
+        _check(self.lib, self.h, self.lib.les_get_tuning(self.h, C.byref(t)), "get tuning")
+        return {k: getattr(t, k) for k, _ in t._fields_ if k not in ("struct_size", "reserved0")}
+
+    def set_tuning(self, **kw) -> None:
+        t = LesTuning()
+        t.struct_size = C.sizeof(LesTuning)
+        for k, v in kw.items():
+            setattr(t, k, v)
+        _check(self.lib, self.h, self.lib.les_set_tuning(self.h, C.byref(t)), "set tuning")
 
     def launch_count(self) -> int:
         return int(self.lib.les_launch_count(self.h))

@@ -287,3 +287,98 @@ def test_ragged_and_minimum_grids(les_mod, shape):
     ref.step(2)
     for f in ("u", "v", "w"):
         assert rel(sim.get(f), ref.get(f)) < 1e-9, f
+
+
+# --------------------------------------------------------------------------
+# persistent single-launch CG (fast path for nx a multiple of the tile width)
+
+
+def _fused_launches(sim):
+    return sum(k["launches"] for k in sim.profile_read() if k["name"] == "cg_fused")
+
+
+@pytest.mark.parametrize("precision,walls,shape", [(32, True, (128, 16, 12)), (32, False, (256, 8, 5)),
+                                                   (64, True, (64, 8, 9)), (64, False, (128, 4, 2))])
+def test_fused_cg_matches_oracle(les_mod, precision, walls, shape):
+    from oracle import Oracle
+    nx, ny, nz = shape
+    case = inputs.Case(name="fused", nx=nx, ny=ny, nz=nz, dx=35.0, dy=30.0, dz=10.0, walls=walls,
+                       precision=precision, init="zero", physics=())
+    sim = les_mod.Simulation(case)
+    ref = Oracle(case.replace(precision=64))
+    b = inputs.uniform(21, 0, case.n, -1, 1).reshape(case.shape) + 0.25
+    xr, st, itr, _ = ref.poisson(b, tol=1e-12, maxit=20000)
+    dt = torch.float64 if precision == 64 else torch.float32
+    tol = 1e-11 if precision == 64 else 1e-6
+    bt = torch.from_numpy(b).to("cuda", dt)
+    results = []
+    for ty, zc in ((4, 4), (1, 1), (2, 3), (8, 16)):
+        if ny % ty:
+            continue
+        sim.set_tuning(cg_tile_rows=ty, cg_tile_planes=zc)
+        sim.profile_reset()
+        x = torch.zeros_like(bt)
+        rc, it, res = sim.poisson_solve(bt, x, tol, 20000)
+        assert rc == 0 and res <= tol
+        assert _fused_launches(sim) == 1
+        xn = x.cpu().double().numpy()
+        # zero-mean gauge, to rounding of the field's magnitude
+        assert abs(xn.mean()) < (1e-14 if precision == 64 else 1e-6) * np.abs(xn).max()
+        assert rel(xn, xr) < (1e-8 if precision == 64 else 5e-4), (ty, zc)
+        results.append((it, xn))
+    # the per-phase launch path reaches the same solution
+    case1 = case.replace(solver_path=1)
+    sim1 = les_mod.Simulation(case1)
+    x1 = torch.zeros_like(bt)
+    rc, it1, res1 = sim1.poisson_solve(bt, x1, tol, 20000)
+    assert _fused_launches(sim1) == 0
+    for it, xn in results:
+        assert abs(it - it1) <= 2
+        assert rel(xn, x1.cpu().double().numpy()) < (1e-9 if precision == 64 else 2e-5)
+
+
+def test_fused_cg_barrier_timeout_is_reported(les_mod):
+    case = inputs.Case(name="fused", nx=128, ny=8, nz=4, dx=1.0, dy=1.0, dz=1.0, precision=32,
+                       init="zero", physics=())
+    sim = les_mod.Simulation(case)
+    b = torch.from_numpy(inputs.uniform(3, 0, case.n, -1, 1).reshape(case.shape)).to("cuda", torch.float32)
+    x = torch.zeros_like(b)
+    # every barrier waits for one block that never arrives: each wait must end
+    # after its limit with a status the host reads, leaving the device usable
+    sim.set_tuning(barrier_timeout_ms=20.0, fault_missing_arrivals=1)
+    with pytest.raises(les_mod.LesError) as e:
+        sim.poisson_solve(b, x, 1e-6, 100)
+    assert e.value.status == les_mod.LES_ERR_TIMEOUT
+    sim.set_tuning(barrier_timeout_ms=2000.0, fault_missing_arrivals=0)
+    x.zero_()
+    rc, it, res = sim.poisson_solve(b, x, 1e-6, 1000)
+    assert rc == 0 and res <= 1e-6
+
+
+def test_fused_steps_fp64(les_mod):
+    case = _moist_case(nx=64, ny=16, nz=16, dt=1.0)
+    sim, ref, _ = pair(les_mod, case)
+    sim.profile_reset()
+    sim.step(3)
+    ref.step(3)
+    assert _fused_launches(sim) == 3 * case.K
+    for f in ("u", "v", "w", "theta_l", "q_t"):
+        assert rel(sim.get(f), ref.get(f)) < 1e-9, f
+    assert rel(demean(sim.get("p")), demean(ref.get("p"))) < 1e-8
+
+
+def test_bench_workload_full_size_step(les_mod):
+    """The bench workload at its full size (128 x 128 x 96, FP32, persistent CG)
+    against the FP64 oracle after one step."""
+    case = inputs.cbl(128, 128, 96, precision=32)
+    sim, ref, _ = pair(les_mod, case)
+    sim.profile_reset()
+    stats = sim.step(1)
+    ref.step(1)
+    assert _fused_launches(sim) == case.K and stats["not_converged"] == 0
+    errs = {f: rel(sim.get(f), ref.get(f)) for f in ("u", "v", "w", "theta_l", "q_t")}
+    errs["p"] = rel(demean(sim.get("p")), demean(ref.get("p")))
+    print("full-size FP32 vs FP64 relative L2 after 1 step:", errs)
+    assert errs["theta_l"] < 1e-6 and errs["q_t"] < 1e-5
+    assert errs["u"] < 1e-5 and errs["v"] < 1e-5
+    assert errs["w"] < 5e-2 and errs["p"] < 5e-2
