@@ -257,8 +257,11 @@ int les_poisson_solve_static(const les_config *cfg, const void *d_rho0, const vo
  * after barrier_timeout_ms; the solve then returns LES_ERR_TIMEOUT and the
  * device stays usable.  fault_missing_arrivals is a failure-detection test
  * hook: the barrier then waits for that many blocks that never arrive, so
- * every wait runs out; it must be 0 otherwise.  A zero field in a set call
- * keeps the current value (except fault_missing_arrivals). */
+ * every wait runs out; it must be 0 otherwise.  stencil_path 0 (default) runs
+ * the shared-memory tiled predictors with nu_t computed in-tile, 1 the
+ * direct-load predictors with nu_t stored between kernels (same results to
+ * rounding).  A zero field in a set call keeps the current value (except
+ * fault_missing_arrivals and stencil_path, which are always taken). */
 typedef struct les_tuning {
   uint32_t struct_size;            /* sizeof(les_tuning)                   */
   int32_t  cg_tile_rows;           /* 1, 2, 4 or 8                          */
@@ -266,7 +269,7 @@ typedef struct les_tuning {
   int32_t  cg_max_blocks;          /* >= 1                                  */
   double   barrier_timeout_ms;     /* > 0                                   */
   int32_t  fault_missing_arrivals; /* 0 in production                      */
-  int32_t  reserved0;
+  int32_t  stencil_path;           /* 0 tiled (default), 1 direct-load      */
 } les_tuning;
 int les_get_tuning(les_handle *h, les_tuning *out);
 int les_set_tuning(les_handle *h, const les_tuning *in);

@@ -246,8 +246,11 @@ int fields_per_cell(const les_config& c, int id) {
     case KI_RADIATION: return 3;
     case KI_NU: return 4 + (fb ? 1 : 0);
     case KI_NU_HALF: return 10 + (fb ? 1 : 0);
-    case KI_SCALAR: return 10 + ((c.physics & LES_PHYS_RAD) ? 1 : 0);
-    case KI_MOMENTUM: return 11 + ((c.physics & LES_PHYS_BUOY) ? 1 : 0);
+    // tiled predictors (nu_t in-tile): scalar reads u, v, w, phi^k (2),
+    // phi^{n+1/2} (2) [+ b for f_B, + radiative source], writes 2; momentum
+    // reads u^k (3), u^n (3), p, b and writes 3
+    case KI_SCALAR: return 9 + (fb ? 1 : 0) + ((c.physics & LES_PHYS_RAD) ? 1 : 0);
+    case KI_MOMENTUM: return 11;
     case KI_RHS: return c.poisson_op == LES_OP_COMPACT ? 5 : 4;
     case KI_CORRECT: return 9;
     case KI_DIAG: return 7;
@@ -317,14 +320,20 @@ int stage_scalar(les_handle* h) {
   auto a = stage_args<T>(h);
   cudaError_t e;
   T* const* F = (T* const*)h->fixed;
-  if ((e = launch_nu<T>(a, F[B_U], F[B_V], F[B_W], nullptr, nullptr, nullptr, F[B_B], nullptr, nullptr, nullptr,
-                        F[B_NU])) != cudaSuccess)
-    return h->cuda_fail(e, "nu (scalars)");
   const int ti = h->cur ? B_THB : B_THA, qi = h->cur ? B_QTB : B_QTA;
   const int to = h->cur ? B_THA : B_THB, qo = h->cur ? B_QTA : B_QTB;
-  if ((e = launch_scalar<T>(a, F[B_U], F[B_V], F[B_W], F[B_NU], F[ti], F[qi], F[B_THH], F[B_QTH], F[B_SRAD],
-                            F[to], F[qo])) != cudaSuccess)
-    return h->cuda_fail(e, "scalar predictor");
+  if (h->fused.stencil_path == 0) {
+    if ((e = launch_scalar_tiled<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_B], F[ti], F[qi], F[B_THH],
+                                    F[B_QTH], F[B_SRAD], F[to], F[qo])) != cudaSuccess)
+      return h->cuda_fail(e, "scalar predictor");
+  } else {
+    if ((e = launch_nu<T>(a, F[B_U], F[B_V], F[B_W], nullptr, nullptr, nullptr, F[B_B], nullptr, nullptr,
+                          nullptr, F[B_NU])) != cudaSuccess)
+      return h->cuda_fail(e, "nu (scalars)");
+    if ((e = launch_scalar<T>(a, F[B_U], F[B_V], F[B_W], F[B_NU], F[ti], F[qi], F[B_THH], F[B_QTH], F[B_SRAD],
+                              F[to], F[qo])) != cudaSuccess)
+      return h->cuda_fail(e, "scalar predictor");
+  }
   h->cur ^= 1;
   return LES_OK;
 }
@@ -334,12 +343,18 @@ int stage_momentum(les_handle* h) {
   auto a = stage_args<T>(h);
   cudaError_t e;
   T* const* F = (T* const*)h->fixed;
-  if ((e = launch_nu<T>(a, F[B_U], F[B_V], F[B_W], F[B_UN], F[B_VN], F[B_WN], F[B_B], F[B_UHALF], F[B_VHALF],
-                        F[B_WHALF], F[B_NU])) != cudaSuccess)
-    return h->cuda_fail(e, "nu (momentum)");
-  if ((e = launch_momentum<T>(a, F[B_UHALF], F[B_VHALF], F[B_WHALF], F[B_UN], F[B_VN], F[B_WN], F[B_NU], F[B_P],
-                              F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess)
-    return h->cuda_fail(e, "momentum predictor");
+  if (h->fused.stencil_path == 0) {
+    if ((e = launch_momentum_tiled<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_UN], F[B_VN], F[B_WN],
+                                      F[B_P], F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess)
+      return h->cuda_fail(e, "momentum predictor");
+  } else {
+    if ((e = launch_nu<T>(a, F[B_U], F[B_V], F[B_W], F[B_UN], F[B_VN], F[B_WN], F[B_B], F[B_UHALF],
+                          F[B_VHALF], F[B_WHALF], F[B_NU])) != cudaSuccess)
+      return h->cuda_fail(e, "nu (momentum)");
+    if ((e = launch_momentum<T>(a, F[B_UHALF], F[B_VHALF], F[B_WHALF], F[B_UN], F[B_VN], F[B_WN], F[B_NU],
+                                F[B_P], F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess)
+      return h->cuda_fail(e, "momentum predictor");
+  }
   if ((e = launch_rhs<T>(a, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI], F[B_RHS])) !=
       cudaSuccess)
     return h->cuda_fail(e, "poisson rhs");
@@ -708,6 +723,7 @@ int les_get_tuning(les_handle* h, les_tuning* out) {
   out->cg_max_blocks = h->fused.max_blocks;
   out->barrier_timeout_ms = h->fused.timeout_ms;
   out->fault_missing_arrivals = h->fused.missing;
+  out->stencil_path = h->fused.stencil_path;
   return LES_OK;
 }
 
@@ -730,6 +746,8 @@ int les_set_tuning(les_handle* h, const les_tuning* in) {
     h->fused.spin_cycles = (long long)(in->barrier_timeout_ms * (double)khz);
   }
   h->fused.missing = in->fault_missing_arrivals;
+  if (in->stencil_path != 0 && in->stencil_path != 1) return h->fail(LES_ERR_INVALID_ARG, "stencil_path must be 0 or 1");
+  h->fused.stencil_path = in->stencil_path;
   return LES_OK;
 }
 

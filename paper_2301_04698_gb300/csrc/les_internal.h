@@ -84,6 +84,7 @@ struct FusedCfg {
   long long spin_cycles = 4000000000LL; // barrier wait limit (~2 s at 2 GHz)
   double timeout_ms = 2000.0;
   int missing = 0;                      // test hook: arrivals that never come
+  int stencil_path = 0;                 // 0 tiled predictors, 1 direct-load predictors
 };
 
 struct LaunchCfg {
@@ -206,6 +207,15 @@ template <typename T>
 cudaError_t launch_momentum(const StageArgs<T>& a, const T* uh, const T* vh, const T* wh,
                             const T* un, const T* vn, const T* wn, const T* nu, const T* p,
                             const T* b, T* ou, T* ov, T* ow);
+// shared-memory tiled predictors with nu_t computed in-tile (les_stencil_tiled.cu)
+template <typename T>
+cudaError_t launch_scalar_tiled(const StageArgs<T>& a, int max_blocks, const T* u, const T* v, const T* w,
+                                const T* b, const T* thk, const T* qtk, const T* thh, const T* qth,
+                                const T* srad, T* th_out, T* qt_out);
+template <typename T>
+cudaError_t launch_momentum_tiled(const StageArgs<T>& a, int max_blocks, const T* uk, const T* vk, const T* wk,
+                                  const T* un, const T* vn, const T* wn, const T* p, const T* b, T* ou, T* ov,
+                                  T* ow);
 template <typename T>
 cudaError_t launch_rhs(const StageArgs<T>& a, int op, const T* ou, const T* ov, const T* ow,
                        const T* psi, T* rhs);

@@ -80,7 +80,7 @@ class LesKernelStat(C.Structure):
 class LesTuning(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("cg_tile_rows", C.c_int32), ("cg_tile_planes", C.c_int32),
                 ("cg_max_blocks", C.c_int32), ("barrier_timeout_ms", C.c_double),
-                ("fault_missing_arrivals", C.c_int32), ("reserved0", C.c_int32)]
+                ("fault_missing_arrivals", C.c_int32), ("stencil_path", C.c_int32)]
 
 
 class LesError(RuntimeError):
@@ -336,11 +336,12 @@ class Simulation:
     def tuning(self) -> dict:
         t = LesTuning()
         _check(self.lib, self.h, self.lib.les_get_tuning(self.h, C.byref(t)), "get tuning")
-        return {k: getattr(t, k) for k, _ in t._fields_ if k not in ("struct_size", "reserved0")}
+        return {k: getattr(t, k) for k, _ in t._fields_ if k != "struct_size"}
 
     def set_tuning(self, **kw) -> None:
         t = LesTuning()
         t.struct_size = C.sizeof(LesTuning)
+        t.stencil_path = self.tuning()["stencil_path"]
         for k, v in kw.items():
             setattr(t, k, v)
         _check(self.lib, self.h, self.lib.les_set_tuning(self.h, C.byref(t)), "set tuning")

@@ -140,8 +140,10 @@ def _moist_case(nx=37, ny=11, nz=12, **kw):
     return c.replace(**kw)
 
 
-@pytest.mark.parametrize("walls", [True, False])
-def test_stages_fp64(les_mod, walls):
+@pytest.mark.parametrize("walls,stencil_path", [(True, 0), (False, 0), (True, 1), (False, 1)])
+def test_stages_fp64(les_mod, walls, stencil_path):
+    """Stage-by-stage FP64 parity; stencil_path 0 = shared-memory tiled
+    predictors (nu_t in-tile), 1 = direct-load predictors."""
     case = _moist_case()
     if not walls:
         case = case.replace(walls=False, physics=("adv", "sgs", "fb", "moist", "buoy", "coriolis"))
@@ -151,6 +153,7 @@ def test_stages_fp64(les_mod, walls):
         st[k] = st[k] + pert[k]
     st["p"] = pert["p"]
     sim, ref, _ = pair(les_mod, case, st)
+    sim.set_tuning(stencil_path=stencil_path)
     sim.stage("begin")
     ref.begin_step()
     assert abs(sim.dt - ref.dt) == 0.0
