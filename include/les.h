@@ -274,6 +274,51 @@ typedef struct les_tuning {
 int les_get_tuning(les_handle *h, les_tuning *out);
 int les_set_tuning(les_handle *h, const les_tuning *in);
 
+/* ---- learned Poisson warm start (not in the paper) ---------------------------
+ * A 3-level 3-D U-Net with periodic padding predicts the first guess psi_0 of
+ * the pressure-correction solve from its right-hand side b (Sec. 2.4 defines
+ * the solve; the network is this library's addition):
+ *   x0 = b / s, s = rms(b); e1 = B(x0; 1->16); e2 = B(pool e1; 16->32);
+ *   e3 = B(pool e2; 32->64); g2 = B([up e3, e2]; 96->32);
+ *   g1 = B([up g2, e1]; 48->16); y = conv1x1(g1; 16->1); psi_0 = s (y - mean y)
+ * B(.; a->c): two 3x3x3 convolutions, each followed by a leaky ReLU (0.1);
+ * pool: 2x2x2 mean; up: nearest doubling; [.,.]: channel concatenation.
+ * BF16 weights and activations, FP32 accumulation (tensor cores), FP32
+ * master weights and Adam.  The grid is cubic, n a multiple of 4 (>= 8).
+ * Weights are one flat FP32 vector of les_unet_param_count() values, layer by
+ * layer (enc1a, enc1b, enc2a, enc2b, enc3a, enc3b, dec2a, dec2b, dec1a,
+ * dec1b, head), each W[cout][cin][kz][ky][kx] followed by bias[cout].
+ * The model borrows a caller-allocated device workspace like the solver.
+ * b / psi arrays: device, batch * n^3 values of the given precision (32/64),
+ * one sample after another, x fastest. */
+typedef struct les_unet les_unet;
+int64_t les_unet_param_count(void);
+int les_unet_workspace_bytes(int32_t n, int32_t max_batch, size_t *bytes);
+int les_unet_create(int32_t n, int32_t max_batch, void *workspace, size_t workspace_bytes, void *stream,
+                    les_unet **out);
+void les_unet_destroy(les_unet *u);
+int les_unet_set_stream(les_unet *u, void *stream);
+/* load / read the FP32 master weights (resets the Adam moments on load) */
+int les_unet_set_weights(les_unet *u, const float *w, int32_t on_device);
+int les_unet_get_weights(les_unet *u, float *w, int32_t on_device);
+/* psi_0 for each of `batch` right-hand sides */
+int les_unet_forward(les_unet *u, int32_t precision, const void *d_b, int32_t batch, void *d_psi0);
+/* mean squared error of the network output against psi / s and its gradient
+ * with respect to every weight (d_grad: device FP32, may be NULL); *loss on
+ * the host (may be NULL; synchronises the stream when given) */
+int les_unet_loss_grad(les_unet *u, int32_t precision, const void *d_b, const void *d_psi, int32_t batch,
+                       double *loss, float *d_grad);
+/* loss_grad followed by one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) */
+int les_unet_train_step(les_unet *u, int32_t precision, const void *d_b, const void *d_psi, int32_t batch,
+                        float lr, double *loss);
+const char *les_unet_last_error(const les_unet *u);
+/* Attach a model to a solver handle for LES_WARM_LEARNED (NULL detaches).
+ * The model's grid must equal the handle's (nx = ny = nz = n); the handle
+ * borrows the model until detached or destroyed.  If the model fails, the
+ * solve falls back to a zero first guess and the step reports it in
+ * les_last_error(). */
+int les_set_warm_model(les_handle *h, les_unet *u);
+
 /* ---- launch accounting and event profiling -------------------------------- */
 #define LES_MAX_KERNELS 32
 typedef struct les_kernel_stat {

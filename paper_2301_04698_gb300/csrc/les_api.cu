@@ -125,6 +125,8 @@ struct les_handle {
   double* diag = nullptr;
   FusedBar* bar = nullptr;
   FusedCfg fused;
+  les_unet* model = nullptr;
+  int learned_fallbacks = 0;
   int cur = 0;           // scalar ping-pong: 0 -> A holds phi^k, 1 -> B
   int next_stage = LES_STAGE_BEGIN;
   int sub = 0;
@@ -371,7 +373,15 @@ int stage_solve(les_handle* h, les_step_stats* st) {
     if ((e = cudaMemcpyAsync(psi, h->prev[k], bytes, cudaMemcpyDeviceToDevice, h->st)) != cudaSuccess)
       return h->cuda_fail(e, "warm start");
   } else if (h->cfg.warm_start == LES_WARM_LEARNED) {
-    return h->fail(LES_ERR_NO_MODEL, "learned warm start is not available in this build");
+    if (!h->model) return h->fail(LES_ERR_NO_MODEL, "learned warm start requested but no model is attached");
+    std::string merr;
+    const int mrc = unet_predict(h->model, h->cfg.precision, h->fixed[B_RHS], psi, h->st, &merr);
+    if (mrc != LES_OK) {
+      // the plain solver is the fallback: start from zero
+      h->learned_fallbacks += 1;
+      h->err = "learned warm start failed (" + merr + "); solved from a zero first guess";
+      if ((e = cudaMemsetAsync(psi, 0, bytes, h->st)) != cudaSuccess) return h->cuda_fail(e, "memset");
+    }
   } else {
     if ((e = cudaMemsetAsync(psi, 0, bytes, h->st)) != cudaSuccess) return h->cuda_fail(e, "memset");
   }
@@ -448,7 +458,8 @@ namespace les {
 
 const char* const kKernelNames[KI_COUNT] = {
     "thermo", "radiation", "nu", "nu_half", "scalar", "momentum", "rhs", "correct", "diag",
-    "cfl", "apply", "sum", "cg_init", "cg_matvec", "cg_update", "jacobi", "finish", "ctl", "cg_fused"};
+    "cfl", "apply", "sum", "cg_init", "cg_matvec", "cg_update", "jacobi", "finish", "ctl", "cg_fused",
+    "unet_conv", "unet_wgrad", "unet_adam"};
 
 template <typename T>
 Grid<T> make_grid(const les_config& c, int zc) {
@@ -748,6 +759,17 @@ int les_set_tuning(les_handle* h, const les_tuning* in) {
   h->fused.missing = in->fault_missing_arrivals;
   if (in->stencil_path != 0 && in->stencil_path != 1) return h->fail(LES_ERR_INVALID_ARG, "stencil_path must be 0 or 1");
   h->fused.stencil_path = in->stencil_path;
+  return LES_OK;
+}
+
+int les_set_warm_model(les_handle* h, les_unet* u) {
+  if (!h) return LES_ERR_INVALID_ARG;
+  if (u) {
+    const int n = unet_grid(u);
+    if (h->cfg.nx != n || h->cfg.ny != n || h->cfg.nz != n)
+      return h->fail(LES_ERR_INVALID_ARG, "the model's grid differs from the handle's");
+  }
+  h->model = u;
   return LES_OK;
 }
 

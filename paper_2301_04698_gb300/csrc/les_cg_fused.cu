@@ -88,8 +88,10 @@ __device__ __forceinline__ int zmap(int k, int nz, int walls) {
   return k < 0 ? k + nz : (k >= nz ? k - nz : k);
 }
 
-// Grid-wide FP64 sum of NV values (block partials in thread 0 after the block
-// reduce).  Returns false (in every thread) if the barrier wait timed out.
+// Grid-wide FP64 sum of NV values.  Every block posts its partials; the last
+// block to arrive folds them in block order (deterministic), publishes the
+// totals and bumps the generation that the others poll.  Returns false (in
+// every thread) if a wait ran past its limit.
 template <int NV>
 __device__ bool grid_sum(double (&v)[NV], FusedBar* bar, double* partials, long long spin_cycles,
                          unsigned expected) {
@@ -105,10 +107,9 @@ __device__ bool grid_sum(double (&v)[NV], FusedBar* bar, double* partials, long 
     if (tid == 0) partials[(size_t)q * G + blockIdx.x] = bv;
   }
   if (tid == 0) {
-    s_gen = ld_volatile(&bar->gen);
+    s_gen = ld_volatile(&bar->gen.v);
     __threadfence();
-    const unsigned a = atomicAdd(&bar->count, 1u);
-    s_last = (a == expected - 1);
+    s_last = atomicAdd(&bar->count.v, 1u) == expected - 1;
     s_fail = 0;
   }
   __syncthreads();
@@ -122,15 +123,17 @@ __device__ bool grid_sum(double (&v)[NV], FusedBar* bar, double* partials, long 
       if (tid == 0) bar->value[q] = tot;
     }
     if (tid == 0) {
-      bar->count = 0;
+      bar->count.v = 0u;
       __threadfence();
-      atomicAdd(&bar->gen, 1u);
+      atomicAdd(&bar->gen.v, 1u);
     }
   } else if (tid == 0) {
     const long long t0 = clock64();
-    while (ld_volatile(&bar->gen) == s_gen) {
-      if (ld_volatile(reinterpret_cast<const unsigned*>(&bar->fail)) != 0u || clock64() - t0 > spin_cycles) {
-        atomicExch(&bar->fail, 1);
+    unsigned spins = 0;
+    while (ld_volatile(&bar->gen.v) == s_gen) {
+      if ((++spins & 63u) == 0u &&
+          (ld_volatile(&bar->fail.v) != 0u || clock64() - t0 > spin_cycles)) {
+        atomicExch(&bar->fail.v, 1u);
         s_fail = 1;
         break;
       }
@@ -144,78 +147,68 @@ __device__ bool grid_sum(double (&v)[NV], FusedBar* bar, double* partials, long 
   return true;
 }
 
-// One 2.5-D sweep of the compact Laplacian over this block's tiles.
+// One sweep of the compact Laplacian over this block's tiles.  A tile is
+// (32 VW) x TY x zc nodes; all zc + 2 planes of the operand (with the x / y
+// halos of the zc interior planes) are requested at once and staged in
+// shared memory, so a tile costs one round of memory latency.
 // loadP(o, m): the VW operand values at linear index m; emit(m, P, q).
 template <typename T, typename LoadP, typename LoadP1, typename Emit>
 __device__ __forceinline__ void stencil_sweep(const FusedArgs<T>& f, T* sm, const LoadP& loadP,
                                               const LoadP1& loadP1, const Emit& emit) {
   constexpr int VW = VT<T>::VW, W = VT<T>::W;
   const int tx = threadIdx.x, ty = threadIdx.y, TY = blockDim.y;
-  const int SW = W + 2;
+  const int SW = W + 2, SP = (TY + 2) * SW;  // row and plane strides of the staging buffer
   for (long long t = blockIdx.x; t < f.ntiles; t += gridDim.x) {
     const int ti = (int)(t % f.ntx);
     const long long rr = t / f.ntx;
     const int tj = (int)(rr % f.nty);
     const int tk = (int)(rr / f.nty);
     const int x0 = ti * W, y0 = tj * TY, k0 = tk * f.zc, k1 = min(k0 + f.zc, f.nz);
+    const int nzt = k1 - k0;
     const int xs = x0 + tx * VW, y = y0 + ty;
     const int yd = y0 == 0 ? f.ny - 1 : y0 - 1;
     const int yu = y0 + TY == f.ny ? 0 : y0 + TY;
     const int xl = x0 == 0 ? f.nx - 1 : x0 - 1;
     const int xr = x0 + W == f.nx ? 0 : x0 + W;
     auto lin = [&](int xx, int yy, int kk) -> size_t { return ((size_t)kk * f.ny + yy) * f.nx + xx; };
-    T Pm[VW], Pc[VW], Pp[VW], Pn[VW], hd[VW], hu[VW];
-    T hl = T(0), hr = T(0);
-    loadP(Pm, lin(xs, y, zmap(k0 - 1, f.nz, f.walls)));
-    loadP(Pc, lin(xs, y, k0));
-    loadP(Pp, lin(xs, y, zmap(k0 + 1, f.nz, f.walls)));
-    if (ty == 0) loadP(hd, lin(xs, yd, k0));
-    if (ty == TY - 1) loadP(hu, lin(xs, yu, k0));
-    if (tx == 0) hl = loadP1(lin(xl, y, k0));
-    if (tx == 31) hr = loadP1(lin(xr, y, k0));
-    T* row = sm + (1 + ty) * SW + 1 + tx * VW;
+    __syncthreads();  // the previous tile's reads of the staging buffer are done
+    // plane q of the buffer holds global plane k0 - 1 + q (ghost-mapped)
+    for (int q = 0; q < nzt + 2; ++q) {
+      const int kk = zmap(k0 - 1 + q, f.nz, f.walls);
+      T c[VW];
+      loadP(c, lin(xs, y, kk));
+      T* row = sm + q * SP + (1 + ty) * SW + 1 + tx * VW;
 #pragma unroll
-    for (int e = 0; e < VW; ++e) {
-      row[e] = Pc[e];
-      if (ty == 0) row[e - SW] = hd[e];
-      if (ty == TY - 1) row[e + SW] = hu[e];
-    }
-    if (tx == 0) row[-1] = hl;
-    if (tx == 31) row[VW] = hr;
-    __syncthreads();
-    for (int k = k0; k < k1; ++k) {
-      const bool more = k + 1 < k1;
-      if (more) {
-        // prefetch plane k+2 (window) and the halos of plane k+1
-        loadP(Pn, lin(xs, y, zmap(k + 2, f.nz, f.walls)));
-        if (ty == 0) loadP(hd, lin(xs, yd, k + 1));
-        if (ty == TY - 1) loadP(hu, lin(xs, yu, k + 1));
-        if (tx == 0) hl = loadP1(lin(xl, y, k + 1));
-        if (tx == 31) hr = loadP1(lin(xr, y, k + 1));
+      for (int e = 0; e < VW; ++e) row[e] = c[e];
+      if (q >= 1 && q <= nzt) {  // x / y halos only for the interior planes
+        if (ty == 0) {
+          T h[VW];
+          loadP(h, lin(xs, yd, kk));
+#pragma unroll
+          for (int e = 0; e < VW; ++e) row[e - SW] = h[e];
+        }
+        if (ty == TY - 1) {
+          T h[VW];
+          loadP(h, lin(xs, yu, kk));
+#pragma unroll
+          for (int e = 0; e < VW; ++e) row[e + SW] = h[e];
+        }
+        if (tx == 0) row[-1] = loadP1(lin(xl, y, kk));
+        if (tx == 31) row[VW] = loadP1(lin(xr, y, kk));
       }
-      T qv[VW];
+    }
+    __syncthreads();
+    for (int q = 1; q <= nzt; ++q) {
+      const T* row = sm + q * SP + (1 + ty) * SW + 1 + tx * VW;
+      T P[VW], qv[VW];
 #pragma unroll
       for (int e = 0; e < VW; ++e) {
-        const T c = Pc[e];
+        const T c = row[e];
+        P[e] = c;
         qv[e] = (row[e - 1] + row[e + 1] - T(2) * c) * f.cx + (row[e - SW] + row[e + SW] - T(2) * c) * f.cy +
-                (Pm[e] + Pp[e] - T(2) * c) * f.cz;
+                (row[e - SP] + row[e + SP] - T(2) * c) * f.cz;
       }
-      emit(lin(xs, y, k), Pc, qv);
-      __syncthreads();
-      if (more) {
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-          Pm[e] = Pc[e];
-          Pc[e] = Pp[e];
-          Pp[e] = Pn[e];
-          row[e] = Pc[e];
-          if (ty == 0) row[e - SW] = hd[e];
-          if (ty == TY - 1) row[e + SW] = hu[e];
-        }
-        if (tx == 0) row[-1] = hl;
-        if (tx == 31) row[VW] = hr;
-      }
-      __syncthreads();
+      emit(lin(xs, y, k0 + q - 1), P, qv);
     }
   }
 }
@@ -314,21 +307,35 @@ __global__ void __launch_bounds__(256) k_cg_fused(FusedArgs<T> f) {
     const T ta = (T)alpha;
     // phase B: x += alpha p, r -= alpha q, r.r
     double sb[1] = {0.0};
-    for (long long v = gtid; v < f.nv; v += gstride) {
-      const size_t m = (size_t)v * VW;
-      T xv[VW], pv[VW], rv[VW], qv[VW];
-      ldv(xv, f.x + m);
-      ldv(pv, pn + m);
-      ldv(rv, f.r + m);
-      ldv(qv, f.q + m);
+    constexpr int U = 4;  // vectors in flight per thread
+    for (long long v0 = gtid; v0 < f.nv; v0 += U * gstride) {
+      T xv[U][VW], pv[U][VW], rv[U][VW], qv[U][VW];
 #pragma unroll
-      for (int e = 0; e < VW; ++e) {
-        xv[e] += ta * pv[e];
-        rv[e] -= ta * qv[e];
+      for (int u = 0; u < U; ++u) {
+        const long long v = v0 + u * gstride;
+        if (v < f.nv) {
+          const size_t m = (size_t)v * VW;
+          ldv(xv[u], f.x + m);
+          ldv(pv[u], pn + m);
+          ldv(rv[u], f.r + m);
+          ldv(qv[u], f.q + m);
+        }
       }
-      stv(f.x + m, xv);
-      stv(f.r + m, rv);
-      sb[0] += vdot(rv, rv);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long v = v0 + u * gstride;
+        if (v < f.nv) {
+          const size_t m = (size_t)v * VW;
+#pragma unroll
+          for (int e = 0; e < VW; ++e) {
+            xv[u][e] += ta * pv[u][e];
+            rv[u][e] -= ta * qv[u][e];
+          }
+          stv(f.x + m, xv[u]);
+          stv(f.r + m, rv[u]);
+          sb[0] += vdot(rv[u], rv[u]);
+        }
+      }
     }
     if (!grid_sum<1>(sb, f.bar, f.partials, f.spin_cycles, f.expected)) {
       status = 5;
@@ -398,7 +405,7 @@ int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, 
   f.cx = a.g.idx * a.g.idx;
   f.cy = a.g.idy * a.g.idy;
   f.cz = a.g.idz * a.g.idz;
-  f.zc = std::max(1, std::min(fc.zc, f.nz));
+  f.zc = std::max(1, std::min(std::min(fc.zc, 32), f.nz));
   f.ntx = f.nx / W;
   f.nty = f.ny / fc.ty;
   f.ntz = (f.nz + f.zc - 1) / f.zc;
@@ -418,11 +425,13 @@ int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, 
   f.maxit = maxit;
   f.spin_cycles = fc.spin_cycles;
   const dim3 block(32, fc.ty);
-  const size_t smem = (size_t)(fc.ty + 2) * (W + 2) * sizeof(T);
+  const size_t smem = (size_t)(f.zc + 2) * (fc.ty + 2) * (W + 2) * sizeof(T);
   int per_sm = 0, dev = 0, nsm = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
       (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_cg_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+          cudaSuccess ||
       (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_fused<T>, 32 * fc.ty, smem)) !=
           cudaSuccess) {
     if (err) *err = std::string("fused CG occupancy: ") + cudaGetErrorString(e);

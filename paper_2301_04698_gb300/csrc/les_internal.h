@@ -68,12 +68,19 @@ enum Ticket { TK_SUM = 0, TK_INIT, TK_MATVEC, TK_UPDATE, TK_JACOBI, TK_DIAG, TK_
 
 // Grid barrier of the persistent solver (lives in the workspace, cleared
 // before every launch).
+// Grid barrier of the persistent solver (lives in the workspace, cleared
+// before every launch).  The arrival counter, the generation and the fail
+// flag each sit in their own 128-byte line so that polling does not contend
+// with the arrivals.
+struct alignas(128) BarLine {
+  unsigned v;
+  unsigned pad[31];
+};
 struct FusedBar {
-  unsigned count;   // blocks arrived at the current barrier
-  unsigned gen;     // barrier generation
-  int fail;         // a wait timed out
-  int pad;
-  double value[4];  // totals published by the last block to arrive
+  BarLine count;                 // blocks arrived at the current barrier
+  BarLine gen;                   // barrier generation
+  BarLine fail;                  // a wait timed out
+  alignas(128) double value[4];  // totals published by the last block to arrive
 };
 
 // Tile shape and limits of the persistent solver.
@@ -95,7 +102,7 @@ struct LaunchCfg {
 enum KernelId : int {
   KI_THERMO = 0, KI_RADIATION, KI_NU, KI_NU_HALF, KI_SCALAR, KI_MOMENTUM, KI_RHS, KI_CORRECT,
   KI_DIAG, KI_CFL, KI_APPLY, KI_SUM, KI_CG_INIT, KI_CG_MATVEC, KI_CG_UPDATE, KI_JACOBI, KI_FINISH,
-  KI_CTL, KI_CG_FUSED, KI_COUNT
+  KI_CTL, KI_CG_FUSED, KI_UNET_CONV, KI_UNET_WGRAD, KI_UNET_ADAM, KI_COUNT
 };
 extern const char* const kKernelNames[KI_COUNT];
 
@@ -263,6 +270,13 @@ bool fused_cg_eligible(const Grid<T>& g, int op, int solver, int ty);
 template <typename T>
 int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
                         int* iters, double* rel, std::string* err);
+
+}  // namespace les
+struct les_unet;
+namespace les {
+// learned warm start (les_unet.cu): psi_0 from b on the model's cubic grid
+int unet_predict(les_unet* u, int precision, const void* b, void* psi0, cudaStream_t st, std::string* err);
+int unet_grid(const les_unet* u);
 
 // Solve A x = b; returns LES_OK / LES_ERR_NOT_CONVERGED / LES_ERR_CUDA.
 template <typename T>

@@ -40,7 +40,10 @@ EXPORTED = ("les_config_default", "les_workspace_bytes", "les_init", "les_destro
             "les_poisson_solve", "les_apply_poisson", "les_diagnostics", "les_get_dt", "les_set_dt",
             "les_last_error", "les_status_string", "les_profile_enable", "les_profile_read",
             "les_profile_reset", "les_launch_count", "les_poisson_solve_static", "les_get_tuning",
-            "les_set_tuning")
+            "les_set_tuning", "les_unet_param_count", "les_unet_workspace_bytes", "les_unet_create",
+            "les_unet_destroy", "les_unet_set_stream", "les_unet_set_weights", "les_unet_get_weights",
+            "les_unet_forward", "les_unet_loss_grad", "les_unet_train_step", "les_unet_last_error",
+            "les_set_warm_model")
 
 
 class LesConfig(C.Structure):
@@ -150,6 +153,30 @@ def load_library(path: str = LIB_PATH):
     lib.les_get_tuning.argtypes = [vp, C.POINTER(LesTuning)]
     lib.les_set_tuning.restype = C.c_int
     lib.les_set_tuning.argtypes = [vp, C.POINTER(LesTuning)]
+    lib.les_unet_param_count.restype = C.c_int64
+    lib.les_unet_param_count.argtypes = []
+    lib.les_unet_workspace_bytes.restype = C.c_int
+    lib.les_unet_workspace_bytes.argtypes = [i32, i32, C.POINTER(sz)]
+    lib.les_unet_create.restype = C.c_int
+    lib.les_unet_create.argtypes = [i32, i32, vp, sz, vp, C.POINTER(vp)]
+    lib.les_unet_destroy.restype = None
+    lib.les_unet_destroy.argtypes = [vp]
+    lib.les_unet_set_stream.restype = C.c_int
+    lib.les_unet_set_stream.argtypes = [vp, vp]
+    lib.les_unet_set_weights.restype = C.c_int
+    lib.les_unet_set_weights.argtypes = [vp, vp, i32]
+    lib.les_unet_get_weights.restype = C.c_int
+    lib.les_unet_get_weights.argtypes = [vp, vp, i32]
+    lib.les_unet_forward.restype = C.c_int
+    lib.les_unet_forward.argtypes = [vp, i32, vp, i32, vp]
+    lib.les_unet_loss_grad.restype = C.c_int
+    lib.les_unet_loss_grad.argtypes = [vp, i32, vp, vp, i32, C.POINTER(dbl), vp]
+    lib.les_unet_train_step.restype = C.c_int
+    lib.les_unet_train_step.argtypes = [vp, i32, vp, vp, i32, C.c_float, C.POINTER(dbl)]
+    lib.les_unet_last_error.restype = C.c_char_p
+    lib.les_unet_last_error.argtypes = [vp]
+    lib.les_set_warm_model.restype = C.c_int
+    lib.les_set_warm_model.argtypes = [vp, vp]
     lib.les_poisson_solve_static.restype = C.c_int
     lib.les_poisson_solve_static.argtypes = [cfgp, vp, vp, vp, dbl, i32, vp, C.POINTER(i32), C.POINTER(dbl),
                                              C.c_char_p, sz]
@@ -354,3 +381,87 @@ class Simulation:
         rc = self.lib.les_diagnostics(self.h, out)
         _check(self.lib, self.h, rc, "les_diagnostics", (LES_OK, LES_ERR_NONFINITE))
         return dict(zip(DIAG_NAMES, list(out)))
+
+
+class UNet:
+    """The learned warm-start network behind the C ABI (les_unet_*)."""
+
+    def __init__(self, n: int, max_batch: int = 1, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = lib = load_library()
+        self.n, self.max_batch = int(n), int(max_batch)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        nbytes = C.c_size_t(0)
+        rc = lib.les_unet_workspace_bytes(self.n, self.max_batch, C.byref(nbytes))
+        _check(lib, None, rc, "les_unet_workspace_bytes")
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        rc = lib.les_unet_create(self.n, self.max_batch, C.c_void_p(self.workspace.data_ptr()), nbytes,
+                                 C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        _check(lib, None, rc, "les_unet_create")
+        self.h = h
+        self.nparams = int(lib.les_unet_param_count())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.les_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, rc, what):
+        if rc != LES_OK:
+            raise LesError(rc, f"{what}: {self.lib.les_unet_last_error(self.h).decode()}")
+
+    def set_weights(self, w) -> None:
+        t = self.torch
+        wt = t.as_tensor(np.asarray(w, dtype=np.float32) if not isinstance(w, t.Tensor) else w,
+                         dtype=t.float32).to(self.device).contiguous()
+        assert wt.numel() == self.nparams
+        self._ck(self.lib.les_unet_set_weights(self.h, C.c_void_p(wt.data_ptr()), 1), "set_weights")
+        self.stream.synchronize()
+
+    def get_weights(self) -> np.ndarray:
+        out = np.empty(self.nparams, dtype=np.float32)
+        self._ck(self.lib.les_unet_get_weights(self.h, C.c_void_p(out.ctypes.data), 0), "get_weights")
+        return out
+
+    def forward(self, b):
+        """psi_0 for a (batch, n, n, n) or (n, n, n) tensor of right-hand sides."""
+        psi = self.torch.empty_like(b)
+        batch = b.numel() // self.n ** 3
+        prec = 64 if b.dtype == self.torch.float64 else 32
+        self._ck(self.lib.les_unet_forward(self.h, prec, C.c_void_p(b.data_ptr()), batch,
+                                           C.c_void_p(psi.data_ptr())), "forward")
+        return psi
+
+    def loss_grad(self, b, psi):
+        grad = self.torch.empty(self.nparams, dtype=self.torch.float32, device=self.device)
+        loss = C.c_double(0.0)
+        batch = b.numel() // self.n ** 3
+        prec = 64 if b.dtype == self.torch.float64 else 32
+        self._ck(self.lib.les_unet_loss_grad(self.h, prec, C.c_void_p(b.data_ptr()), C.c_void_p(psi.data_ptr()),
+                                             batch, C.byref(loss), C.c_void_p(grad.data_ptr())), "loss_grad")
+        return loss.value, grad
+
+    def train_step(self, b, psi, lr: float, want_loss: bool = True):
+        loss = C.c_double(0.0)
+        batch = b.numel() // self.n ** 3
+        prec = 64 if b.dtype == self.torch.float64 else 32
+        self._ck(self.lib.les_unet_train_step(self.h, prec, C.c_void_p(b.data_ptr()), C.c_void_p(psi.data_ptr()),
+                                              batch, float(lr), C.byref(loss) if want_loss else None),
+                 "train_step")
+        return loss.value if want_loss else None
+
+
+def attach_model(sim: "Simulation", model) -> None:
+    """Use `model` for LES_WARM_LEARNED solves of `sim` (None detaches)."""
+    rc = sim.lib.les_set_warm_model(sim.h, model.h if model is not None else None)
+    _check(sim.lib, sim.h, rc, "les_set_warm_model")
+    sim._model = model

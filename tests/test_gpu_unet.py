@@ -1,0 +1,143 @@
+"""Learned warm start: the library's BF16 tensor-core U-Net (through the C ABI)
+against the FP64 numpy oracle of the same network.
+
+Tolerances: activations and weights are BF16 (8-bit significand, relative
+rounding 2^-9 ~ 2e-3 per value) through 11 layers with FP32 accumulation, so
+the forward output is held to a few 1e-2 relative L2 and the gradients to a
+few 1e-2 relative L2 per layer.
+"""
+import numpy as np
+import pytest
+
+from oracle import unet_oracle as U
+from paper_2301_04698_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def les_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2301_04698_gb300 import build, les
+    build.build()
+    les.load_library()
+    return les
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def _smooth_field(n, seed, kmax=3):
+    """a random sum of low Fourier modes (a Poisson-like right side)"""
+    rng = np.random.default_rng(seed)
+    x = (np.arange(n) + 0.5) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    f = np.zeros((n, n, n))
+    for _ in range(6):
+        k = rng.integers(1, kmax + 1, size=3)
+        ph = rng.uniform(0, 2 * np.pi, size=3)
+        f += rng.standard_normal() * np.sin(2 * np.pi * k[0] * X + ph[0]) * np.sin(
+            2 * np.pi * k[1] * Y + ph[1]) * np.cos(2 * np.pi * k[2] * Z + ph[2])
+    return f + 0.05 * rng.standard_normal((n, n, n))
+
+
+@pytest.mark.parametrize("n,precision", [(8, 64), (16, 32), (16, 64)])
+def test_unet_forward_matches_oracle(les_mod, n, precision):
+    w = U.init_weights(7)
+    b = np.stack([_smooth_field(n, s) for s in (1, 2)])
+    model = les_mod.UNet(n, max_batch=2)
+    model.set_weights(w)
+    assert np.array_equal(model.get_weights(), w.astype(np.float32))
+    dt = torch.float64 if precision == 64 else torch.float32
+    psi = model.forward(torch.from_numpy(b).to("cuda", dt)).cpu().double().numpy()
+    for s in range(2):
+        ref = U.warm_start(w.astype(np.float32).astype(np.float64), b[s])
+        err = rel(psi[s], ref)
+        print(f"n={n} sample {s}: forward relative L2 {err:.3e}")
+        assert err < 3e-2
+        assert abs(psi[s].mean()) < 1e-5 * np.abs(psi[s]).max()
+
+
+def test_unet_gradients_match_oracle(les_mod):
+    n = 16
+    w = U.init_weights(11) + 0.02 * np.random.default_rng(0).standard_normal(U.n_params())
+    w32 = w.astype(np.float32).astype(np.float64)
+    b = np.stack([_smooth_field(n, s) for s in (3, 4)])
+    t = np.stack([_smooth_field(n, s + 10) for s in (3, 4)])
+    model = les_mod.UNet(n, max_batch=2)
+    model.set_weights(w32)
+    bt = torch.from_numpy(b).cuda()
+    tt = torch.from_numpy(t).cuda()
+    loss, grad = model.loss_grad(bt, tt)
+    grad = grad.cpu().double().numpy()
+    # oracle: mean over both samples of (y - t/s)^2 with per-sample scale s
+    P = U.unpack(w32)
+    gsum = np.zeros_like(w32)
+    lsum = 0.0
+    for s in range(2):
+        sc = np.sqrt(np.mean(b[s] ** 2))
+        y, cache = U.forward(P, (b[s] / sc)[None])
+        d = y - (t[s] / sc)[None]
+        lsum += float((d * d).sum())
+        g, _ = U.backward(P, cache, 2.0 * d / (2 * n ** 3))
+        gsum += g
+    lref = lsum / (2 * n ** 3)
+    print(f"loss gpu {loss:.6e} oracle {lref:.6e}")
+    assert abs(loss - lref) < 2e-2 * lref
+    off = 0
+    for name, ci, co, k in U.LAYERS:
+        nw = co * ci * k ** 3
+        ew = rel(grad[off:off + nw], gsum[off:off + nw])
+        eb = rel(grad[off + nw:off + nw + co], gsum[off + nw:off + nw + co])
+        print(f"{name}: weight grad rel L2 {ew:.3e}, bias grad rel L2 {eb:.3e}")
+        assert ew < 5e-2 and eb < 5e-2, name
+        off += nw + co
+    assert rel(grad, gsum) < 3e-2
+
+
+def test_unet_training_reduces_loss(les_mod):
+    n = 16
+    b = np.stack([_smooth_field(n, s) for s in range(4)])
+    # target: the exact periodic Poisson solution of each right side
+    k = 2 * np.pi * np.fft.fftfreq(n)
+    lam = -4 * n * n * (np.sin(k / 2)[:, None, None] ** 2 + np.sin(k / 2)[None, :, None] ** 2 +
+                        np.sin(k / 2)[None, None, :] ** 2)
+    lam[0, 0, 0] = 1.0
+    t = np.stack([np.real(np.fft.ifftn(np.fft.fftn(bb - bb.mean()) / lam * (lam != 1.0))) for bb in b])
+    model = les_mod.UNet(n, max_batch=4)
+    model.set_weights(U.init_weights(3))
+    bt = torch.from_numpy(b).float().cuda()
+    tt = torch.from_numpy(t).float().cuda()
+    l0 = model.train_step(bt, tt, 1e-3)
+    for _ in range(150):
+        l1 = model.train_step(bt, tt, 1e-3)
+    print(f"training loss {l0:.4e} -> {l1:.4e}")
+    assert l1 < 0.3 * l0
+
+
+def test_learned_warm_start_in_a_step(les_mod):
+    case = inputs.tgv(16, warm="learned", steps_tol=1e-8)
+    sim = les_mod.Simulation(case)
+    sim.set_state(inputs.initial_state(case))
+    with pytest.raises(les_mod.LesError) as e:
+        sim.step(1)
+    assert e.value.status == les_mod.LES_ERR_NO_MODEL
+    sim2 = les_mod.Simulation(case)
+    sim2.set_state(inputs.initial_state(case))
+    model = les_mod.UNet(16, max_batch=1)
+    model.set_weights(U.init_weights(2))
+    les_mod.attach_model(sim2, model)
+    st = sim2.step(2)
+    assert st["not_converged"] == 0 and st["solves"] == 2 * case.K
+    # same physics as a zero warm start to the solver tolerance
+    sim3 = les_mod.Simulation(case.replace(warm="zero"))
+    sim3.set_state(inputs.initial_state(case))
+    sim3.step(2)
+    for f in ("u", "v", "w"):
+        assert rel(sim2.get(f), sim3.get(f)) < 1e-6
+    small = les_mod.UNet(8, max_batch=1)
+    with pytest.raises(les_mod.LesError):
+        les_mod.attach_model(sim2, small)
