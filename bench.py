@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--workload", default="cbl128", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", default="auto", help="oracle sample: auto | full | NXxNY")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain Poisson leg")
+    ap.add_argument("--learned-seeds", type=int, default=20, help="training runs for the learned leg")
+    ap.add_argument("--learned-train-steps", type=int, default=1500)
     return ap.parse_args()
 
 
@@ -93,12 +96,12 @@ def barrier(world):
         dist.barrier()
 
 
-def allmax(world, x: float) -> float:
+def allmax(world, x: float, device: str = "cuda") -> float:
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -363,6 +366,24 @@ def main():
     e2e = {"value": world * case.n * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": les.NDIAG * 8}
 
+    # ---- Poisson ms/step at a fixed residual: learned vs plain first guesses ----
+    learned = None
+    if rank == 0 and not args.no_learned:
+        from paper_2301_04698_gb300 import learned as L
+        t0 = time.perf_counter()
+        B, P = L.generate_pairs(list(range(100, 100 + args.learned_seeds)), 50, n=32)
+        nval = 16
+        model = les.UNet(32, max_batch=16)
+        model.set_weights(L.init_weights(0))
+        model.out_scale = L.output_scale(B[nval:], P[nval:])
+        hist, t_train = L.train(model, B[nval:], P[nval:], steps=args.learned_train_steps, batch=16)
+        ev = L.evaluate(model, [1, 2], steps=10, n=32, tol=1e-6)
+        learned = {"workload": "Taylor-Green 32^3, FP64, K=3, CG to 1e-6 relative residual, held-out seeds 1-2",
+                   "pairs": int(B.shape[0]), "train_steps": args.learned_train_steps, "train_s": t_train,
+                   "leg_s": time.perf_counter() - t0, "val_rel_err": L.relative_error(model, B[:nval], P[:nval]),
+                   **ev}
+        del B, P, model
+
     # ---- CPU oracle baseline ---------------------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -387,7 +408,8 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
             "poisson": {"ms_per_step": stage_ms["solve"], "iters_per_step": iters / args.steps,
-                        "not_converged": nc, "warm_start": case.warm, "tol": case.tol},
+                        "not_converged": nc, "warm_start": case.warm, "tol": case.tol,
+                        "learned_vs_plain": learned},
             "stage_ms_per_step": stage_ms,
             "kernels": kernels,
             "wall_s_timed": wall,

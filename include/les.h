@@ -261,7 +261,8 @@ int les_poisson_solve_static(const les_config *cfg, const void *d_rho0, const vo
  * the shared-memory tiled predictors with nu_t computed in-tile, 1 the
  * direct-load predictors with nu_t stored between kernels (same results to
  * rounding).  A zero field in a set call keeps the current value (except
- * fault_missing_arrivals and stencil_path, which are always taken). */
+ * fault_missing_arrivals, stencil_path and cg_variant, which are always
+ * taken). */
 typedef struct les_tuning {
   uint32_t struct_size;            /* sizeof(les_tuning)                   */
   int32_t  cg_tile_rows;           /* 1, 2, 4 or 8                          */
@@ -270,6 +271,12 @@ typedef struct les_tuning {
   double   barrier_timeout_ms;     /* > 0                                   */
   int32_t  fault_missing_arrivals; /* 0 in production                      */
   int32_t  stencil_path;           /* 0 tiled (default), 1 direct-load      */
+  int32_t  cg_variant;             /* persistent CG: 0 standard CG (two grid
+                                      barriers per iteration, default), 1
+                                      Chronopoulos-Gear (one; its recurrences
+                                      drift in FP32 and may need more
+                                      iterations)                          */
+  int32_t  reserved0;
 } les_tuning;
 int les_get_tuning(les_handle *h, les_tuning *out);
 int les_set_tuning(les_handle *h, const les_tuning *in);
@@ -290,7 +297,10 @@ int les_set_tuning(les_handle *h, const les_tuning *in);
  * dec1b, head), each W[cout][cin][kz][ky][kx] followed by bias[cout].
  * The model borrows a caller-allocated device workspace like the solver.
  * b / psi arrays: device, batch * n^3 values of the given precision (32/64),
- * one sample after another, x fastest. */
+ * one sample after another, x fastest.  The output is scaled as
+ * psi_0 = s * out_scale * (y - mean y) and the training target is
+ * psi / (s * out_scale); out_scale (default 1) should be the typical ratio
+ * rms(psi) / rms(b) of the data so that the network works at unit scale. */
 typedef struct les_unet les_unet;
 int64_t les_unet_param_count(void);
 int les_unet_workspace_bytes(int32_t n, int32_t max_batch, size_t *bytes);
@@ -311,12 +321,15 @@ int les_unet_loss_grad(les_unet *u, int32_t precision, const void *d_b, const vo
 /* loss_grad followed by one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) */
 int les_unet_train_step(les_unet *u, int32_t precision, const void *d_b, const void *d_psi, int32_t batch,
                         float lr, double *loss);
+int les_unet_set_output_scale(les_unet *u, double out_scale);
+double les_unet_get_output_scale(const les_unet *u);
 const char *les_unet_last_error(const les_unet *u);
 /* Attach a model to a solver handle for LES_WARM_LEARNED (NULL detaches).
  * The model's grid must equal the handle's (nx = ny = nz = n); the handle
- * borrows the model until detached or destroyed.  If the model fails, the
- * solve falls back to a zero first guess and the step reports it in
- * les_last_error(). */
+ * borrows the model until detached or destroyed.  The plain solver is the
+ * fallback and the judge: if the model fails, or its guess leaves a larger
+ * residual than a zero guess (||b - A psi_0|| > ||b||), the solve starts
+ * from zero; every solve still iterates to the same relative residual. */
 int les_set_warm_model(les_handle *h, les_unet *u);
 
 /* ---- launch accounting and event profiling -------------------------------- */

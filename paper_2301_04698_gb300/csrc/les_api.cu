@@ -237,6 +237,11 @@ SolverArgs<T> solver_args(les_handle* h) {
   s.prof = &h->prof;
   s.bar = h->bar;
   s.fused = h->cfg.solver_path == 0 ? &h->fused : nullptr;
+  // the nu / u^{n+1/2} fields of the direct-load predictors are free during
+  // a solve and serve as the extra vectors of the one-barrier CG
+  s.e0 = (T*)h->fixed[B_NU];
+  s.e1 = (T*)h->fixed[B_UHALF];
+  s.e2 = (T*)h->fixed[B_VHALF];
   return s;
 }
 
@@ -386,6 +391,7 @@ int stage_solve(les_handle* h, les_step_stats* st) {
     if ((e = cudaMemsetAsync(psi, 0, bytes, h->st)) != cudaSuccess) return h->cuda_fail(e, "memset");
   }
   auto s = solver_args<T>(h);
+  s.guard = h->cfg.warm_start == LES_WARM_LEARNED ? 1 : 0;
   int iters = 0;
   double rel = 0;
   std::string err;
@@ -735,6 +741,7 @@ int les_get_tuning(les_handle* h, les_tuning* out) {
   out->barrier_timeout_ms = h->fused.timeout_ms;
   out->fault_missing_arrivals = h->fused.missing;
   out->stencil_path = h->fused.stencil_path;
+  out->cg_variant = h->fused.variant;
   return LES_OK;
 }
 
@@ -759,6 +766,8 @@ int les_set_tuning(les_handle* h, const les_tuning* in) {
   h->fused.missing = in->fault_missing_arrivals;
   if (in->stencil_path != 0 && in->stencil_path != 1) return h->fail(LES_ERR_INVALID_ARG, "stencil_path must be 0 or 1");
   h->fused.stencil_path = in->stencil_path;
+  if (in->cg_variant != 0 && in->cg_variant != 1) return h->fail(LES_ERR_INVALID_ARG, "cg_variant must be 0 or 1");
+  h->fused.variant = in->cg_variant;
   return LES_OK;
 }
 

@@ -92,6 +92,7 @@ struct FusedCfg {
   double timeout_ms = 2000.0;
   int missing = 0;                      // test hook: arrivals that never come
   int stencil_path = 0;                 // 0 tiled predictors, 1 direct-load predictors
+  int variant = 0;                      // 0 standard CG (2 barriers / iteration), 1 Chronopoulos-Gear (1)
 };
 
 struct LaunchCfg {
@@ -256,6 +257,10 @@ struct SolverArgs {
   T* q;
   Profiler* prof;
   FusedBar* bar = nullptr;          // persistent-solver barrier (workspace)
+  int guard = 0;                    // restart from x = 0 if ||b - A x0|| > ||b|| (learned guesses)
+  T* e0 = nullptr;                  // extra vectors for the one-barrier variant
+  T* e1 = nullptr;
+  T* e2 = nullptr;
   const FusedCfg* fused = nullptr;  // enables the persistent CG when eligible
 };
 

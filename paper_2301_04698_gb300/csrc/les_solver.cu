@@ -146,6 +146,30 @@ __global__ void __launch_bounds__(NTHREADS) k_init(Grid<T> g, int op, const T* _
   }
 }
 
+// a learned first guess that leaves a larger residual than zero is dropped:
+// x = 0, r = b - mean b (decided on the device from the init reduction)
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_guard(Grid<T> g, const T* __restrict__ b, T* __restrict__ x,
+                                                    T* __restrict__ r, SolverCtl* ctl) {
+  if (ctl->done || !(ctl->rr > ctl->bn2)) return;
+  const T mean = (T)ctl->scal;
+  for (long long t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+    int i, j, k0, k1;
+    tile_origin(g, t, i, j, k0, k1);
+    if (i >= g.nx || j >= g.ny) continue;
+    for (int k = k0; k < k1; ++k) {
+      const size_t m = g.lin(i, j, k);
+      x[m] = T(0);
+      r[m] = b[m] - mean;
+    }
+  }
+}
+__global__ void k_guard_fix(SolverCtl* ctl) {
+  if (ctl->done || !(ctl->rr > ctl->bn2)) return;
+  ctl->rr = ctl->bn2;
+  ctl->rel = 1.0;
+}
+
 // CG, part 1: p_new = r + beta p_old (at all stencil nodes), q = A p_new, p_new.q
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS) k_cg_matvec(Grid<T> g, int op, const T* __restrict__ rho0,
@@ -297,6 +321,10 @@ int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxi
   {
     ProfScope ps(a.prof, KI_CG_INIT, a.st);
     k_init<T><<<G, B, 0, a.st>>>(a.g, a.op, a.rho0, b, x, a.r, a.partials, a.ctl);
+  }
+  if (a.guard && a.solver == LES_SOLVER_CG) {
+    k_guard<T><<<G, B, 0, a.st>>>(a.g, b, x, a.r, a.ctl);
+    k_guard_fix<<<1, 1, 0, a.st>>>(a.ctl);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "poisson init");
   T* pbuf[2] = {a.p0, a.p1};

@@ -356,8 +356,8 @@ __global__ void k_scale(const double* part, int nblk, long long n3, int batch, d
 }
 // x0[v][0] = b / s, other 15 channels 0; optional normalised target t = psi / s
 template <typename T>
-__global__ void k_pack(const T* b, const T* psi, long long n3, int batch, const double* scale, bf16* x0,
-                       float* tgt) {
+__global__ void k_pack(const T* b, const T* psi, long long n3, int batch, const double* scale, double out_scale,
+                       bf16* x0, float* tgt) {
   const long long total = (long long)batch * n3;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const int s = (int)(i / n3);
@@ -369,7 +369,7 @@ __global__ void k_pack(const T* b, const T* psi, long long n3, int batch, const 
     o[0] = lo;
 #pragma unroll
     for (int q = 1; q < 8; ++q) o[q] = z;
-    if (tgt) tgt[i] = (float)((double)psi[i] * inv);
+    if (tgt) tgt[i] = (float)((double)psi[i] * inv / out_scale);
   }
 }
 // MSE over batch x n3 of y (channel 0 of [.][8] FP32) vs t; gy = 2 (y - t) / count
@@ -408,11 +408,12 @@ __global__ void k_ymean(const float* y, long long n3, double* out) {
 }
 // psi_0 = s (y - mean y)
 template <typename T>
-__global__ void k_unpack(const float* y, long long n3, int batch, const double* scale, const double* ymean, T* psi) {
+__global__ void k_unpack(const float* y, long long n3, int batch, const double* scale, double out_scale,
+                         const double* ymean, T* psi) {
   const long long total = (long long)batch * n3;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const int s = (int)(i / n3);
-    psi[i] = (T)(scale[s] * ((double)y[(size_t)i * 8] - ymean[s]));
+    psi[i] = (T)(scale[s] * out_scale * ((double)y[(size_t)i * 8] - ymean[s]));
   }
 }
 
@@ -474,6 +475,7 @@ struct les_unet {
   size_t wpart_floats = 0;
   double *scale, *ymean, *dpart, *loss;
   int step = 0;
+  double out_scale = 1.0;  // psi_0 = s * out_scale * (y - mean y)
   std::string err;
   Profiler* prof = nullptr;
 };
@@ -702,7 +704,8 @@ cudaError_t pack_inputs(les_unet* u, const T* b, const T* psi, int batch) {
   const int nblk = 64;
   k_sumsq<T><<<dim3(nblk, batch), 256, 0, u->st>>>(b, n3, u->dpart);
   k_scale<<<1, 64, 0, u->st>>>(u->dpart, nblk, n3, batch, u->scale);
-  k_pack<T><<<eblocks(batch * n3), 256, 0, u->st>>>(b, psi, n3, batch, u->scale, u->x0, psi ? u->tgt : nullptr);
+  k_pack<T><<<eblocks(batch * n3), 256, 0, u->st>>>(b, psi, n3, batch, u->scale, u->out_scale, u->x0,
+                                                     psi ? u->tgt : nullptr);
   return cudaGetLastError();
 }
 
@@ -713,7 +716,7 @@ int run_forward(les_unet* u, const T* b, int batch, T* psi0) {
   if ((e = forward(u, batch)) != cudaSuccess) return unet_fail(u, e, "forward");
   const long long n3 = (long long)u->n * u->n * u->n;
   k_ymean<<<batch, 256, 0, u->st>>>(u->y, n3, u->ymean);
-  k_unpack<T><<<eblocks(batch * n3), 256, 0, u->st>>>(u->y, n3, batch, u->scale, u->ymean, psi0);
+  k_unpack<T><<<eblocks(batch * n3), 256, 0, u->st>>>(u->y, n3, batch, u->scale, u->out_scale, u->ymean, psi0);
   e = cudaGetLastError();
   return e == cudaSuccess ? LES_OK : unet_fail(u, e, "unpack");
 }
@@ -860,6 +863,14 @@ int les_unet_train_step(les_unet* u, int32_t precision, const void* d_b, const v
   cudaError_t e = refresh_weights(u);
   return e == cudaSuccess ? LES_OK : unet_fail(u, e, "adam");
 }
+
+int les_unet_set_output_scale(les_unet* u, double scale) {
+  if (!u || !(scale > 0) || !std::isfinite(scale)) return LES_ERR_INVALID_ARG;
+  u->out_scale = scale;
+  return LES_OK;
+}
+
+double les_unet_get_output_scale(const les_unet* u) { return u ? u->out_scale : 0.0; }
 
 const char* les_unet_last_error(const les_unet* u) { return u ? u->err.c_str() : "no model"; }
 

@@ -43,7 +43,7 @@ EXPORTED = ("les_config_default", "les_workspace_bytes", "les_init", "les_destro
             "les_set_tuning", "les_unet_param_count", "les_unet_workspace_bytes", "les_unet_create",
             "les_unet_destroy", "les_unet_set_stream", "les_unet_set_weights", "les_unet_get_weights",
             "les_unet_forward", "les_unet_loss_grad", "les_unet_train_step", "les_unet_last_error",
-            "les_set_warm_model")
+            "les_set_warm_model", "les_unet_set_output_scale", "les_unet_get_output_scale")
 
 
 class LesConfig(C.Structure):
@@ -83,7 +83,8 @@ class LesKernelStat(C.Structure):
 class LesTuning(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("cg_tile_rows", C.c_int32), ("cg_tile_planes", C.c_int32),
                 ("cg_max_blocks", C.c_int32), ("barrier_timeout_ms", C.c_double),
-                ("fault_missing_arrivals", C.c_int32), ("stencil_path", C.c_int32)]
+                ("fault_missing_arrivals", C.c_int32), ("stencil_path", C.c_int32), ("cg_variant", C.c_int32),
+                ("reserved0", C.c_int32)]
 
 
 class LesError(RuntimeError):
@@ -175,6 +176,10 @@ def load_library(path: str = LIB_PATH):
     lib.les_unet_train_step.argtypes = [vp, i32, vp, vp, i32, C.c_float, C.POINTER(dbl)]
     lib.les_unet_last_error.restype = C.c_char_p
     lib.les_unet_last_error.argtypes = [vp]
+    lib.les_unet_set_output_scale.restype = C.c_int
+    lib.les_unet_set_output_scale.argtypes = [vp, dbl]
+    lib.les_unet_get_output_scale.restype = dbl
+    lib.les_unet_get_output_scale.argtypes = [vp]
     lib.les_set_warm_model.restype = C.c_int
     lib.les_set_warm_model.argtypes = [vp, vp]
     lib.les_poisson_solve_static.restype = C.c_int
@@ -363,12 +368,14 @@ class Simulation:
     def tuning(self) -> dict:
         t = LesTuning()
         _check(self.lib, self.h, self.lib.les_get_tuning(self.h, C.byref(t)), "get tuning")
-        return {k: getattr(t, k) for k, _ in t._fields_ if k != "struct_size"}
+        return {k: getattr(t, k) for k, _ in t._fields_ if k not in ("struct_size", "reserved0")}
 
     def set_tuning(self, **kw) -> None:
         t = LesTuning()
         t.struct_size = C.sizeof(LesTuning)
-        t.stencil_path = self.tuning()["stencil_path"]
+        cur = self.tuning()
+        t.stencil_path = cur["stencil_path"]
+        t.cg_variant = cur["cg_variant"]
         for k, v in kw.items():
             setattr(t, k, v)
         _check(self.lib, self.h, self.lib.les_set_tuning(self.h, C.byref(t)), "set tuning")
@@ -426,6 +433,14 @@ class UNet:
         assert wt.numel() == self.nparams
         self._ck(self.lib.les_unet_set_weights(self.h, C.c_void_p(wt.data_ptr()), 1), "set_weights")
         self.stream.synchronize()
+
+    @property
+    def out_scale(self) -> float:
+        return float(self.lib.les_unet_get_output_scale(self.h))
+
+    @out_scale.setter
+    def out_scale(self, v: float) -> None:
+        self._ck(self.lib.les_unet_set_output_scale(self.h, float(v)), "set_output_scale")
 
     def get_weights(self) -> np.ndarray:
         out = np.empty(self.nparams, dtype=np.float32)

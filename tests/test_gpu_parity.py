@@ -315,10 +315,10 @@ def test_fused_cg_matches_oracle(les_mod, precision, walls, shape):
     tol = 1e-11 if precision == 64 else 1e-6
     bt = torch.from_numpy(b).to("cuda", dt)
     results = []
-    for ty, zc in ((4, 4), (1, 1), (2, 3), (8, 16)):
+    for variant, ty, zc in ((1, 4, 4), (1, 1, 1), (1, 2, 3), (1, 8, 16), (0, 4, 4), (0, 2, 3)):
         if ny % ty:
             continue
-        sim.set_tuning(cg_tile_rows=ty, cg_tile_planes=zc)
+        sim.set_tuning(cg_tile_rows=ty, cg_tile_planes=zc, cg_variant=variant)
         sim.profile_reset()
         x = torch.zeros_like(bt)
         rc, it, res = sim.poisson_solve(bt, x, tol, 20000)
@@ -327,17 +327,20 @@ def test_fused_cg_matches_oracle(les_mod, precision, walls, shape):
         xn = x.cpu().double().numpy()
         # zero-mean gauge, to rounding of the field's magnitude
         assert abs(xn.mean()) < (1e-14 if precision == 64 else 1e-6) * np.abs(xn).max()
-        assert rel(xn, xr) < (1e-8 if precision == 64 else 5e-4), (ty, zc)
-        results.append((it, xn))
+        assert rel(xn, xr) < (1e-8 if precision == 64 else 5e-4), (variant, ty, zc)
+        results.append((variant, it, xn))
     # the per-phase launch path reaches the same solution
     case1 = case.replace(solver_path=1)
     sim1 = les_mod.Simulation(case1)
     x1 = torch.zeros_like(bt)
     rc, it1, res1 = sim1.poisson_solve(bt, x1, tol, 20000)
     assert _fused_launches(sim1) == 0
-    for it, xn in results:
-        assert abs(it - it1) <= 2
-        assert rel(xn, x1.cpu().double().numpy()) < (1e-9 if precision == 64 else 2e-5)
+    for variant, it, xn in results:
+        # standard CG follows the same iterates; the one-barrier variant keeps
+        # s = A p and w = A r by recurrence, which drifts in FP32
+        if variant == 0 or precision == 64:
+            assert abs(it - it1) <= 3, (variant, it, it1)
+        assert rel(xn, x1.cpu().double().numpy()) < (1e-9 if precision == 64 else 5e-4)
 
 
 def test_fused_cg_barrier_timeout_is_reported(les_mod):
