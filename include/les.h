@@ -257,12 +257,19 @@ int les_poisson_solve_static(const les_config *cfg, const void *d_rho0, const vo
  * after barrier_timeout_ms; the solve then returns LES_ERR_TIMEOUT and the
  * device stays usable.  fault_missing_arrivals is a failure-detection test
  * hook: the barrier then waits for that many blocks that never arrive, so
- * every wait runs out; it must be 0 otherwise.  stencil_path 0 (default) runs
- * the shared-memory tiled predictors with nu_t computed in-tile, 1 the
- * direct-load predictors with nu_t stored between kernels (same results to
- * rounding).  A zero field in a set call keeps the current value (except
- * fault_missing_arrivals, stencil_path and cg_variant, which are always
- * taken). */
+ * every wait runs out; it must be 0 otherwise.  stencil_path selects the
+ * predictor kernels (same results to rounding): 0 (default) both
+ * predictors as rolling z-marches through shared-memory plane rings; 1
+ * direct-load kernels with nu_t stored between kernels; 2 both predictors in
+ * shared-memory 3-D tiles.  Paths 0 and 2 compute nu_t in place.  With
+ * cg_resident = 0 the standard CG solve first tries a decomposition of the
+ * grid into one brick per thread block (x extent 32, 64 or 128 dividing nx,
+ * y and z extents dividing ny and nz, at most one block per SM, x, r and p
+ * of a brick within the per-block shared memory); the blocks then exchange
+ * only brick faces through global memory, and cg_tile_rows and
+ * cg_tile_planes do not apply.  A zero field in a set call keeps the
+ * current value (except fault_missing_arrivals, stencil_path, cg_variant and
+ * cg_resident, which are always taken). */
 typedef struct les_tuning {
   uint32_t struct_size;            /* sizeof(les_tuning)                   */
   int32_t  cg_tile_rows;           /* 1, 2, 4 or 8                          */
@@ -270,13 +277,16 @@ typedef struct les_tuning {
   int32_t  cg_max_blocks;          /* >= 1                                  */
   double   barrier_timeout_ms;     /* > 0                                   */
   int32_t  fault_missing_arrivals; /* 0 in production                      */
-  int32_t  stencil_path;           /* 0 tiled (default), 1 direct-load      */
+  int32_t  stencil_path;           /* 0 rolling (default), 1 direct, 2 tiled */
   int32_t  cg_variant;             /* persistent CG: 0 standard CG (two grid
                                       barriers per iteration, default), 1
                                       Chronopoulos-Gear (one; its recurrences
                                       drift in FP32 and may need more
                                       iterations)                          */
-  int32_t  reserved0;
+  int32_t  cg_resident;            /* 0 (default): standard CG keeps its
+                                      vectors in shared memory when the grid
+                                      fits there; 1: always streams them
+                                      through global memory                */
 } les_tuning;
 int les_get_tuning(les_handle *h, les_tuning *out);
 int les_set_tuning(les_handle *h, const les_tuning *in);

@@ -270,6 +270,7 @@ int fields_per_cell(const les_config& c, int id) {
     case KI_JACOBI: return 3;
     case KI_FINISH: return 2;
     case KI_CG_FUSED: return 0;  // varies with the iteration count
+    case KI_CG_RESIDENT: return 0;
     default: return 0;
   }
 }
@@ -330,6 +331,10 @@ int stage_scalar(les_handle* h) {
   const int ti = h->cur ? B_THB : B_THA, qi = h->cur ? B_QTB : B_QTA;
   const int to = h->cur ? B_THA : B_THB, qo = h->cur ? B_QTA : B_QTB;
   if (h->fused.stencil_path == 0) {
+    if ((e = launch_scalar_roll<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_B], F[ti], F[qi], F[B_THH],
+                                   F[B_QTH], F[B_SRAD], F[to], F[qo])) != cudaSuccess)
+      return h->cuda_fail(e, "scalar predictor");
+  } else if (h->fused.stencil_path == 2) {
     if ((e = launch_scalar_tiled<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_B], F[ti], F[qi], F[B_THH],
                                     F[B_QTH], F[B_SRAD], F[to], F[qo])) != cudaSuccess)
       return h->cuda_fail(e, "scalar predictor");
@@ -351,6 +356,10 @@ int stage_momentum(les_handle* h) {
   cudaError_t e;
   T* const* F = (T* const*)h->fixed;
   if (h->fused.stencil_path == 0) {
+    if ((e = launch_momentum_roll<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_UN], F[B_VN], F[B_WN],
+                                     F[B_P], F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess)
+      return h->cuda_fail(e, "momentum predictor");
+  } else if (h->fused.stencil_path == 2) {
     if ((e = launch_momentum_tiled<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_UN], F[B_VN], F[B_WN],
                                       F[B_P], F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess)
       return h->cuda_fail(e, "momentum predictor");
@@ -465,7 +474,7 @@ namespace les {
 const char* const kKernelNames[KI_COUNT] = {
     "thermo", "radiation", "nu", "nu_half", "scalar", "momentum", "rhs", "correct", "diag",
     "cfl", "apply", "sum", "cg_init", "cg_matvec", "cg_update", "jacobi", "finish", "ctl", "cg_fused",
-    "unet_conv", "unet_wgrad", "unet_adam"};
+    "unet_conv", "unet_wgrad", "unet_adam", "cg_resident"};
 
 template <typename T>
 Grid<T> make_grid(const les_config& c, int zc) {
@@ -742,6 +751,7 @@ int les_get_tuning(les_handle* h, les_tuning* out) {
   out->fault_missing_arrivals = h->fused.missing;
   out->stencil_path = h->fused.stencil_path;
   out->cg_variant = h->fused.variant;
+  out->cg_resident = h->fused.resident;
   return LES_OK;
 }
 
@@ -764,10 +774,13 @@ int les_set_tuning(les_handle* h, const les_tuning* in) {
     h->fused.spin_cycles = (long long)(in->barrier_timeout_ms * (double)khz);
   }
   h->fused.missing = in->fault_missing_arrivals;
-  if (in->stencil_path != 0 && in->stencil_path != 1) return h->fail(LES_ERR_INVALID_ARG, "stencil_path must be 0 or 1");
+  if (in->stencil_path < 0 || in->stencil_path > 2)
+    return h->fail(LES_ERR_INVALID_ARG, "stencil_path must be 0, 1 or 2");
   h->fused.stencil_path = in->stencil_path;
   if (in->cg_variant != 0 && in->cg_variant != 1) return h->fail(LES_ERR_INVALID_ARG, "cg_variant must be 0 or 1");
   h->fused.variant = in->cg_variant;
+  if (in->cg_resident != 0 && in->cg_resident != 1) return h->fail(LES_ERR_INVALID_ARG, "cg_resident must be 0 or 1");
+  h->fused.resident = in->cg_resident;
   return LES_OK;
 }
 

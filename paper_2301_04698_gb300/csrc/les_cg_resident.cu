@@ -1,0 +1,482 @@
+// les_cg_resident.cu -- the conjugate-gradient Poisson solve with its
+// vectors resident in shared memory (Sec. 2.4: L_c psi = b, compact 7-point
+// Laplacian, periodic in x, y, mirror or periodic in z; mean of b removed,
+// psi returned with zero mean).
+//
+// When the whole grid fits in the GPU's shared memory (a 128 x 128 x 96 FP32
+// grid needs about 21 MB of the 34 MB on 152 SMs), every iteration of the
+// streaming solver is dominated by the latency of its passes through L2, not
+// by their bytes.  Here each block of one persistent cooperative launch owns
+// a brick of bx x by x bz nodes for the whole solve and keeps x, r and p of
+// its brick (p with a one-node ghost layer) in shared memory.  The only
+// global traffic of an iteration is the exchange of brick faces:
+//   phase A  p = r + beta p in place; the ghost layer is filled from the
+//            neighbours' published faces of r (this iteration) and p (the
+//            previous one, double-buffered by parity) as r + beta p_old, so
+//            no barrier separates the p update from the matvec; p faces
+//            published; q = L_c p; p.q
+//   phase B  q = L_c p again (recomputed, not stored); x += alpha p,
+//            r -= alpha q; r faces published; r.r
+// each followed by a grid-wide FP64 sum (les_gridsync.cuh).  Dot products
+// are formed in T over at most eight terms per thread and then accumulated
+// in FP64.  Ghost loads are issued in batches so that each costs one round
+// of memory latency.
+#include <algorithm>
+#include <string>
+
+#include "les_gridsync.cuh"
+#include "les_internal.h"
+
+namespace les {
+namespace {
+
+constexpr int kResThreads = 512;
+
+template <typename T>
+struct ResArgs {
+  int nx, ny, nz, walls;
+  T cx, cy, cz;      // 1/dx^2, 1/dy^2, 1/dz^2
+  int by, bz;        // brick extent in y and z (x extent: the template BX)
+  int px, py;        // bricks along x and y
+  long long n;
+  const T* b;
+  T* x;
+  T* rg;             // published faces of r
+  T* pg0;            // published faces of p, even iterations
+  T* pg1;            // ... odd iterations
+  double* partials;  // [4][gridDim.x]
+  FusedBar* bar;
+  SolverCtl* ctl;
+  double tol;
+  int maxit;
+  long long spin_cycles;
+  unsigned expected;
+  int guard;
+};
+
+// FP64 sum of products formed in T: float terms are summed in float in
+// groups of eight before entering the FP64 accumulator
+template <typename T>
+struct Acc;
+template <>
+struct Acc<float> {
+  double d = 0.0;
+  float f = 0.f;
+  int n = 0;
+  __device__ __forceinline__ void add(float v) {
+    f += v;
+    if (++n == 8) {
+      d += (double)f;
+      f = 0.f;
+      n = 0;
+    }
+  }
+  __device__ __forceinline__ double total() const { return d + (double)f; }
+};
+template <>
+struct Acc<double> {
+  double d = 0.0;
+  __device__ __forceinline__ void add(double v) { d += v; }
+  __device__ __forceinline__ double total() const { return d; }
+};
+
+__device__ __forceinline__ int zghost(int k, int nz, int walls) {
+  if (walls) return k < 0 ? -1 - k : (k >= nz ? 2 * nz - 1 - k : k);
+  return k < 0 ? k + nz : (k >= nz ? k - nz : k);
+}
+
+template <typename T, int BX>
+__global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
+  constexpr int L = BX / 32;  // nodes per lane along a brick row
+  constexpr int RB = 3;       // ghost rows per warp whose loads are in flight together
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int by = f.by, bz = f.bz;
+  const int SY = BX + 2, SZ = (BX + 2) * (by + 2);  // strides of the haloed p brick
+  const int nrow = by * bz;
+  const int bcells = BX * nrow;
+  T* P = reinterpret_cast<T*>(smraw);  // (BX + 2)(by + 2)(bz + 2)
+  T* R = P + SZ * (bz + 2);            // BX by bz
+  T* X = R + bcells;                   // BX by bz
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+  const int bi = blockIdx.x % f.px, bj = (blockIdx.x / f.px) % f.py, bk = blockIdx.x / (f.px * f.py);
+  const int i0 = bi * BX, j0 = bj * by, k0 = bk * bz;
+  const T cx = f.cx, cy = f.cy, cz = f.cz;
+
+  // global index of local node (lx, ly, lz), at most one node outside the brick
+  auto gidx = [&](int lx, int ly, int lz) -> size_t {
+    int i = i0 + lx, j = j0 + ly;
+    i = i < 0 ? i + f.nx : (i >= f.nx ? i - f.nx : i);
+    j = j < 0 ? j + f.ny : (j >= f.ny ? j - f.ny : j);
+    const int k = zghost(k0 + lz, f.nz, f.walls);
+    return ((size_t)k * f.ny + j) * f.nx + i;
+  };
+  // second differences formed before scaling: for smooth p they are small
+  // differences of nearly equal values, exact in floating point
+  auto Lc = [&](int pi) -> T {
+    const T c2 = T(2) * P[pi];
+    return (P[pi - 1] + P[pi + 1] - c2) * cx + (P[pi - SY] + P[pi + SY] - c2) * cy +
+           (P[pi - SZ] + P[pi + SZ] - c2) * cz;
+  };
+  // body(c, pi, g, face) for every owned node: c its index in R / X, pi in P,
+  // g in global memory; face: the node lies on the brick surface
+  auto own = [&](auto&& body) {
+    for (int row = warp; row < nrow; row += nwarp) {
+      const int ly = row % by, lz = row / by;
+      const bool rface = ly == 0 || ly == by - 1 || lz == 0 || lz == bz - 1;
+      const size_t grow = ((size_t)(k0 + lz) * f.ny + (j0 + ly)) * f.nx + i0;
+      const int prow = (lz + 1) * SZ + (ly + 1) * SY + 1;
+#pragma unroll
+      for (int u = 0; u < L; ++u) {
+        const int lx = lane + 32 * u;
+        body(row * BX + lx, prow + lx, grow + lx, rface || lx == 0 || lx == BX - 1);
+      }
+    }
+  };
+  // fill the ghost layer of P: val(g) for each face-neighbour node outside
+  // the brick (edges and corners are not used by the 7-point stencil)
+  auto ghosts = [&](auto&& val) {
+    // rows along x: the two z faces (2 by rows), then the two y faces (2 bz rows)
+    const int nr = 2 * by + 2 * bz;
+    for (int r0 = warp; r0 < nr; r0 += RB * nwarp) {
+      T v[RB][L];
+      int pr[RB];
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        const int row = r0 + q * nwarp;
+        pr[q] = -1;
+        if (row < nr) {
+          int ly, lz;
+          if (row < 2 * by) {
+            ly = row >> 1;
+            lz = (row & 1) ? bz : -1;
+          } else {
+            lz = (row - 2 * by) >> 1;
+            ly = (row & 1) ? by : -1;
+          }
+          pr[q] = (lz + 1) * SZ + (ly + 1) * SY + 1;
+          const size_t g0 = gidx(0, ly, lz);
+#pragma unroll
+          for (int u = 0; u < L; ++u) v[q][u] = val(g0 + lane + 32 * u);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < RB; ++q)
+        if (pr[q] >= 0)
+#pragma unroll
+          for (int u = 0; u < L; ++u) P[pr[q] + lane + 32 * u] = v[q][u];
+    }
+    // the two x faces: strided single nodes
+    constexpr int XB = 4;
+    for (int c0 = tid; c0 < 2 * nrow; c0 += XB * nthr) {
+      T v[XB];
+      int pi[XB];
+#pragma unroll
+      for (int q = 0; q < XB; ++q) {
+        const int c = c0 + q * nthr;
+        pi[q] = -1;
+        if (c < 2 * nrow) {
+          const int row = c >> 1, ly = row % by, lz = row / by, lx = (c & 1) ? BX : -1;
+          pi[q] = (lz + 1) * SZ + (ly + 1) * SY + 1 + lx;
+          v[q] = val(gidx(lx, ly, lz));
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < XB; ++q)
+        if (pi[q] >= 0) P[pi[q]] = v[q];
+    }
+  };
+
+  int status = 0;  // 0 running, 1 converged, 2 maxit, 3 breakdown, 4 zero rhs, 5 timeout
+  // mean of b; b staged in R
+  Acc<T> a1;
+  own([&](int c, int, size_t g, bool) {
+    const T v = __ldcg(f.b + g);
+    R[c] = v;
+    a1.add(v);
+  });
+  double s1[1] = {a1.total()};
+  if (!grid_sum<1>(s1, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+  const T mean = (T)(s1[0] / (double)f.n);
+
+  // x0 with its ghosts; r = (b - mean) - L_c x0, published; r.r and |b - mean|^2
+  double s2[2] = {0.0, 0.0};
+  if (!status) {
+    own([&](int c, int pi, size_t g, bool) {
+      const T v = __ldcg(f.x + g);
+      X[c] = v;
+      P[pi] = v;
+    });
+    ghosts([&](size_t g) { return __ldcg(f.x + g); });
+    __syncthreads();
+    Acc<T> arr, abb;
+    own([&](int c, int pi, size_t g, bool face) {
+      const T bm = R[c] - mean;
+      const T rv = bm - Lc(pi);
+      R[c] = rv;
+      if (face) __stcg(f.rg + g, rv);
+      arr.add(rv * rv);
+      abb.add(bm * bm);
+    });
+    s2[0] = arr.total();
+    s2[1] = abb.total();
+    if (!grid_sum<2>(s2, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+  }
+  // the plain solver judges a learned first guess: if it leaves a larger
+  // residual than x0 = 0, restart from zero (r = b - mean b, r.r = |b|^2)
+  if (!status && f.guard && s2[0] > s2[1]) {
+    own([&](int c, int, size_t g, bool face) {
+      const T rv = __ldcg(f.b + g) - mean;
+      X[c] = T(0);
+      R[c] = rv;
+      if (face) __stcg(f.rg + g, rv);
+    });
+    double sz[1] = {0.0};
+    if (!grid_sum<1>(sz, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+    s2[0] = s2[1];
+  }
+  double rr = s2[0];
+  const double bb = s2[1];
+  double rel = 0.0;
+  if (!status) {
+    if (bb == 0.0) status = 4;
+    else {
+      rel = sqrt(rr / bb);
+      if (rel <= f.tol) status = 1;
+      else if (f.maxit <= 0) status = 2;
+    }
+  }
+
+  int iter = 0;
+  double beta = 0.0;
+  while (!status) {
+    const bool first = iter == 0;
+    const T tb = (T)beta;
+    T* pw = (iter & 1) ? f.pg1 : f.pg0;         // this iteration's p faces
+    const T* po = (iter & 1) ? f.pg0 : f.pg1;   // the previous iteration's
+    // phase A: p = r + beta p (owned in place, ghosts from published faces)
+    own([&](int c, int pi, size_t g, bool face) {
+      const T pv = first ? R[c] : R[c] + tb * P[pi];
+      P[pi] = pv;
+      if (face) __stcg(pw + g, pv);
+    });
+    if (first) ghosts([&](size_t g) { return __ldcg(f.rg + g); });
+    else ghosts([&](size_t g) { return __ldcg(f.rg + g) + tb * __ldcg(po + g); });
+    __syncthreads();
+    Acc<T> apq;
+    own([&](int, int pi, size_t, bool) { apq.add(P[pi] * Lc(pi)); });
+    double sa[1] = {apq.total()};
+    if (!grid_sum<1>(sa, f.bar, f.partials, f.spin_cycles, f.expected)) {
+      status = 5;
+      break;
+    }
+    const double pq = sa[0];
+    if (pq == 0.0 || !isfinite(pq)) {
+      status = 3;
+      break;
+    }
+    const double alpha = rr / pq;
+    const T ta = (T)alpha;
+    // phase B: x += alpha p, r -= alpha L_c p, r faces published, r.r
+    Acc<T> ar;
+    own([&](int c, int pi, size_t g, bool face) {
+      const T pv = P[pi];
+      X[c] += ta * pv;
+      const T rv = R[c] - ta * Lc(pi);
+      R[c] = rv;
+      if (face) __stcg(f.rg + g, rv);
+      ar.add(rv * rv);
+    });
+    double sb[1] = {ar.total()};
+    if (!grid_sum<1>(sb, f.bar, f.partials, f.spin_cycles, f.expected)) {
+      status = 5;
+      break;
+    }
+    const double rr_new = sb[0];
+    iter += 1;
+    rel = sqrt(rr_new / bb);
+    beta = rr_new / rr;
+    rr = rr_new;
+    if (rel <= f.tol) status = 1;
+    else if (iter >= f.maxit) status = 2;
+    else if (!isfinite(rr_new)) status = 3;
+  }
+
+  // zero-mean gauge (or zero for a zero right side), written back to x
+  if (status != 5) {
+    Acc<T> ax;
+    own([&](int c, int, size_t, bool) { ax.add(X[c]); });
+    double sx[1] = {ax.total()};
+    if (!grid_sum<1>(sx, f.bar, f.partials, f.spin_cycles, f.expected)) {
+      status = 5;
+    } else {
+      const T mx = (T)(sx[0] / (double)f.n);
+      own([&](int c, int, size_t g, bool) { __stcg(f.x + g, status == 4 ? T(0) : X[c] - mx); });
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    f.ctl->iter = iter;
+    f.ctl->rel = rel;
+    f.ctl->done = status;
+  }
+}
+
+struct Plan {
+  int bx = 0, by = 0, bz = 0, px = 0, py = 0, pz = 0;
+  size_t smem = 0;
+};
+
+template <typename T>
+size_t resident_smem(int bx, int by, int bz) {
+  return ((size_t)(bx + 2) * (by + 2) * (bz + 2) + 2 * (size_t)bx * by * bz) * sizeof(T);
+}
+
+// Brick decomposition: bx in {128, 64, 32} dividing nx, by | ny, bz | nz,
+// at most one brick per SM and within the per-block shared memory; among
+// those the one with the least work per block (owned nodes + ghost nodes +
+// a per-block barrier cost).
+template <typename T>
+bool make_plan(const Grid<T>& g, int nsm, size_t smem_max, int max_blocks, Plan& best) {
+  long long best_score = -1;
+  const int gmax = std::min(nsm, max_blocks);
+  for (int bx : {128, 64, 32}) {
+    if (g.nx % bx) continue;
+    for (int by = 1; by <= g.ny; ++by) {
+      if (g.ny % by) continue;
+      for (int bz = 1; bz <= g.nz; ++bz) {
+        if (g.nz % bz) continue;
+        const long long G = (long long)(g.nx / bx) * (g.ny / by) * (g.nz / bz);
+        if (G > gmax) continue;
+        const size_t smem = resident_smem<T>(bx, by, bz);
+        if (smem > smem_max) continue;
+        const long long cells = (long long)bx * by * bz;
+        // x-face ghosts are strided single nodes: weighted as four
+        const long long ghosts = 2LL * bx * by + 2LL * bx * bz + 8LL * by * bz;
+        const long long score = cells + ghosts + 4 * G;
+        if (best_score < 0 || score < best_score) {
+          best_score = score;
+          best.bx = bx;
+          best.by = by;
+          best.bz = bz;
+          best.px = g.nx / bx;
+          best.py = g.ny / by;
+          best.pz = g.nz / bz;
+          best.smem = smem;
+        }
+      }
+    }
+  }
+  return best_score >= 0;
+}
+
+template <typename T>
+const void* resident_kernel(int bx) {
+  switch (bx) {
+    case 128: return (const void*)k_cg_resident<T, 128>;
+    case 64: return (const void*)k_cg_resident<T, 64>;
+    case 32: return (const void*)k_cg_resident<T, 32>;
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+int poisson_solve_resident(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
+                           int* iters, double* rel, std::string* err, bool* used) {
+  *used = false;
+  if (!(a.op == LES_OP_COMPACT && a.solver == LES_SOLVER_CG && a.g.nz >= 2 && a.bar && a.r && a.p0 && a.p1))
+    return LES_OK;
+  int dev = 0, nsm = 0, smem_optin = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) {
+    if (err) *err = std::string("resident CG: ") + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  Plan pl;
+  // leave room for the reduction's static shared memory
+  if (!make_plan(a.g, nsm, (size_t)std::max(0, smem_optin - 1024), fc.max_blocks, pl)) return LES_OK;
+  const void* kern = resident_kernel<T>(pl.bx);
+  int per_sm = 0;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem)) != cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kResThreads, pl.smem)) != cudaSuccess) {
+    if (err) *err = std::string("resident CG occupancy: ") + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  const long long G = (long long)pl.px * pl.py * pl.pz;
+  if (per_sm < 1 || G > (long long)per_sm * nsm) return LES_OK;  // not co-resident: stream instead
+  ResArgs<T> f;
+  f.nx = a.g.nx;
+  f.ny = a.g.ny;
+  f.nz = a.g.nz;
+  f.walls = a.g.walls;
+  f.cx = a.g.idx * a.g.idx;
+  f.cy = a.g.idy * a.g.idy;
+  f.cz = a.g.idz * a.g.idz;
+  f.by = pl.by;
+  f.bz = pl.bz;
+  f.px = pl.px;
+  f.py = pl.py;
+  f.n = (long long)f.nx * f.ny * f.nz;
+  f.b = b;
+  f.x = x;
+  f.rg = a.r;
+  f.pg0 = a.p0;
+  f.pg1 = a.p1;
+  f.partials = a.partials;
+  f.bar = a.bar;
+  f.ctl = a.ctl;
+  f.tol = tol;
+  f.maxit = maxit;
+  f.spin_cycles = fc.spin_cycles;
+  f.expected = (unsigned)G + (unsigned)std::max(0, fc.missing);
+  f.guard = a.guard;
+  *used = true;
+  if ((e = cudaMemsetAsync(a.bar, 0, sizeof(FusedBar), a.st)) != cudaSuccess) {
+    if (err) *err = std::string("resident CG barrier reset: ") + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  void* args[] = {&f};
+  {
+    ProfScope ps(a.prof, KI_CG_RESIDENT, a.st);
+    e = cudaLaunchCooperativeKernel(kern, dim3((unsigned)G), dim3(kResThreads), args, pl.smem, a.st);
+  }
+  if (e != cudaSuccess) {
+    if (err) *err = std::string("resident CG launch: ") + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  if ((e = cudaMemcpyAsync(a.ctl_host, a.ctl, sizeof(SolverCtl), cudaMemcpyDeviceToHost, a.st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(a.st)) != cudaSuccess) {
+    if (err) *err = std::string("resident CG: ") + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  const SolverCtl& c = *a.ctl_host;
+  if (iters) *iters = c.iter;
+  if (rel) *rel = c.rel;
+  // algorithmic traffic of the same CG written as streaming passes (as for
+  // the streaming solver), so that the two report comparable rates
+  if (a.prof) a.prof->bytes[KI_CG_RESIDENT] += (7.0 + 10.0 * c.iter) * (double)f.n * sizeof(T);
+  switch (c.done) {
+    case 1:
+    case 4: return LES_OK;
+    case 2: return LES_ERR_NOT_CONVERGED;
+    case 3:
+      if (err) *err = "poisson: breakdown (zero or non-finite p.Ap / residual)";
+      return LES_ERR_NONFINITE;
+    case 5:
+      if (err) *err = "poisson: a grid barrier wait timed out";
+      return LES_ERR_TIMEOUT;
+    default:
+      if (err) *err = "poisson: resident solver returned no status";
+      return LES_ERR_CUDA;
+  }
+}
+
+template int poisson_solve_resident<float>(const SolverArgs<float>&, const FusedCfg&, const float*, float*, double,
+                                           int, int*, double*, std::string*, bool*);
+template int poisson_solve_resident<double>(const SolverArgs<double>&, const FusedCfg&, const double*, double*,
+                                            double, int, int*, double*, std::string*, bool*);
+
+}  // namespace les

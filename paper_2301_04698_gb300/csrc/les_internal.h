@@ -91,8 +91,9 @@ struct FusedCfg {
   long long spin_cycles = 4000000000LL; // barrier wait limit (~2 s at 2 GHz)
   double timeout_ms = 2000.0;
   int missing = 0;                      // test hook: arrivals that never come
-  int stencil_path = 0;                 // 0 tiled predictors, 1 direct-load predictors
+  int stencil_path = 0;                 // 0 rolling z-march, 1 direct-load, 2 tiled
   int variant = 0;                      // 0 standard CG (2 barriers / iteration), 1 Chronopoulos-Gear (1)
+  int resident = 0;                     // 0 shared-memory-resident CG when the grid fits, 1 never
 };
 
 struct LaunchCfg {
@@ -103,7 +104,7 @@ struct LaunchCfg {
 enum KernelId : int {
   KI_THERMO = 0, KI_RADIATION, KI_NU, KI_NU_HALF, KI_SCALAR, KI_MOMENTUM, KI_RHS, KI_CORRECT,
   KI_DIAG, KI_CFL, KI_APPLY, KI_SUM, KI_CG_INIT, KI_CG_MATVEC, KI_CG_UPDATE, KI_JACOBI, KI_FINISH,
-  KI_CTL, KI_CG_FUSED, KI_UNET_CONV, KI_UNET_WGRAD, KI_UNET_ADAM, KI_COUNT
+  KI_CTL, KI_CG_FUSED, KI_UNET_CONV, KI_UNET_WGRAD, KI_UNET_ADAM, KI_CG_RESIDENT, KI_COUNT
 };
 extern const char* const kKernelNames[KI_COUNT];
 
@@ -224,6 +225,15 @@ template <typename T>
 cudaError_t launch_momentum_tiled(const StageArgs<T>& a, int max_blocks, const T* uk, const T* vk, const T* wk,
                                   const T* un, const T* vn, const T* wn, const T* p, const T* b, T* ou, T* ov,
                                   T* ow);
+// rolling-window predictors (les_stencil_roll.cu)
+template <typename T>
+cudaError_t launch_scalar_roll(const StageArgs<T>& a, int max_blocks, const T* u, const T* v, const T* w,
+                               const T* b, const T* thk, const T* qtk, const T* thh, const T* qth, const T* srad,
+                               T* th_out, T* qt_out);
+template <typename T>
+cudaError_t launch_momentum_roll(const StageArgs<T>& a, int max_blocks, const T* uk, const T* vk, const T* wk,
+                                 const T* un, const T* vn, const T* wn, const T* p, const T* b, T* ou, T* ov,
+                                 T* ow);
 template <typename T>
 cudaError_t launch_rhs(const StageArgs<T>& a, int op, const T* ou, const T* ov, const T* ow,
                        const T* psi, T* rhs);
@@ -275,6 +285,12 @@ bool fused_cg_eligible(const Grid<T>& g, int op, int solver, int ty);
 template <typename T>
 int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
                         int* iters, double* rel, std::string* err);
+// Persistent CG with its vectors in shared memory (les_cg_resident.cu).
+// Sets *used = false and returns LES_OK without launching when the grid has
+// no brick decomposition that fits on chip; the caller then streams.
+template <typename T>
+int poisson_solve_resident(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
+                           int* iters, double* rel, std::string* err, bool* used);
 
 }  // namespace les
 struct les_unet;

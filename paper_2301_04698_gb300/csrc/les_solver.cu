@@ -302,6 +302,11 @@ cudaError_t launch_apply(const SolverArgs<T>& a, int op, const T* x, T* y) {
 template <typename T>
 int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxit, int* iters, double* rel,
                   std::string* err) {
+  if (a.fused && a.bar && a.fused->resident == 0 && a.fused->variant == 0) {
+    bool used = false;
+    const int rc = poisson_solve_resident<T>(a, *a.fused, b, x, tol, maxit, iters, rel, err, &used);
+    if (used || rc != LES_OK) return rc;
+  }
   if (a.fused && a.bar && fused_cg_eligible(a.g, a.op, a.solver, a.fused->ty))
     return poisson_solve_fused<T>(a, *a.fused, b, x, tol, maxit, iters, rel, err);
   auto fail = [&](cudaError_t e, const char* where) {

@@ -84,7 +84,7 @@ class LesTuning(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("cg_tile_rows", C.c_int32), ("cg_tile_planes", C.c_int32),
                 ("cg_max_blocks", C.c_int32), ("barrier_timeout_ms", C.c_double),
                 ("fault_missing_arrivals", C.c_int32), ("stencil_path", C.c_int32), ("cg_variant", C.c_int32),
-                ("reserved0", C.c_int32)]
+                ("cg_resident", C.c_int32)]
 
 
 class LesError(RuntimeError):
@@ -376,6 +376,7 @@ class Simulation:
         cur = self.tuning()
         t.stencil_path = cur["stencil_path"]
         t.cg_variant = cur["cg_variant"]
+        t.cg_resident = cur["cg_resident"]
         for k, v in kw.items():
             setattr(t, k, v)
         _check(self.lib, self.h, self.lib.les_set_tuning(self.h, C.byref(t)), "set tuning")

@@ -140,10 +140,11 @@ def _moist_case(nx=37, ny=11, nz=12, **kw):
     return c.replace(**kw)
 
 
-@pytest.mark.parametrize("walls,stencil_path", [(True, 0), (False, 0), (True, 1), (False, 1)])
+@pytest.mark.parametrize("walls,stencil_path", [(True, 0), (False, 0), (True, 1), (False, 1), (True, 2),
+                                                (False, 2)])
 def test_stages_fp64(les_mod, walls, stencil_path):
-    """Stage-by-stage FP64 parity; stencil_path 0 = shared-memory tiled
-    predictors (nu_t in-tile), 1 = direct-load predictors."""
+    """Stage-by-stage FP64 parity; stencil_path 0 = rolling momentum + tiled
+    scalar predictors, 1 = direct-load predictors, 2 = tiled predictors."""
     case = _moist_case()
     if not walls:
         case = case.replace(walls=False, physics=("adv", "sgs", "fb", "moist", "buoy", "coriolis"))
@@ -296,8 +297,8 @@ def test_ragged_and_minimum_grids(les_mod, shape):
 # persistent single-launch CG (fast path for nx a multiple of the tile width)
 
 
-def _fused_launches(sim):
-    return sum(k["launches"] for k in sim.profile_read() if k["name"] == "cg_fused")
+def _fused_launches(sim, names=("cg_fused", "cg_resident")):
+    return sum(k["launches"] for k in sim.profile_read() if k["name"] in names)
 
 
 @pytest.mark.parametrize("precision,walls,shape", [(32, True, (128, 16, 12)), (32, False, (256, 8, 5)),
@@ -315,15 +316,18 @@ def test_fused_cg_matches_oracle(les_mod, precision, walls, shape):
     tol = 1e-11 if precision == 64 else 1e-6
     bt = torch.from_numpy(b).to("cuda", dt)
     results = []
-    for variant, ty, zc in ((1, 4, 4), (1, 1, 1), (1, 2, 3), (1, 8, 16), (0, 4, 4), (0, 2, 3)):
+    # (variant, tile rows, tile planes, streaming only): the standard variant
+    # runs both streaming and with its vectors in shared memory
+    for variant, ty, zc, stream in ((1, 4, 4, 1), (1, 1, 1, 1), (1, 2, 3, 1), (1, 8, 16, 1), (0, 4, 4, 1),
+                                    (0, 2, 3, 1), (0, 4, 4, 0)):
         if ny % ty:
             continue
-        sim.set_tuning(cg_tile_rows=ty, cg_tile_planes=zc, cg_variant=variant)
+        sim.set_tuning(cg_tile_rows=ty, cg_tile_planes=zc, cg_variant=variant, cg_resident=stream)
         sim.profile_reset()
         x = torch.zeros_like(bt)
         rc, it, res = sim.poisson_solve(bt, x, tol, 20000)
         assert rc == 0 and res <= tol
-        assert _fused_launches(sim) == 1
+        assert _fused_launches(sim, ("cg_resident",) if stream == 0 else ("cg_fused",)) == 1
         xn = x.cpu().double().numpy()
         # zero-mean gauge, to rounding of the field's magnitude
         assert abs(xn.mean()) < (1e-14 if precision == 64 else 1e-6) * np.abs(xn).max()
@@ -343,22 +347,74 @@ def test_fused_cg_matches_oracle(les_mod, precision, walls, shape):
         assert rel(xn, x1.cpu().double().numpy()) < (1e-9 if precision == 64 else 5e-4)
 
 
-def test_fused_cg_barrier_timeout_is_reported(les_mod):
+@pytest.mark.parametrize("stream", [0, 1])
+def test_fused_cg_barrier_timeout_is_reported(les_mod, stream):
     case = inputs.Case(name="fused", nx=128, ny=8, nz=4, dx=1.0, dy=1.0, dz=1.0, precision=32,
                        init="zero", physics=())
     sim = les_mod.Simulation(case)
+    sim.set_tuning(cg_resident=stream)
     b = torch.from_numpy(inputs.uniform(3, 0, case.n, -1, 1).reshape(case.shape)).to("cuda", torch.float32)
     x = torch.zeros_like(b)
     # every barrier waits for one block that never arrives: each wait must end
     # after its limit with a status the host reads, leaving the device usable
     sim.set_tuning(barrier_timeout_ms=20.0, fault_missing_arrivals=1)
+    sim.profile_reset()
     with pytest.raises(les_mod.LesError) as e:
         sim.poisson_solve(b, x, 1e-6, 100)
     assert e.value.status == les_mod.LES_ERR_TIMEOUT
+    assert _fused_launches(sim, ("cg_resident",) if stream == 0 else ("cg_fused",)) == 1
     sim.set_tuning(barrier_timeout_ms=2000.0, fault_missing_arrivals=0)
     x.zero_()
     rc, it, res = sim.poisson_solve(b, x, 1e-6, 1000)
     assert rc == 0 and res <= 1e-6
+
+
+@pytest.mark.parametrize("precision,walls,shape,max_blocks", [
+    (32, True, (128, 16, 12), 0),     # 32-wide bricks, several along x
+    (32, False, (256, 8, 5), 4),      # 64-wide bricks
+    (32, True, (256, 8, 5), 2),       # 128-wide bricks, two along x
+    (64, False, (32, 32, 32), 0),     # the learned-guess grid
+    (64, True, (64, 7, 11), 0),       # odd brick extents in y and z
+    (32, False, (32, 3, 2), 0)])      # one-node bricks in y and z
+def test_resident_cg_matches_oracle(les_mod, precision, walls, shape, max_blocks):
+    """The shared-memory-resident CG against the FP64 oracle and against the
+    streaming persistent CG, which follows the same iterates."""
+    from oracle import Oracle
+    nx, ny, nz = shape
+    case = inputs.Case(name="res", nx=nx, ny=ny, nz=nz, dx=35.0, dy=30.0, dz=10.0, walls=walls,
+                       precision=precision, init="zero", physics=())
+    sim = les_mod.Simulation(case)
+    ref = Oracle(case.replace(precision=64))
+    b = inputs.uniform(23, 0, case.n, -1, 1).reshape(case.shape) + 0.25
+    xr, st, itr, _ = ref.poisson(b, tol=1e-12, maxit=20000)
+    dt = torch.float64 if precision == 64 else torch.float32
+    tol = 1e-11 if precision == 64 else 1e-6
+    bt = torch.from_numpy(b).to("cuda", dt)
+    out = {}
+    for stream in (0, 1):
+        sim.set_tuning(cg_resident=stream, cg_max_blocks=max_blocks if stream == 0 else 1 << 20)
+        sim.profile_reset()
+        # a nonzero first guess exercises the initial residual's ghost exchange
+        x = torch.from_numpy(0.1 * inputs.uniform(24, 0, case.n, -1, 1).reshape(case.shape)).to("cuda", dt)
+        rc, it, res = sim.poisson_solve(bt, x, tol, 20000)
+        assert rc == 0 and res <= tol
+        if stream == 0:
+            assert _fused_launches(sim, ("cg_resident",)) == 1
+        xn = x.cpu().double().numpy()
+        assert abs(xn.mean()) < (1e-14 if precision == 64 else 1e-6) * np.abs(xn).max()
+        assert rel(xn, xr) < (1e-8 if precision == 64 else 5e-4), stream
+        out[stream] = (it, xn)
+    assert abs(out[0][0] - out[1][0]) <= (1 if precision == 64 else 3)
+    assert rel(out[0][1], out[1][1]) < (1e-9 if precision == 64 else 5e-4)
+    # not converged within maxit: the status and the iteration count come back
+    x = torch.zeros_like(bt)
+    sim.set_tuning(cg_resident=0, cg_max_blocks=max_blocks)
+    rc, it, res = sim.poisson_solve(bt, x, 1e-30, 5, allow_not_converged=True)
+    assert rc == les_mod.LES_ERR_NOT_CONVERGED and it == 5
+    # a zero right side returns x = 0 with no iteration
+    x = torch.ones_like(bt)
+    rc, it, res = sim.poisson_solve(torch.zeros_like(bt), x, tol, 100)
+    assert rc == 0 and it == 0 and float(x.abs().max()) == 0.0
 
 
 def test_fused_steps_fp64(les_mod):

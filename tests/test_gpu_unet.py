@@ -141,3 +141,25 @@ def test_learned_warm_start_in_a_step(les_mod):
     small = les_mod.UNet(8, max_batch=1)
     with pytest.raises(les_mod.LesError):
         les_mod.attach_model(sim2, small)
+
+
+def test_learned_guess_judged_by_resident_solver(les_mod):
+    """On the 32^3 grid the CG solve keeps its vectors in shared memory; the
+    learned first guess of an untrained network is judged there (kept or
+    replaced by zero) and the step reaches the zero-guess result."""
+    case = inputs.tgv(32, warm="learned", steps_tol=1e-8)
+    sim = les_mod.Simulation(case)
+    sim.set_state(inputs.initial_state(case))
+    model = les_mod.UNet(32, max_batch=1)
+    model.set_weights(U.init_weights(5))
+    les_mod.attach_model(sim, model)
+    sim.profile_reset()
+    st = sim.step(2)
+    assert st["not_converged"] == 0
+    launches = {k["name"]: k["launches"] for k in sim.profile_read()}
+    assert launches.get("cg_resident", 0) == 2 * case.K
+    sim0 = les_mod.Simulation(case.replace(warm="zero"))
+    sim0.set_state(inputs.initial_state(case))
+    sim0.step(2)
+    for f in ("u", "v", "w"):
+        assert rel(sim.get(f), sim0.get(f)) < 1e-6
