@@ -13,10 +13,10 @@
 //            planes k-1, k+1 in registers, prefetching plane k+1 while
 //            computing plane k; each thread handles VW = 16 B of cells;
 //   phase B  x += alpha p, r -= alpha q, r.r -- 16-byte vector streaming;
-// each followed by a grid-wide FP64 sum: every block posts its partial, the
-// last block to arrive folds the partials in block order (deterministic) and
-// publishes the total with the barrier generation.  All blocks then compute
-// the same alpha, beta and stop decision.  Data written by other blocks is
+// each followed by a grid-wide FP64 sum (les_gridsync.cuh): every block
+// posts its partial, and once all have arrived every block folds all
+// partials in block order (deterministic), so all blocks compute the same
+// alpha, beta and stop decision.  Data written by other blocks is
 // read with ld.global.cg (L2), never through the non-coherent L1 path.
 // Every barrier wait is bounded in time; on expiry the kernel records a
 // timeout in the control block and returns.
@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_fused(FusedArgs<T> f) {
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const long long gstride = (long long)gridDim.x * blockDim.x * blockDim.y;
   const long long gtid = (long long)blockIdx.x * blockDim.x * blockDim.y + tid;
+  GridSync gs{f.bar, f.partials, f.spin_cycles, f.expected, 0u};
   int status = 0;  // 0 running, 1 converged, 2 maxit, 3 breakdown, 4 zero rhs, 5 timeout
 
   // mean of b
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_fused(FusedArgs<T> f) {
 #pragma unroll
     for (int e = 0; e < VW; ++e) s1[0] += (double)bv[e];
   }
-  if (!grid_sum<1>(s1, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+  if (!grid_sum<1>(s1, gs)) status = 5;
   const T mean = (T)(s1[0] / (double)f.n);
 
   // r = (b - mean) - L_c x0;  r.r and |b - mean|^2
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_fused(FusedArgs<T> f) {
       s2[1] += vdot(bv, bv);
     };
     stencil_sweep(f, sm, loadX, loadX1, emitR);
-    if (!grid_sum<2>(s2, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+    if (!grid_sum<2>(s2, gs)) status = 5;
   }
   // the plain solver judges a learned first guess: if it leaves a larger
   // residual than x0 = 0, restart from zero (r = b - mean b, r.r = |b|^2)
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_fused(FusedArgs<T> f) {
       stv(f.r + v * VW, bv);
     }
     double sz[1] = {0.0};
-    if (!grid_sum<1>(sz, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+    if (!grid_sum<1>(sz, gs)) status = 5;
     s2[0] = s2[1];
   }
   double rr = s2[0];
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_fused(FusedArgs<T> f) {
       sa[0] += vdot(P, qv);
     };
     stencil_sweep(f, sm, loadP, loadP1, emitQ);
-    if (!grid_sum<1>(sa, f.bar, f.partials, f.spin_cycles, f.expected)) {
+    if (!grid_sum<1>(sa, gs)) {
       status = 5;
       break;
     }
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_fused(FusedArgs<T> f) {
         }
       }
     }
-    if (!grid_sum<1>(sb, f.bar, f.partials, f.spin_cycles, f.expected)) {
+    if (!grid_sum<1>(sb, gs)) {
       status = 5;
       break;
     }
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_fused(FusedArgs<T> f) {
 #pragma unroll
       for (int e = 0; e < VW; ++e) sx[0] += (double)xv[e];
     }
-    if (!grid_sum<1>(sx, f.bar, f.partials, f.spin_cycles, f.expected)) {
+    if (!grid_sum<1>(sx, gs)) {
       status = 5;
     } else {
       const T mx = (T)(sx[0] / (double)f.n);
@@ -373,6 +374,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_cgg(FusedArgs<T> f) {
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const long long gstride = (long long)gridDim.x * blockDim.x * blockDim.y;
   const long long gtid = (long long)blockIdx.x * blockDim.x * blockDim.y + tid;
+  GridSync gs{f.bar, f.partials, f.spin_cycles, f.expected, 0u};
   int status = 0;
   double s1[1] = {0.0};
   for (long long v = gtid; v < f.nv; v += gstride) {
@@ -381,7 +383,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_cgg(FusedArgs<T> f) {
 #pragma unroll
     for (int e = 0; e < VW; ++e) s1[0] += (double)bv[e];
   }
-  if (!grid_sum<1>(s1, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+  if (!grid_sum<1>(s1, gs)) status = 5;
   const T mean = (T)(s1[0] / (double)f.n);
   T* rc = f.r;   // r, w, s of the current iteration
   T* wc = f.q;
@@ -407,7 +409,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_cgg(FusedArgs<T> f) {
       s2[1] += vdot(bv, bv);
     };
     stencil_sweep(f, sm, loadX, loadX1, emitR);
-    if (!grid_sum<2>(s2, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+    if (!grid_sum<2>(s2, gs)) status = 5;
   }
   // the plain solver judges a learned first guess: if it leaves a larger
   // residual than x0 = 0, restart from zero (r = b - mean b, r.r = |b|^2)
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_cgg(FusedArgs<T> f) {
       stv(rc + v * VW, bv);
     }
     double sz[1] = {0.0};
-    if (!grid_sum<1>(sz, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+    if (!grid_sum<1>(sz, gs)) status = 5;
     s2[0] = s2[1];
   }
   double gamma = s2[0];
@@ -449,7 +451,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_cgg(FusedArgs<T> f) {
       sd[0] += vdot(qv, P);
     };
     stencil_sweep(f, sm, loadR, loadR1, emitW);
-    if (!grid_sum<1>(sd, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+    if (!grid_sum<1>(sd, gs)) status = 5;
     delta = sd[0];
     if (!status && (delta == 0.0 || !isfinite(delta))) status = 3;
   }
@@ -511,7 +513,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_cgg(FusedArgs<T> f) {
       sg[1] += vdot(qv, Rn);
     };
     stencil_sweep(f, sm, loadRn, loadRn1, emitIt);
-    if (!grid_sum<2>(sg, f.bar, f.partials, f.spin_cycles, f.expected)) {
+    if (!grid_sum<2>(sg, gs)) {
       status = 5;
       break;
     }
@@ -540,7 +542,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_cgg(FusedArgs<T> f) {
 #pragma unroll
       for (int e = 0; e < VW; ++e) sx[0] += (double)xv[e];
     }
-    if (!grid_sum<1>(sx, f.bar, f.partials, f.spin_cycles, f.expected)) {
+    if (!grid_sum<1>(sx, gs)) {
       status = 5;
     } else {
       const T mx = (T)(sx[0] / (double)f.n);
@@ -619,6 +621,7 @@ int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, 
   long long G = (long long)per_sm * nsm;
   G = std::min<long long>(G, fc.max_blocks);
   G = std::max<long long>(1, std::min<long long>(G, std::max<long long>(f.ntiles, nsm)));
+  G = std::min<long long>(G, 8LL * nsm);  // the partials hold 2 x 2 x 8 slots per SM
   f.expected = (unsigned)G + (unsigned)std::max(0, fc.missing);
   f.guard = a.guard;
   if ((e = cudaMemsetAsync(a.bar, 0, sizeof(FusedBar), a.st)) != cudaSuccess) {

@@ -17,10 +17,9 @@
 //            published; q = L_c p; p.q
 //   phase B  q = L_c p again (recomputed, not stored); x += alpha p,
 //            r -= alpha q; r faces published; r.r
-// each followed by a grid-wide FP64 sum (les_gridsync.cuh).  Dot products
-// are formed in T over at most eight terms per thread and then accumulated
-// in FP64.  Ghost loads are issued in batches so that each costs one round
-// of memory latency.
+// each followed by a grid-wide sum (les_gridsync.cuh; FP32 dot products are
+// accumulated as compensated FP32 pairs, FP64 ones in FP64).  Ghost loads
+// are issued in batches so that each costs one round of memory latency.
 #include <algorithm>
 #include <string>
 
@@ -52,32 +51,6 @@ struct ResArgs {
   long long spin_cycles;
   unsigned expected;
   int guard;
-};
-
-// FP64 sum of products formed in T: float terms are summed in float in
-// groups of eight before entering the FP64 accumulator
-template <typename T>
-struct Acc;
-template <>
-struct Acc<float> {
-  double d = 0.0;
-  float f = 0.f;
-  int n = 0;
-  __device__ __forceinline__ void add(float v) {
-    f += v;
-    if (++n == 8) {
-      d += (double)f;
-      f = 0.f;
-      n = 0;
-    }
-  }
-  __device__ __forceinline__ double total() const { return d + (double)f; }
-};
-template <>
-struct Acc<double> {
-  double d = 0.0;
-  __device__ __forceinline__ void add(double v) { d += v; }
-  __device__ __forceinline__ double total() const { return d; }
 };
 
 __device__ __forceinline__ int zghost(int k, int nz, int walls) {
@@ -187,16 +160,17 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
     }
   };
 
+  GridSync gs{f.bar, f.partials, f.spin_cycles, f.expected, 0u};
   int status = 0;  // 0 running, 1 converged, 2 maxit, 3 breakdown, 4 zero rhs, 5 timeout
   // mean of b; b staged in R
-  Acc<T> a1;
+  Dot<T> a1[1];
   own([&](int c, int, size_t g, bool) {
     const T v = __ldcg(f.b + g);
     R[c] = v;
-    a1.add(v);
+    a1[0].add(v);
   });
-  double s1[1] = {a1.total()};
-  if (!grid_sum<1>(s1, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+  double s1[1];
+  if (!grid_dot<1>(a1, gs, s1)) status = 5;
   const T mean = (T)(s1[0] / (double)f.n);
 
   // x0 with its ghosts; r = (b - mean) - L_c x0, published; r.r and |b - mean|^2
@@ -209,18 +183,16 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
     });
     ghosts([&](size_t g) { return __ldcg(f.x + g); });
     __syncthreads();
-    Acc<T> arr, abb;
+    Dot<T> a2[2];
     own([&](int c, int pi, size_t g, bool face) {
       const T bm = R[c] - mean;
       const T rv = bm - Lc(pi);
       R[c] = rv;
       if (face) __stcg(f.rg + g, rv);
-      arr.add(rv * rv);
-      abb.add(bm * bm);
+      a2[0].add(rv * rv);
+      a2[1].add(bm * bm);
     });
-    s2[0] = arr.total();
-    s2[1] = abb.total();
-    if (!grid_sum<2>(s2, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+    if (!grid_dot<2>(a2, gs, s2)) status = 5;
   }
   // the plain solver judges a learned first guess: if it leaves a larger
   // residual than x0 = 0, restart from zero (r = b - mean b, r.r = |b|^2)
@@ -232,7 +204,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
       if (face) __stcg(f.rg + g, rv);
     });
     double sz[1] = {0.0};
-    if (!grid_sum<1>(sz, f.bar, f.partials, f.spin_cycles, f.expected)) status = 5;
+    if (!grid_sum<1>(sz, gs)) status = 5;
     s2[0] = s2[1];
   }
   double rr = s2[0];
@@ -263,10 +235,10 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
     if (first) ghosts([&](size_t g) { return __ldcg(f.rg + g); });
     else ghosts([&](size_t g) { return __ldcg(f.rg + g) + tb * __ldcg(po + g); });
     __syncthreads();
-    Acc<T> apq;
-    own([&](int, int pi, size_t, bool) { apq.add(P[pi] * Lc(pi)); });
-    double sa[1] = {apq.total()};
-    if (!grid_sum<1>(sa, f.bar, f.partials, f.spin_cycles, f.expected)) {
+    Dot<T> apq[1];
+    own([&](int, int pi, size_t, bool) { apq[0].add(P[pi] * Lc(pi)); });
+    double sa[1];
+    if (!grid_dot<1>(apq, gs, sa)) {
       status = 5;
       break;
     }
@@ -278,17 +250,17 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
     const double alpha = rr / pq;
     const T ta = (T)alpha;
     // phase B: x += alpha p, r -= alpha L_c p, r faces published, r.r
-    Acc<T> ar;
+    Dot<T> ar[1];
     own([&](int c, int pi, size_t g, bool face) {
       const T pv = P[pi];
       X[c] += ta * pv;
       const T rv = R[c] - ta * Lc(pi);
       R[c] = rv;
       if (face) __stcg(f.rg + g, rv);
-      ar.add(rv * rv);
+      ar[0].add(rv * rv);
     });
-    double sb[1] = {ar.total()};
-    if (!grid_sum<1>(sb, f.bar, f.partials, f.spin_cycles, f.expected)) {
+    double sb[1];
+    if (!grid_dot<1>(ar, gs, sb)) {
       status = 5;
       break;
     }
@@ -304,10 +276,10 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
 
   // zero-mean gauge (or zero for a zero right side), written back to x
   if (status != 5) {
-    Acc<T> ax;
-    own([&](int c, int, size_t, bool) { ax.add(X[c]); });
-    double sx[1] = {ax.total()};
-    if (!grid_sum<1>(sx, f.bar, f.partials, f.spin_cycles, f.expected)) {
+    Dot<T> ax[1];
+    own([&](int c, int, size_t, bool) { ax[0].add(X[c]); });
+    double sx[1];
+    if (!grid_dot<1>(ax, gs, sx)) {
       status = 5;
     } else {
       const T mx = (T)(sx[0] / (double)f.n);
@@ -396,8 +368,8 @@ int poisson_solve_resident(const SolverArgs<T>& a, const FusedCfg& fc, const T* 
     return LES_ERR_CUDA;
   }
   Plan pl;
-  // leave room for the reduction's static shared memory
-  if (!make_plan(a.g, nsm, (size_t)std::max(0, smem_optin - 1024), fc.max_blocks, pl)) return LES_OK;
+  // leave room for the reductions' static shared memory (about 1 KB)
+  if (!make_plan(a.g, nsm, (size_t)std::max(0, smem_optin - 2048), fc.max_blocks, pl)) return LES_OK;
   const void* kern = resident_kernel<T>(pl.bx);
   int per_sm = 0;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem)) != cudaSuccess ||

@@ -1,11 +1,24 @@
-// les_gridsync.cuh -- grid-wide FP64 sums for persistent cooperative kernels
-// (the global reductions of the conjugate-gradient solve, Sec. 2.4).
+// les_gridsync.cuh -- grid-wide sums for persistent cooperative kernels (the
+// global reductions of the conjugate-gradient solve, Sec. 2.4).
 //
-// Every block posts its partials; the last block to arrive folds them in
-// block order (deterministic for a fixed grid), publishes the totals and
-// bumps the generation that the other blocks poll.  Every wait is bounded in
-// time: on expiry the fail flag is raised and the call returns false in
-// every thread, leaving the device usable.
+// Protocol: the arrival counter only grows.  At its e-th grid sum a block
+// writes its block partials into slot e mod 2 of the partials array, adds
+// one to the counter with release semantics and waits until the counter
+// reaches (e + 1) x (arrivals per sum); then every block reads all partials
+// and folds them in block order, so every block obtains the same totals
+// (deterministic for a fixed grid) and no block has to publish them.  Two
+// slots suffice: a block writes slot e mod 2 again only at sum e + 2, which
+// it can reach only after every block has arrived at sum e + 1, i.e. after
+// every block has finished reading the slot of sum e.
+//
+// Every wait is bounded in time: on expiry the fail flag is raised and the
+// call returns false in every thread of the block, leaving the device usable.
+//
+// Dot products of FP32 vectors are accumulated as compensated FP32 pairs
+// (hi + lo, Knuth's TwoSum for the exact error of each addition), reduced in
+// the same arithmetic and turned into FP64 totals at the end: on this GPU an
+// FP64 instruction costs tens of FP32 ones, and the compensated pair keeps
+// about 48 significant bits.
 #pragma once
 
 #include "les_common.cuh"
@@ -16,8 +29,8 @@ namespace les {
 __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
   return *reinterpret_cast<const volatile unsigned*>(p);
 }
-// GPU-scope acquire load / release store / acq_rel fetch-add: the ordering the
-// barrier needs without full membar.gl fences
+// GPU-scope acquire load / release store and reduction: the ordering the
+// grid sum needs without full membar.gl fences
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -26,78 +39,212 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid-wide FP64 sum of NV values.  Every block posts its partials; the last
-// block to arrive folds them in block order (deterministic), publishes the
-// totals and bumps the generation that the others poll.  Returns false (in
-// every thread) if a wait ran past its limit.
+// ---- compensated FP32 pair ---------------------------------------------------
+struct F2 {
+  float hi, lo;
+};
+// a + b: TwoSum of the high parts (exact error e), low parts added to e, then
+// renormalised with Fast2Sum so that |lo| <= ulp(hi) / 2
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  const float s = a.hi + b.hi;
+  const float bp = s - a.hi;
+  const float e = (a.hi - (s - bp)) + (b.hi - bp);
+  const float t = e + (a.lo + b.lo);
+  const float h = s + t;
+  return F2{h, t - (h - s)};
+}
+// a += v for one FP32 term (no renormalisation: the low part only collects
+// the exact rounding errors of the high part)
+__device__ __forceinline__ void f2_acc(F2& a, float v) {
+  const float s = a.hi + v;
+  const float bp = s - a.hi;
+  a.lo += (a.hi - (s - bp)) + (v - bp);
+  a.hi = s;
+}
+__device__ __forceinline__ double f2_value(F2 a) { return (double)a.hi + (double)a.lo; }
+
+// Per-thread accumulator of a sum of T terms: compensated FP32 for float,
+// plain FP64 for double.
+template <typename T>
+struct Dot;
+template <>
+struct Dot<float> {
+  F2 s{0.f, 0.f};
+  __device__ __forceinline__ void add(float v) { f2_acc(s, v); }
+};
+template <>
+struct Dot<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+};
+
+// ---- block reductions with the total broadcast to every thread ---------------
 template <int NV>
-__device__ bool grid_sum(double (&v)[NV], FusedBar* bar, double* partials, long long spin_cycles,
-                         unsigned expected) {
-  __shared__ double sh[32];
-  __shared__ unsigned s_last, s_gen;
-  __shared__ int s_fail;
+__device__ __forceinline__ void block_sum_bcast(F2 (&v)[NV]) {
+  __shared__ F2 sh[NV][32];
+  __shared__ F2 out[NV];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  const int nthr = blockDim.x * blockDim.y;
-  const unsigned G = gridDim.x;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
-    const double bv = block_reduce<false>(v[q], sh);
-    if (tid == 0) partials[(size_t)q * G + blockIdx.x] = bv;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const F2 b{__shfl_xor_sync(0xffffffffu, v[q].hi, o), __shfl_xor_sync(0xffffffffu, v[q].lo, o)};
+      v[q] = f2_add(v[q], b);
+    }
   }
-  if (tid == 0) {
-    s_gen = ld_acquire(&bar->gen.v);
-    // the arrival releases this block's partials and, for the last block,
-    // acquires everybody else's
-    s_last = atom_add_acq_rel(&bar->count.v, 1u) == expected - 1;
-    s_fail = 0;
-  }
+  __syncthreads();  // earlier readers of sh / out are done
+  if ((tid & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q][tid >> 5] = v[q];
   __syncthreads();
-  if (s_last) {
+  if (tid < 32) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      // up to 8 independent loads in flight per thread, then a fixed-order sum
-      double acc = 0.0;
-      for (unsigned b0 = tid; b0 < G; b0 += 8 * nthr) {
-        double x[8];
+      F2 a = tid < nw ? sh[q][tid] : F2{0.f, 0.f};
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const unsigned b = b0 + u * nthr;
-          x[u] = b < G ? __ldcg(partials + (size_t)q * G + b) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc += x[u];
+      for (int o = 16; o > 0; o >>= 1) {
+        const F2 b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+        a = f2_add(a, b);
       }
-      const double tot = block_reduce<false>(acc, sh);
-      if (tid == 0) bar->value[q] = tot;
+      if (tid == 0) out[q] = a;
     }
-    if (tid == 0) {
-      bar->count.v = 0u;
-      // publish the totals and the reset counter with the new generation
-      st_release(&bar->gen.v, s_gen + 1u);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = out[q];
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum_bcast(double (&v)[NV]) {
+  __shared__ double sh[NV][32];
+  __shared__ double out[NV];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+  __syncthreads();
+  if ((tid & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q][tid >> 5] = v[q];
+  __syncthreads();
+  if (tid < 32) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double a = tid < nw ? sh[q][tid] : 0.0;
+      a = warp_sum(a);
+      if (tid == 0) out[q] = a;
     }
-  } else if (tid == 0) {
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = out[q];
+}
+
+// ---- the grid sum ---------------------------------------------------------------
+// Per-block state of the grid sums of one launch (held in registers).
+struct GridSync {
+  FusedBar* bar;
+  void* partials;     // >= 2 x NV x gridDim.x 8-byte slots
+  long long spin;     // wait limit in clock cycles
+  unsigned expected;  // arrivals per sum: gridDim.x (+ the test hook's missing ones)
+  unsigned epoch;     // sums completed by this block
+};
+
+// arrive after this block's partials are written, wait for all arrivals
+__device__ __forceinline__ bool grid_arrive_wait(GridSync& gs) {
+  __shared__ int s_fail;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  if (tid == 0) {
+    s_fail = 0;
+    // the release orders this block's partials (and, through the barrier
+    // before it, every thread's earlier writes) before the arrival
+    red_release_add(&gs.bar->count.v, 1u);
+    const unsigned target = (gs.epoch + 1u) * gs.expected;
     const long long t0 = clock64();
     unsigned spins = 0;
-    while (ld_acquire(&bar->gen.v) == s_gen) {
-      if ((++spins & 63u) == 0u &&
-          (ld_volatile(&bar->fail.v) != 0u || clock64() - t0 > spin_cycles)) {
-        atomicExch(&bar->fail.v, 1u);
+    while ((int)(ld_acquire(&gs.bar->count.v) - target) < 0) {
+      if ((++spins & 63u) == 0u && (ld_volatile(&gs.bar->fail.v) != 0u || clock64() - t0 > gs.spin)) {
+        atomicExch(&gs.bar->fail.v, 1u);
         s_fail = 1;
         break;
       }
     }
   }
   __syncthreads();
-  if (s_fail) return false;
+  return s_fail == 0;
+}
+
+// Grid-wide sum of NV per-thread FP32-pair partials; totals in FP64.
+template <int NV>
+__device__ bool grid_sum(F2 (&v)[NV], GridSync& gs, double (&tot)[NV]) {
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  const unsigned G = gridDim.x;
+  float2* slot = reinterpret_cast<float2*>(gs.partials) + (size_t)(gs.epoch & 1u) * NV * G;
+  block_sum_bcast<NV>(v);
+  if (tid == 0)
 #pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = __ldcg(&bar->value[q]);
+    for (int q = 0; q < NV; ++q) slot[(size_t)q * G + blockIdx.x] = make_float2(v[q].hi, v[q].lo);
+  __syncthreads();
+  if (!grid_arrive_wait(gs)) return false;
+  F2 a[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    a[q] = F2{0.f, 0.f};
+    for (unsigned b = tid; b < G; b += nthr) {
+      const float2 p = __ldcg(slot + (size_t)q * G + b);
+      a[q] = f2_add(a[q], F2{p.x, p.y});
+    }
+  }
+  block_sum_bcast<NV>(a);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) tot[q] = f2_value(a[q]);
+  gs.epoch += 1u;
   return true;
+}
+
+// Grid-wide sum of NV per-thread FP64 partials (totals replace v).
+template <int NV>
+__device__ bool grid_sum(double (&v)[NV], GridSync& gs) {
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  const unsigned G = gridDim.x;
+  double* slot = reinterpret_cast<double*>(gs.partials) + (size_t)(gs.epoch & 1u) * NV * G;
+  block_sum_bcast<NV>(v);
+  if (tid == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) slot[(size_t)q * G + blockIdx.x] = v[q];
+  __syncthreads();
+  if (!grid_arrive_wait(gs)) return false;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double acc = 0.0;
+    for (unsigned b = tid; b < G; b += nthr) acc += __ldcg(slot + (size_t)q * G + b);
+    v[q] = acc;
+  }
+  block_sum_bcast<NV>(v);
+  gs.epoch += 1u;
+  return true;
+}
+
+// one grid sum of a Dot<T> accumulator per value
+template <int NV>
+__device__ __forceinline__ bool grid_dot(Dot<float> (&d)[NV], GridSync& gs, double (&tot)[NV]) {
+  F2 v[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = d[q].s;
+  return grid_sum<NV>(v, gs, tot);
+}
+template <int NV>
+__device__ __forceinline__ bool grid_dot(Dot<double> (&d)[NV], GridSync& gs, double (&tot)[NV]) {
+#pragma unroll
+  for (int q = 0; q < NV; ++q) tot[q] = d[q].s;
+  return grid_sum<NV>(tot, gs);
 }
 
 }  // namespace les
