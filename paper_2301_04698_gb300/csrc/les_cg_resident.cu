@@ -4,19 +4,18 @@
 // psi returned with zero mean).
 //
 // When the whole grid fits in the GPU's shared memory (a 128 x 128 x 96 FP32
-// grid needs about 21 MB of the 34 MB on 152 SMs), every iteration of the
+// grid needs about 27 MB of the 34 MB on 152 SMs), every iteration of the
 // streaming solver is dominated by the latency of its passes through L2, not
 // by their bytes.  Here each block of one persistent cooperative launch owns
-// a brick of bx x by x bz nodes for the whole solve and keeps x, r and p of
-// its brick (p with a one-node ghost layer) in shared memory.  The only
+// a brick of bx x by x bz nodes for the whole solve and keeps x, r, p and
+// q = L_c p of its brick (p with a one-node ghost layer) in shared memory.  The only
 // global traffic of an iteration is the exchange of brick faces:
 //   phase A  p = r + beta p in place; the ghost layer is filled from the
 //            neighbours' published faces of r (this iteration) and p (the
 //            previous one, double-buffered by parity) as r + beta p_old, so
 //            no barrier separates the p update from the matvec; p faces
 //            published; q = L_c p; p.q
-//   phase B  q = L_c p again (recomputed, not stored); x += alpha p,
-//            r -= alpha q; r faces published; r.r
+//   phase B  x += alpha p, r -= alpha q; r faces published; r.r
 // each followed by a grid-wide sum (les_gridsync.cuh; FP32 dot products are
 // accumulated as compensated FP32 pairs, FP64 ones in FP64).  Ghost loads
 // are issued in batches so that each costs one round of memory latency.
@@ -61,7 +60,8 @@ __device__ __forceinline__ int zghost(int k, int nz, int walls) {
 template <typename T, int BX>
 __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
   constexpr int L = BX / 32;  // nodes per lane along a brick row
-  constexpr int RB = 3;       // ghost rows per warp whose loads are in flight together
+  // ghost rows per warp whose loads are in flight together (within the registers)
+  constexpr int RB = sizeof(T) == 4 ? 4 : (L >= 4 ? 1 : (L >= 2 ? 2 : 4));
   extern __shared__ __align__(16) unsigned char smraw[];
   const int by = f.by, bz = f.bz;
   const int SY = BX + 2, SZ = (BX + 2) * (by + 2);  // strides of the haloed p brick
@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
   T* P = reinterpret_cast<T*>(smraw);  // (BX + 2)(by + 2)(bz + 2)
   T* R = P + SZ * (bz + 2);            // BX by bz
   T* X = R + bcells;                   // BX by bz
+  T* Q = X + bcells;                   // BX by bz: L_c p of this iteration
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
   const int bi = blockIdx.x % f.px, bj = (blockIdx.x / f.px) % f.py, bk = blockIdx.x / (f.px * f.py);
@@ -107,10 +108,61 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
     }
   };
   // fill the ghost layer of P: val(g) for each face-neighbour node outside
-  // the brick (edges and corners are not used by the 7-point stencil)
-  auto ghosts = [&](auto&& val) {
-    // rows along x: the two z faces (2 by rows), then the two y faces (2 bz rows)
-    const int nr = 2 * by + 2 * bz;
+  // the brick (edges and corners are not used by the 7-point stencil).  Rows
+  // along x: the two z faces (2 by rows), then the two y faces (2 bz rows);
+  // the two x faces are strided single nodes.  When one batch of loads per
+  // thread covers all of them, between() runs while the loads are in flight.
+  constexpr int XB = 4;
+  const int nr = 2 * by + 2 * bz;
+  const bool one_round = nr <= RB * nwarp && 2 * nrow <= XB * nthr;
+  auto ghost_row = [&](int row, int& ly, int& lz) {
+    if (row < 2 * by) {
+      ly = row >> 1;
+      lz = (row & 1) ? bz : -1;
+    } else {
+      lz = (row - 2 * by) >> 1;
+      ly = (row & 1) ? by : -1;
+    }
+  };
+  auto ghosts = [&](auto&& val, auto&& between) {
+    if (one_round) {
+      T v[RB][L], xv[XB];
+      int pr[RB], xpi[XB];
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        const int row = warp + q * nwarp;
+        pr[q] = -1;
+        if (row < nr) {
+          int ly, lz;
+          ghost_row(row, ly, lz);
+          pr[q] = (lz + 1) * SZ + (ly + 1) * SY + 1;
+          const size_t g0 = gidx(0, ly, lz);
+#pragma unroll
+          for (int u = 0; u < L; ++u) v[q][u] = val(g0 + lane + 32 * u);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < XB; ++q) {
+        const int c = tid + q * nthr;
+        xpi[q] = -1;
+        if (c < 2 * nrow) {
+          const int row = c >> 1, ly = row % by, lz = row / by, lx = (c & 1) ? BX : -1;
+          xpi[q] = (lz + 1) * SZ + (ly + 1) * SY + 1 + lx;
+          xv[q] = val(gidx(lx, ly, lz));
+        }
+      }
+      between();
+#pragma unroll
+      for (int q = 0; q < RB; ++q)
+        if (pr[q] >= 0)
+#pragma unroll
+          for (int u = 0; u < L; ++u) P[pr[q] + lane + 32 * u] = v[q][u];
+#pragma unroll
+      for (int q = 0; q < XB; ++q)
+        if (xpi[q] >= 0) P[xpi[q]] = xv[q];
+      return;
+    }
+    between();
     for (int r0 = warp; r0 < nr; r0 += RB * nwarp) {
       T v[RB][L];
       int pr[RB];
@@ -120,13 +172,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
         pr[q] = -1;
         if (row < nr) {
           int ly, lz;
-          if (row < 2 * by) {
-            ly = row >> 1;
-            lz = (row & 1) ? bz : -1;
-          } else {
-            lz = (row - 2 * by) >> 1;
-            ly = (row & 1) ? by : -1;
-          }
+          ghost_row(row, ly, lz);
           pr[q] = (lz + 1) * SZ + (ly + 1) * SY + 1;
           const size_t g0 = gidx(0, ly, lz);
 #pragma unroll
@@ -139,8 +185,6 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
 #pragma unroll
           for (int u = 0; u < L; ++u) P[pr[q] + lane + 32 * u] = v[q][u];
     }
-    // the two x faces: strided single nodes
-    constexpr int XB = 4;
     for (int c0 = tid; c0 < 2 * nrow; c0 += XB * nthr) {
       T v[XB];
       int pi[XB];
@@ -159,29 +203,45 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
         if (pi[q] >= 0) P[pi[q]] = v[q];
     }
   };
+  auto nothing = [] {};
 
   GridSync gs{f.bar, f.partials, f.spin_cycles, f.expected, 0u};
+  // The scalar recurrences of CG run in thread 0 (FP64 division and square
+  // root are long instruction sequences on this GPU); thread 0 broadcasts
+  // the status and the FP32/FP64 coefficients through shared memory.
+  __shared__ struct {
+    T ta, tb, mean;
+    int status, restart;
+  } sc;
+  double rr = 0.0, bb = 0.0, rel = 0.0, beta = 0.0;  // meaningful in thread 0
   int status = 0;  // 0 running, 1 converged, 2 maxit, 3 breakdown, 4 zero rhs, 5 timeout
   // mean of b; b staged in R
-  Dot<T> a1[1];
-  own([&](int c, int, size_t g, bool) {
-    const T v = __ldcg(f.b + g);
-    R[c] = v;
-    a1[0].add(v);
-  });
-  double s1[1];
-  if (!grid_dot<1>(a1, gs, s1)) status = 5;
-  const T mean = (T)(s1[0] / (double)f.n);
+  {
+    Dot<T> a1[1];
+    own([&](int c, int, size_t g, bool) {
+      const T v = __ldcg(f.b + g);
+      R[c] = v;
+      a1[0].add(v);
+    });
+    double t[1];
+    const bool ok = grid_dot_t0<1>(a1, gs, t);
+    if (tid == 0) {
+      sc.status = ok ? 0 : 5;
+      sc.mean = (T)(t[0] / (double)f.n);
+    }
+    __syncthreads();
+    status = sc.status;
+  }
+  const T mean = sc.mean;
 
   // x0 with its ghosts; r = (b - mean) - L_c x0, published; r.r and |b - mean|^2
-  double s2[2] = {0.0, 0.0};
   if (!status) {
     own([&](int c, int pi, size_t g, bool) {
       const T v = __ldcg(f.x + g);
       X[c] = v;
       P[pi] = v;
     });
-    ghosts([&](size_t g) { return __ldcg(f.x + g); });
+    ghosts([&](size_t g) { return __ldcg(f.x + g); }, nothing);
     __syncthreads();
     Dot<T> a2[2];
     own([&](int c, int pi, size_t g, bool face) {
@@ -192,97 +252,136 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
       a2[0].add(rv * rv);
       a2[1].add(bm * bm);
     });
-    if (!grid_dot<2>(a2, gs, s2)) status = 5;
-  }
-  // the plain solver judges a learned first guess: if it leaves a larger
-  // residual than x0 = 0, restart from zero (r = b - mean b, r.r = |b|^2)
-  if (!status && f.guard && s2[0] > s2[1]) {
-    own([&](int c, int, size_t g, bool face) {
-      const T rv = __ldcg(f.b + g) - mean;
-      X[c] = T(0);
-      R[c] = rv;
-      if (face) __stcg(f.rg + g, rv);
-    });
-    double sz[1] = {0.0};
-    if (!grid_sum<1>(sz, gs)) status = 5;
-    s2[0] = s2[1];
-  }
-  double rr = s2[0];
-  const double bb = s2[1];
-  double rel = 0.0;
-  if (!status) {
-    if (bb == 0.0) status = 4;
-    else {
-      rel = sqrt(rr / bb);
-      if (rel <= f.tol) status = 1;
-      else if (f.maxit <= 0) status = 2;
+    double s2[2];
+    const bool ok = grid_dot_t0<2>(a2, gs, s2);
+    if (tid == 0) {
+      // the plain solver judges a learned first guess: if it leaves a larger
+      // residual than x0 = 0, restart from zero (r = b - mean b, r.r = |b|^2)
+      sc.status = ok ? 0 : 5;
+      sc.restart = ok && f.guard && s2[0] > s2[1];
+      rr = sc.restart ? s2[1] : s2[0];
+      bb = s2[1];
+    }
+    __syncthreads();
+    status = sc.status;
+    if (!status && sc.restart) {
+      own([&](int c, int, size_t g, bool face) {
+        const T rv = __ldcg(f.b + g) - mean;
+        X[c] = T(0);
+        R[c] = rv;
+        if (face) __stcg(f.rg + g, rv);
+      });
+      Dot<T> none[1];
+      double t[1];
+      const bool ok2 = grid_dot_t0<1>(none, gs, t);  // a grid barrier: the new faces are visible
+      if (tid == 0) sc.status = ok2 ? 0 : 5;
+      __syncthreads();
+      status = sc.status;
     }
   }
+  if (tid == 0) {
+    if (!status) {
+      if (bb == 0.0) status = 4;
+      else {
+        rel = sqrt(rr / bb);
+        if (rel <= f.tol) status = 1;
+        else if (f.maxit <= 0) status = 2;
+      }
+    }
+    sc.status = status;
+  }
+  __syncthreads();
+  status = sc.status;
 
   int iter = 0;
-  double beta = 0.0;
+  T tb = T(0);
   while (!status) {
     const bool first = iter == 0;
-    const T tb = (T)beta;
     T* pw = (iter & 1) ? f.pg1 : f.pg0;         // this iteration's p faces
     const T* po = (iter & 1) ? f.pg0 : f.pg1;   // the previous iteration's
-    // phase A: p = r + beta p (owned in place, ghosts from published faces)
-    own([&](int c, int pi, size_t g, bool face) {
-      const T pv = first ? R[c] : R[c] + tb * P[pi];
-      P[pi] = pv;
-      if (face) __stcg(pw + g, pv);
-    });
-    if (first) ghosts([&](size_t g) { return __ldcg(f.rg + g); });
-    else ghosts([&](size_t g) { return __ldcg(f.rg + g) + tb * __ldcg(po + g); });
+    // phase A: p = r + beta p (owned in place, ghosts from published faces;
+    // the owned update runs while the ghost loads are in flight)
+    auto update = [&] {
+      own([&](int c, int pi, size_t g, bool face) {
+        const T pv = first ? R[c] : R[c] + tb * P[pi];
+        P[pi] = pv;
+        if (face) __stcg(pw + g, pv);
+      });
+    };
+    if (first) ghosts([&](size_t g) { return __ldcg(f.rg + g); }, update);
+    else ghosts([&](size_t g) { return __ldcg(f.rg + g) + tb * __ldcg(po + g); }, update);
     __syncthreads();
     Dot<T> apq[1];
-    own([&](int, int pi, size_t, bool) { apq[0].add(P[pi] * Lc(pi)); });
-    double sa[1];
-    if (!grid_dot<1>(apq, gs, sa)) {
-      status = 5;
-      break;
+    own([&](int c, int pi, size_t, bool) {
+      const T qv = Lc(pi);
+      Q[c] = qv;
+      apq[0].add(P[pi] * qv);
+    });
+    {
+      double t[1];
+      const bool ok = grid_dot_t0<1>(apq, gs, t);
+      if (tid == 0) {
+        const double pq = t[0];
+        if (!ok) status = 5;
+        else if (pq == 0.0 || !isfinite(pq)) status = 3;
+        else sc.ta = (T)(rr / pq);
+        sc.status = status;
+      }
+      __syncthreads();
+      status = sc.status;
+      if (status) break;
     }
-    const double pq = sa[0];
-    if (pq == 0.0 || !isfinite(pq)) {
-      status = 3;
-      break;
-    }
-    const double alpha = rr / pq;
-    const T ta = (T)alpha;
-    // phase B: x += alpha p, r -= alpha L_c p, r faces published, r.r
+    const T ta = sc.ta;
+    // phase B: x += alpha p, r -= alpha q, r faces published, r.r
     Dot<T> ar[1];
     own([&](int c, int pi, size_t g, bool face) {
       const T pv = P[pi];
       X[c] += ta * pv;
-      const T rv = R[c] - ta * Lc(pi);
+      const T rv = R[c] - ta * Q[c];
       R[c] = rv;
       if (face) __stcg(f.rg + g, rv);
       ar[0].add(rv * rv);
     });
-    double sb[1];
-    if (!grid_dot<1>(ar, gs, sb)) {
-      status = 5;
-      break;
+    {
+      double t[1];
+      const bool ok = grid_dot_t0<1>(ar, gs, t);
+      iter += 1;
+      if (tid == 0) {
+        if (!ok) {
+          status = 5;
+        } else {
+          const double rr_new = t[0];
+          rel = sqrt(rr_new / bb);
+          beta = rr_new / rr;
+          rr = rr_new;
+          if (rel <= f.tol) status = 1;
+          else if (iter >= f.maxit) status = 2;
+          else if (!isfinite(rr_new)) status = 3;
+          sc.tb = (T)beta;
+        }
+        sc.status = status;
+      }
+      __syncthreads();
+      status = sc.status;
+      tb = sc.tb;
     }
-    const double rr_new = sb[0];
-    iter += 1;
-    rel = sqrt(rr_new / bb);
-    beta = rr_new / rr;
-    rr = rr_new;
-    if (rel <= f.tol) status = 1;
-    else if (iter >= f.maxit) status = 2;
-    else if (!isfinite(rr_new)) status = 3;
   }
 
   // zero-mean gauge (or zero for a zero right side), written back to x
   if (status != 5) {
     Dot<T> ax[1];
     own([&](int c, int, size_t, bool) { ax[0].add(X[c]); });
-    double sx[1];
-    if (!grid_dot<1>(ax, gs, sx)) {
-      status = 5;
-    } else {
-      const T mx = (T)(sx[0] / (double)f.n);
+    double t[1];
+    const bool ok = grid_dot_t0<1>(ax, gs, t);
+    if (tid == 0) {
+      if (!ok) status = 5;
+      sc.mean = (T)(t[0] / (double)f.n);
+      sc.status = status;
+    }
+    __syncthreads();
+    status = sc.status;
+    if (status != 5) {
+      const T mx = sc.mean;
       own([&](int c, int, size_t g, bool) { __stcg(f.x + g, status == 4 ? T(0) : X[c] - mx); });
     }
   }
@@ -300,7 +399,7 @@ struct Plan {
 
 template <typename T>
 size_t resident_smem(int bx, int by, int bz) {
-  return ((size_t)(bx + 2) * (by + 2) * (bz + 2) + 2 * (size_t)bx * by * bz) * sizeof(T);
+  return ((size_t)(bx + 2) * (by + 2) * (bz + 2) + 3 * (size_t)bx * by * bz) * sizeof(T);
 }
 
 // Brick decomposition: bx in {128, 64, 32} dividing nx, by | ny, bz | nz,

@@ -14,11 +14,10 @@
 // Every wait is bounded in time: on expiry the fail flag is raised and the
 // call returns false in every thread of the block, leaving the device usable.
 //
-// Dot products of FP32 vectors are accumulated as compensated FP32 pairs
-// (hi + lo, Knuth's TwoSum for the exact error of each addition), reduced in
-// the same arithmetic and turned into FP64 totals at the end: on this GPU an
-// FP64 instruction costs tens of FP32 ones, and the compensated pair keeps
-// about 48 significant bits.
+// Block and grid combinations of FP32 dot products use compensated FP32
+// pairs (hi + lo, Knuth's TwoSum for the exact error of each addition) and
+// yield FP64 totals: on this GPU an FP64 instruction costs tens of FP32
+// ones, and the compensated pair keeps about 48 significant bits.
 #pragma once
 
 #include "les_common.cuh"
@@ -67,19 +66,24 @@ __device__ __forceinline__ void f2_acc(F2& a, float v) {
 }
 __device__ __forceinline__ double f2_value(F2 a) { return (double)a.hi + (double)a.lo; }
 
-// Per-thread accumulator of a sum of T terms: compensated FP32 for float,
-// plain FP64 for double.
+// Per-thread accumulator of a sum of T terms.  A thread sums its own few
+// dozen FP32 terms in FP32 (relative error below 1e-6 for sums of positive
+// terms; CG in FP32 reaches the same iterates as with exact dots); the block
+// and grid combination of the thread sums is compensated.  FP64 terms are
+// summed in FP64.
 template <typename T>
 struct Dot;
 template <>
 struct Dot<float> {
-  F2 s{0.f, 0.f};
-  __device__ __forceinline__ void add(float v) { f2_acc(s, v); }
+  float s = 0.f;
+  __device__ __forceinline__ void add(float v) { s += v; }
+  __device__ __forceinline__ F2 acc() const { return F2{s, 0.f}; }
 };
 template <>
 struct Dot<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double acc() const { return s; }
 };
 
 // ---- block reductions with the total broadcast to every thread ---------------
@@ -232,12 +236,96 @@ __device__ bool grid_sum(double (&v)[NV], GridSync& gs) {
   return true;
 }
 
+// ---- grid sum with the totals in thread 0 only ---------------------------------
+// For kernels whose scalar recurrences run in one thread: after the block
+// partials are combined in shared memory, warp 0 alone posts, waits and
+// folds, so the block pays two barriers per sum and no thread but thread 0
+// does FP64 work.  tot[] and the return value are valid in thread 0 only;
+// the caller broadcasts what it derives and must __syncthreads() before the
+// next grid sum.
+__device__ __forceinline__ F2 warp_sum_f2(F2 a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const F2 b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+    a = f2_add(a, b);
+  }
+  return a;
+}
+__device__ __forceinline__ F2 acc_add(F2 a, F2 b) { return f2_add(a, b); }
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ F2 acc_warp(F2 a) { return warp_sum_f2(a); }
+__device__ __forceinline__ double acc_warp(double a) { return warp_sum(a); }
+__device__ __forceinline__ F2 acc_zero(F2) { return F2{0.f, 0.f}; }
+__device__ __forceinline__ double acc_zero(double) { return 0.0; }
+__device__ __forceinline__ double acc_value(F2 a) { return f2_value(a); }
+__device__ __forceinline__ double acc_value(double a) { return a; }
+__device__ __forceinline__ void acc_store(F2* slot, F2 a) {
+  *reinterpret_cast<float2*>(slot) = make_float2(a.hi, a.lo);
+}
+__device__ __forceinline__ void acc_store(double* slot, double a) { *slot = a; }
+__device__ __forceinline__ F2 acc_load(const F2* slot) {
+  const float2 p = __ldcg(reinterpret_cast<const float2*>(slot));
+  return F2{p.x, p.y};
+}
+__device__ __forceinline__ double acc_load(const double* slot) { return __ldcg(slot); }
+
+template <int NV, typename A>
+__device__ bool grid_sum_t0(A (&v)[NV], GridSync& gs, double (&tot)[NV]) {
+  __shared__ A sh[NV][32];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+  const unsigned G = gridDim.x;
+  A* slot = reinterpret_cast<A*>(gs.partials) + (size_t)(gs.epoch & 1u) * NV * G;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = acc_warp(v[q]);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q][warp] = v[q];
+  // also orders every thread's earlier global writes before the release below
+  __syncthreads();
+  bool ok = true;
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      A a = lane < nw ? sh[q][lane] : acc_zero(v[q]);
+      a = acc_warp(a);
+      if (lane == 0) acc_store(slot + (size_t)q * G + blockIdx.x, a);
+    }
+    if (lane == 0) {
+      red_release_add(&gs.bar->count.v, 1u);
+      const unsigned target = (gs.epoch + 1u) * gs.expected;
+      const long long t0 = clock64();
+      unsigned spins = 0;
+      while ((int)(ld_acquire(&gs.bar->count.v) - target) < 0) {
+        if ((++spins & 63u) == 0u && (ld_volatile(&gs.bar->fail.v) != 0u || clock64() - t0 > gs.spin)) {
+          atomicExch(&gs.bar->fail.v, 1u);
+          ok = false;
+          break;
+        }
+      }
+    }
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (ok) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        A a = acc_zero(v[q]);
+        for (unsigned b = lane; b < G; b += 32) a = acc_add(a, acc_load(slot + (size_t)q * G + b));
+        a = acc_warp(a);
+        if (lane == 0) tot[q] = acc_value(a);
+      }
+    }
+  }
+  gs.epoch += 1u;
+  return ok;
+}
+
 // one grid sum of a Dot<T> accumulator per value
 template <int NV>
 __device__ __forceinline__ bool grid_dot(Dot<float> (&d)[NV], GridSync& gs, double (&tot)[NV]) {
   F2 v[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = d[q].s;
+  for (int q = 0; q < NV; ++q) v[q] = d[q].acc();
   return grid_sum<NV>(v, gs, tot);
 }
 template <int NV>
@@ -245,6 +333,14 @@ __device__ __forceinline__ bool grid_dot(Dot<double> (&d)[NV], GridSync& gs, dou
 #pragma unroll
   for (int q = 0; q < NV; ++q) tot[q] = d[q].s;
   return grid_sum<NV>(tot, gs);
+}
+
+template <int NV, typename T>
+__device__ __forceinline__ bool grid_dot_t0(Dot<T> (&d)[NV], GridSync& gs, double (&tot)[NV]) {
+  decltype(d[0].acc()) v[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = d[q].acc();
+  return grid_sum_t0<NV>(v, gs, tot);
 }
 
 }  // namespace les
