@@ -251,9 +251,10 @@ int les_poisson_solve_static(const les_config *cfg, const void *d_rho0, const vo
 
 /* ---- tuning of the persistent CG solve ---------------------------------------
  * The CG solve runs as one persistent cooperative launch when solver_path = 0
- * and the grid is eligible.  A thread block of 32 x cg_tile_rows threads owns
- * a tile of (32 * 16 B of cells) x cg_tile_rows x cg_tile_planes nodes; the
- * grid is capped by occupancy and cg_max_blocks.  Each grid-barrier wait ends
+ * (compact operator).  For cg_variant 1 and 2 a thread block of
+ * 32 x cg_tile_rows threads owns a tile of (32 * 16 B of cells) x
+ * cg_tile_rows x cg_tile_planes nodes; every grid is capped by occupancy and
+ * cg_max_blocks.  Each grid-barrier wait ends
  * after barrier_timeout_ms; the solve then returns LES_ERR_TIMEOUT and the
  * device stays usable.  fault_missing_arrivals is a failure-detection test
  * hook: the barrier then waits for that many blocks that never arrive, so
@@ -278,11 +279,21 @@ typedef struct les_tuning {
   double   barrier_timeout_ms;     /* > 0                                   */
   int32_t  fault_missing_arrivals; /* 0 in production                      */
   int32_t  stencil_path;           /* 0 rolling (default), 1 direct, 2 tiled */
-  int32_t  cg_variant;             /* persistent CG: 0 standard CG (two grid
-                                      barriers per iteration, default), 1
-                                      Chronopoulos-Gear (one; its recurrences
-                                      drift in FP32 and may need more
-                                      iterations)                          */
+  int32_t  cg_variant;             /* persistent CG: 0 (default) the
+                                      standard CG iterates -- in shared
+                                      memory when the grid fits there (see
+                                      cg_resident), else variant 2 on
+                                      tile-aligned grids, else variant 3;
+                                      1 Chronopoulos-Gear (one barrier; its
+                                      vector recurrences drift in FP32 and
+                                      may need more iterations); 2 the
+                                      two-phase streaming CG (two barriers
+                                      per iteration); 3 one pass over memory
+                                      and one grid reduction per iteration,
+                                      any grid.  1 and 2 need nx a multiple
+                                      of 128 (FP32) / 64 (FP64) and ny of
+                                      cg_tile_rows, else the per-phase
+                                      launches run                         */
   int32_t  cg_resident;            /* 0 (default): standard CG keeps its
                                       vectors in shared memory when the grid
                                       fits there; 1: always streams them

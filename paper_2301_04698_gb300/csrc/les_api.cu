@@ -271,6 +271,7 @@ int fields_per_cell(const les_config& c, int id) {
     case KI_FINISH: return 2;
     case KI_CG_FUSED: return 0;  // varies with the iteration count
     case KI_CG_RESIDENT: return 0;
+    case KI_CG_ROLL: return 0;
     default: return 0;
   }
 }
@@ -474,7 +475,7 @@ namespace les {
 const char* const kKernelNames[KI_COUNT] = {
     "thermo", "radiation", "nu", "nu_half", "scalar", "momentum", "rhs", "correct", "diag",
     "cfl", "apply", "sum", "cg_init", "cg_matvec", "cg_update", "jacobi", "finish", "ctl", "cg_fused",
-    "unet_conv", "unet_wgrad", "unet_adam", "cg_resident"};
+    "unet_conv", "unet_wgrad", "unet_adam", "cg_resident", "cg_roll"};
 
 template <typename T>
 Grid<T> make_grid(const les_config& c, int zc) {
@@ -777,7 +778,8 @@ int les_set_tuning(les_handle* h, const les_tuning* in) {
   if (in->stencil_path < 0 || in->stencil_path > 2)
     return h->fail(LES_ERR_INVALID_ARG, "stencil_path must be 0, 1 or 2");
   h->fused.stencil_path = in->stencil_path;
-  if (in->cg_variant != 0 && in->cg_variant != 1) return h->fail(LES_ERR_INVALID_ARG, "cg_variant must be 0 or 1");
+  if (in->cg_variant < 0 || in->cg_variant > 3)
+    return h->fail(LES_ERR_INVALID_ARG, "cg_variant must be 0, 1, 2 or 3");
   h->fused.variant = in->cg_variant;
   if (in->cg_resident != 0 && in->cg_resident != 1) return h->fail(LES_ERR_INVALID_ARG, "cg_resident must be 0 or 1");
   h->fused.resident = in->cg_resident;

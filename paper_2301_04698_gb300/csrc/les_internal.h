@@ -92,7 +92,9 @@ struct FusedCfg {
   double timeout_ms = 2000.0;
   int missing = 0;                      // test hook: arrivals that never come
   int stencil_path = 0;                 // 0 rolling z-march, 1 direct-load, 2 tiled
-  int variant = 0;                      // 0 standard CG (2 barriers / iteration), 1 Chronopoulos-Gear (1)
+  int variant = 0;                      // 0 standard iterates (resident, else two-phase streaming when
+                                        // tile-aligned, else one-pass), 1 Chronopoulos-Gear,
+                                        // 2 two-phase streaming, 3 one-pass one-reduction
   int resident = 0;                     // 0 shared-memory-resident CG when the grid fits, 1 never
 };
 
@@ -104,7 +106,7 @@ struct LaunchCfg {
 enum KernelId : int {
   KI_THERMO = 0, KI_RADIATION, KI_NU, KI_NU_HALF, KI_SCALAR, KI_MOMENTUM, KI_RHS, KI_CORRECT,
   KI_DIAG, KI_CFL, KI_APPLY, KI_SUM, KI_CG_INIT, KI_CG_MATVEC, KI_CG_UPDATE, KI_JACOBI, KI_FINISH,
-  KI_CTL, KI_CG_FUSED, KI_UNET_CONV, KI_UNET_WGRAD, KI_UNET_ADAM, KI_CG_RESIDENT, KI_COUNT
+  KI_CTL, KI_CG_FUSED, KI_UNET_CONV, KI_UNET_WGRAD, KI_UNET_ADAM, KI_CG_RESIDENT, KI_CG_ROLL, KI_COUNT
 };
 extern const char* const kKernelNames[KI_COUNT];
 
@@ -285,6 +287,11 @@ bool fused_cg_eligible(const Grid<T>& g, int op, int solver, int ty);
 template <typename T>
 int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
                         int* iters, double* rel, std::string* err);
+// Persistent one-reduction CG, one pass per iteration (les_cg_roll.cu): any
+// grid, compact operator.
+template <typename T>
+int poisson_solve_roll(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
+                       int* iters, double* rel, std::string* err);
 // Persistent CG with its vectors in shared memory (les_cg_resident.cu).
 // Sets *used = false and returns LES_OK without launching when the grid has
 // no brick decomposition that fits on chip; the caller then streams.

@@ -302,12 +302,21 @@ cudaError_t launch_apply(const SolverArgs<T>& a, int op, const T* x, T* y) {
 template <typename T>
 int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxit, int* iters, double* rel,
                   std::string* err) {
-  if (a.fused && a.bar && a.fused->resident == 0 && a.fused->variant == 0) {
+  // persistent CG: in shared memory when the grid fits there; else the
+  // two-phase streaming kernel on tile-aligned grids (variant 0 or 2) or the
+  // one-pass kernel (variant 0 on other grids, or variant 3); variant 1 is
+  // Chronopoulos-Gear
+  const bool cg_c = a.op == LES_OP_COMPACT && a.solver == LES_SOLVER_CG;
+  const int var = a.fused ? a.fused->variant : -1;
+  const bool tiled = a.fused && fused_cg_eligible(a.g, a.op, a.solver, a.fused->ty);
+  if (a.bar && cg_c && var == 0 && a.fused->resident == 0) {
     bool used = false;
     const int rc = poisson_solve_resident<T>(a, *a.fused, b, x, tol, maxit, iters, rel, err, &used);
     if (used || rc != LES_OK) return rc;
   }
-  if (a.fused && a.bar && fused_cg_eligible(a.g, a.op, a.solver, a.fused->ty))
+  if (a.bar && cg_c && (var == 3 || (var == 0 && !tiled)))
+    return poisson_solve_roll<T>(a, *a.fused, b, x, tol, maxit, iters, rel, err);
+  if (a.bar && tiled && var >= 0 && var <= 2)
     return poisson_solve_fused<T>(a, *a.fused, b, x, tol, maxit, iters, rel, err);
   auto fail = [&](cudaError_t e, const char* where) {
     if (err) *err = std::string(where) + ": " + cudaGetErrorString(e);

@@ -297,7 +297,7 @@ def test_ragged_and_minimum_grids(les_mod, shape):
 # persistent single-launch CG (fast path for nx a multiple of the tile width)
 
 
-def _fused_launches(sim, names=("cg_fused", "cg_resident")):
+def _fused_launches(sim, names=("cg_fused", "cg_resident", "cg_roll")):
     return sum(k["launches"] for k in sim.profile_read() if k["name"] in names)
 
 
@@ -316,10 +316,11 @@ def test_fused_cg_matches_oracle(les_mod, precision, walls, shape):
     tol = 1e-11 if precision == 64 else 1e-6
     bt = torch.from_numpy(b).to("cuda", dt)
     results = []
-    # (variant, tile rows, tile planes, streaming only): the standard variant
-    # runs both streaming and with its vectors in shared memory
-    for variant, ty, zc, stream in ((1, 4, 4, 1), (1, 1, 1, 1), (1, 2, 3, 1), (1, 8, 16, 1), (0, 4, 4, 1),
-                                    (0, 2, 3, 1), (0, 4, 4, 0)):
+    # (variant, tile rows, tile planes, streaming only): variants 1 and 2 run
+    # the tiled streaming kernels; variant 0 runs in shared memory or, when
+    # told to stream, as one pass and one reduction per iteration
+    for variant, ty, zc, stream in ((1, 4, 4, 1), (1, 1, 1, 1), (1, 2, 3, 1), (1, 8, 16, 1), (2, 4, 4, 1),
+                                    (2, 2, 3, 1), (0, 4, 4, 0), (3, 4, 4, 1)):
         if ny % ty:
             continue
         sim.set_tuning(cg_tile_rows=ty, cg_tile_planes=zc, cg_variant=variant, cg_resident=stream)
@@ -327,7 +328,8 @@ def test_fused_cg_matches_oracle(les_mod, precision, walls, shape):
         x = torch.zeros_like(bt)
         rc, it, res = sim.poisson_solve(bt, x, tol, 20000)
         assert rc == 0 and res <= tol
-        assert _fused_launches(sim, ("cg_resident",) if stream == 0 else ("cg_fused",)) == 1
+        kern = {1: "cg_fused", 2: "cg_fused", 3: "cg_roll"}.get(variant, "cg_resident")
+        assert _fused_launches(sim, (kern,)) == 1, (variant, stream)
         xn = x.cpu().double().numpy()
         # zero-mean gauge, to rounding of the field's magnitude
         assert abs(xn.mean()) < (1e-14 if precision == 64 else 1e-6) * np.abs(xn).max()
@@ -342,17 +344,17 @@ def test_fused_cg_matches_oracle(les_mod, precision, walls, shape):
     for variant, it, xn in results:
         # standard CG follows the same iterates; the one-barrier variant keeps
         # s = A p and w = A r by recurrence, which drifts in FP32
-        if variant == 0 or precision == 64:
+        if variant != 1 or precision == 64:
             assert abs(it - it1) <= 3, (variant, it, it1)
         assert rel(xn, x1.cpu().double().numpy()) < (1e-9 if precision == 64 else 5e-4)
 
 
-@pytest.mark.parametrize("stream", [0, 1])
-def test_fused_cg_barrier_timeout_is_reported(les_mod, stream):
+@pytest.mark.parametrize("variant,stream,kern", [(0, 0, "cg_resident"), (3, 1, "cg_roll"), (2, 1, "cg_fused")])
+def test_fused_cg_barrier_timeout_is_reported(les_mod, variant, stream, kern):
     case = inputs.Case(name="fused", nx=128, ny=8, nz=4, dx=1.0, dy=1.0, dz=1.0, precision=32,
                        init="zero", physics=())
     sim = les_mod.Simulation(case)
-    sim.set_tuning(cg_resident=stream)
+    sim.set_tuning(cg_resident=stream, cg_variant=variant)
     b = torch.from_numpy(inputs.uniform(3, 0, case.n, -1, 1).reshape(case.shape)).to("cuda", torch.float32)
     x = torch.zeros_like(b)
     # every barrier waits for one block that never arrives: each wait must end
@@ -362,7 +364,7 @@ def test_fused_cg_barrier_timeout_is_reported(les_mod, stream):
     with pytest.raises(les_mod.LesError) as e:
         sim.poisson_solve(b, x, 1e-6, 100)
     assert e.value.status == les_mod.LES_ERR_TIMEOUT
-    assert _fused_launches(sim, ("cg_resident",) if stream == 0 else ("cg_fused",)) == 1
+    assert _fused_launches(sim, (kern,)) == 1
     sim.set_tuning(barrier_timeout_ms=2000.0, fault_missing_arrivals=0)
     x.zero_()
     rc, it, res = sim.poisson_solve(b, x, 1e-6, 1000)
@@ -379,7 +381,7 @@ def test_fused_cg_barrier_timeout_is_reported(les_mod, stream):
     (32, True, (32, 128, 4), 4)])     # more ghost rows than one batch of loads
 def test_resident_cg_matches_oracle(les_mod, precision, walls, shape, max_blocks):
     """The shared-memory-resident CG against the FP64 oracle and against the
-    streaming persistent CG, which follows the same iterates."""
+    one-reduction rolling CG, which follows the same iterates."""
     from oracle import Oracle
     nx, ny, nz = shape
     case = inputs.Case(name="res", nx=nx, ny=ny, nz=nz, dx=35.0, dy=30.0, dz=10.0, walls=walls,
@@ -393,14 +395,14 @@ def test_resident_cg_matches_oracle(les_mod, precision, walls, shape, max_blocks
     bt = torch.from_numpy(b).to("cuda", dt)
     out = {}
     for stream in (0, 1):
-        sim.set_tuning(cg_resident=stream, cg_max_blocks=max_blocks if stream == 0 else 1 << 20)
+        sim.set_tuning(cg_resident=stream, cg_variant=0 if stream == 0 else 3,
+                       cg_max_blocks=max_blocks if stream == 0 else 1 << 20)
         sim.profile_reset()
         # a nonzero first guess exercises the initial residual's ghost exchange
         x = torch.from_numpy(0.1 * inputs.uniform(24, 0, case.n, -1, 1).reshape(case.shape)).to("cuda", dt)
         rc, it, res = sim.poisson_solve(bt, x, tol, 20000)
         assert rc == 0 and res <= tol
-        if stream == 0:
-            assert _fused_launches(sim, ("cg_resident",)) == 1
+        assert _fused_launches(sim, ("cg_resident",) if stream == 0 else ("cg_roll",)) == 1
         xn = x.cpu().double().numpy()
         assert abs(xn.mean()) < (1e-14 if precision == 64 else 1e-6) * np.abs(xn).max()
         assert rel(xn, xr) < (1e-8 if precision == 64 else 5e-4), stream
@@ -409,10 +411,55 @@ def test_resident_cg_matches_oracle(les_mod, precision, walls, shape, max_blocks
     assert rel(out[0][1], out[1][1]) < (1e-9 if precision == 64 else 5e-4)
     # not converged within maxit: the status and the iteration count come back
     x = torch.zeros_like(bt)
-    sim.set_tuning(cg_resident=0, cg_max_blocks=max_blocks)
+    sim.set_tuning(cg_resident=0, cg_variant=0, cg_max_blocks=max_blocks)
     rc, it, res = sim.poisson_solve(bt, x, 1e-30, 5, allow_not_converged=True)
     assert rc == les_mod.LES_ERR_NOT_CONVERGED and it == 5
     # a zero right side returns x = 0 with no iteration
+    x = torch.ones_like(bt)
+    rc, it, res = sim.poisson_solve(torch.zeros_like(bt), x, tol, 100)
+    assert rc == 0 and it == 0 and float(x.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("precision,walls,shape", [
+    (32, True, (40, 36, 20)),      # ragged in x and y
+    (64, False, (33, 9, 17)),      # odd extents, periodic
+    (64, True, (70, 12, 2)),       # two planes between the walls
+    (32, False, (64, 16, 3)),      # three planes, periodic
+    (32, True, (96, 40, 64))])     # several z-runs per column
+def test_rolling_cg_matches_oracle(les_mod, precision, walls, shape):
+    """The one-pass, one-reduction CG on grids of any extent against the FP64
+    oracle and against the per-phase CG launches (same iterates)."""
+    from oracle import Oracle
+    nx, ny, nz = shape
+    case = inputs.Case(name="roll", nx=nx, ny=ny, nz=nz, dx=35.0, dy=30.0, dz=10.0, walls=walls,
+                       precision=precision, init="zero", physics=())
+    ref = Oracle(case.replace(precision=64))
+    b = inputs.uniform(31, 0, case.n, -1, 1).reshape(case.shape) + 0.25
+    xr, st, itr, _ = ref.poisson(b, tol=1e-12, maxit=20000)
+    dt = torch.float64 if precision == 64 else torch.float32
+    tol = 1e-11 if precision == 64 else 1e-6
+    bt = torch.from_numpy(b).to("cuda", dt)
+    x0 = torch.from_numpy(0.1 * inputs.uniform(32, 0, case.n, -1, 1).reshape(case.shape)).to("cuda", dt)
+    sim = les_mod.Simulation(case)
+    sim.set_tuning(cg_resident=1, cg_variant=3)
+    sim.profile_reset()
+    x = x0.clone()
+    rc, it, res = sim.poisson_solve(bt, x, tol, 20000)
+    assert rc == 0 and res <= tol
+    assert _fused_launches(sim, ("cg_roll",)) == 1
+    xn = x.cpu().double().numpy()
+    assert abs(xn.mean()) < (1e-14 if precision == 64 else 1e-6) * np.abs(xn).max()
+    assert rel(xn, xr) < (1e-8 if precision == 64 else 5e-4)
+    sim1 = les_mod.Simulation(case.replace(solver_path=1))
+    x1 = x0.clone()
+    rc1, it1, res1 = sim1.poisson_solve(bt, x1, tol, 20000)
+    assert _fused_launches(sim1) == 0
+    assert abs(it - it1) <= (1 if precision == 64 else 3)
+    assert rel(xn, x1.cpu().double().numpy()) < (1e-9 if precision == 64 else 5e-4)
+    # not converged within maxit, and a zero right side
+    x = torch.zeros_like(bt)
+    rc, it, res = sim.poisson_solve(bt, x, 1e-30, 5, allow_not_converged=True)
+    assert rc == les_mod.LES_ERR_NOT_CONVERGED and it == 5
     x = torch.ones_like(bt)
     rc, it, res = sim.poisson_solve(torch.zeros_like(bt), x, tol, 100)
     assert rc == 0 and it == 0 and float(x.abs().max()) == 0.0

@@ -143,12 +143,15 @@ def test_learned_warm_start_in_a_step(les_mod):
         les_mod.attach_model(sim2, small)
 
 
-def test_learned_guess_judged_by_resident_solver(les_mod):
-    """On the 32^3 grid the CG solve keeps its vectors in shared memory; the
-    learned first guess of an untrained network is judged there (kept or
-    replaced by zero) and the step reaches the zero-guess result."""
+@pytest.mark.parametrize("stream,kern", [(0, "cg_resident"), (1, "cg_roll")])
+def test_learned_guess_judged_by_persistent_solver(les_mod, stream, kern):
+    """On the 32^3 grid the CG solve keeps its vectors in shared memory (or
+    streams them, one pass per iteration); the learned first guess of an
+    untrained network is judged there (kept or replaced by zero) and the
+    step reaches the zero-guess result."""
     case = inputs.tgv(32, warm="learned", steps_tol=1e-8)
     sim = les_mod.Simulation(case)
+    sim.set_tuning(cg_resident=stream, cg_variant=0 if stream == 0 else 3)
     sim.set_state(inputs.initial_state(case))
     model = les_mod.UNet(32, max_batch=1)
     model.set_weights(U.init_weights(5))
@@ -157,7 +160,7 @@ def test_learned_guess_judged_by_resident_solver(les_mod):
     st = sim.step(2)
     assert st["not_converged"] == 0
     launches = {k["name"]: k["launches"] for k in sim.profile_read()}
-    assert launches.get("cg_resident", 0) == 2 * case.K
+    assert launches.get(kern, 0) == 2 * case.K
     sim0 = les_mod.Simulation(case.replace(warm="zero"))
     sim0.set_state(inputs.initial_state(case))
     sim0.step(2)

@@ -63,7 +63,9 @@ def test_static_solve_matches_handle_solve(les_mod, precision, walls, op):
                                           C.byref(it), C.byref(rel), err, len(err))
         torch.cuda.synchronize()
         assert rc == les_mod.LES_OK, err.value
-        assert rel.value <= tol and it.value == it_ref
+        # the handle's solver may be a different (persistent) CG kernel whose
+        # sums round in another order: the same iterates to within rounding
+        assert rel.value <= tol and abs(it.value - it_ref) <= (1 if precision == 64 else 3)
         assert _rel(x.cpu().double().numpy(), x_ref.cpu().double().numpy()) < (1e-9 if precision == 64 else 1e-5), call
 
 
