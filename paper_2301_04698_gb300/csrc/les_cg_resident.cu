@@ -71,6 +71,9 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
   T* R = P + SZ * (bz + 2);            // BX by bz
   T* X = R + bcells;                   // BX by bz
   T* Q = X + bcells;                   // BX by bz: L_c p of this iteration
+  // per brick row: P offset | face bit, global offset (8-byte aligned: the
+  // T arrays above hold an even number of elements)
+  int2* ROWS = reinterpret_cast<int2*>(Q + bcells);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
   const int bi = blockIdx.x % f.px, bj = (blockIdx.x / f.px) % f.py, bk = blockIdx.x / (f.px * f.py);
@@ -94,12 +97,21 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
   };
   // body(c, pi, g, face) for every owned node: c its index in R / X, pi in P,
   // g in global memory; face: the node lies on the brick surface
+  // the row table: row index arithmetic once per launch, not once per pass
+  const size_t gbase = ((size_t)k0 * f.ny + j0) * f.nx + i0;
+  for (int row = tid; row < nrow; row += nthr) {
+    const int ly = row % by, lz = row / by;
+    const bool rface = ly == 0 || ly == by - 1 || lz == 0 || lz == bz - 1;
+    const int prow = (lz + 1) * SZ + (ly + 1) * SY + 1;
+    ROWS[row] = make_int2(prow | (rface ? (int)0x80000000u : 0), (lz * f.ny + ly) * f.nx);
+  }
+  __syncthreads();
   auto own = [&](auto&& body) {
     for (int row = warp; row < nrow; row += nwarp) {
-      const int ly = row % by, lz = row / by;
-      const bool rface = ly == 0 || ly == by - 1 || lz == 0 || lz == bz - 1;
-      const size_t grow = ((size_t)(k0 + lz) * f.ny + (j0 + ly)) * f.nx + i0;
-      const int prow = (lz + 1) * SZ + (ly + 1) * SY + 1;
+      const int2 t = ROWS[row];
+      const bool rface = t.x < 0;
+      const int prow = t.x & 0x7fffffff;
+      const size_t grow = gbase + (unsigned)t.y;
 #pragma unroll
       for (int u = 0; u < L; ++u) {
         const int lx = lane + 32 * u;
@@ -399,7 +411,8 @@ struct Plan {
 
 template <typename T>
 size_t resident_smem(int bx, int by, int bz) {
-  return ((size_t)(bx + 2) * (by + 2) * (bz + 2) + 3 * (size_t)bx * by * bz) * sizeof(T);
+  return ((size_t)(bx + 2) * (by + 2) * (bz + 2) + 3 * (size_t)bx * by * bz) * sizeof(T) +
+         (size_t)by * bz * sizeof(int2);
 }
 
 // Brick decomposition: bx in {128, 64, 32} dividing nx, by | ny, bz | nz,
