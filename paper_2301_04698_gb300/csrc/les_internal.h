@@ -227,7 +227,10 @@ template <typename T>
 cudaError_t launch_momentum_tiled(const StageArgs<T>& a, int max_blocks, const T* uk, const T* vk, const T* wk,
                                   const T* un, const T* vn, const T* wn, const T* p, const T* b, T* ou, T* ov,
                                   T* ow);
-// rolling-window predictors (les_stencil_roll.cu)
+// rolling-window predictors and Poisson right side (les_stencil_roll.cu)
+template <typename T>
+cudaError_t launch_rhs_roll(const StageArgs<T>& a, int op, const T* ou, const T* ov, const T* ow, const T* psi,
+                            T* rhs);
 template <typename T>
 cudaError_t launch_scalar_roll(const StageArgs<T>& a, int max_blocks, const T* u, const T* v, const T* w,
                                const T* b, const T* thk, const T* qtk, const T* thh, const T* qth, const T* srad,

@@ -1,5 +1,5 @@
-// les_stencil_roll.cu -- momentum and scalar predictors as 2.5-D z-marches
-// with ring buffers (Sec. 2.3-2.4: QUICK advection, Smagorinsky-Lilly
+// les_stencil_roll.cu -- momentum and scalar predictors (and the Poisson
+// right side) as 2.5-D z-marches with ring buffers (Sec. 2.3-2.4: QUICK advection, Smagorinsky-Lilly
 // viscosity with f_B, SGS stress and diffusion, buoyancy, Coriolis, sponge,
 // pressure gradient, subsidence, radiation and surface fluxes).
 //
@@ -493,6 +493,88 @@ __global__ void __launch_bounds__(RX* RY) k_scalar_roll(ScaRoll<T> a) {
   }
 }
 
+// ---- a4 (second half): Poisson right side as per-column z-marches ----------------
+// rhs = (alpha0 / dt) D(rho0 u^) - C(psi) (compact operator, Appendix A) or
+// D(rho0 u^) / dt (consistent operator).  One thread per column: the z
+// neighbours of w^ and psi live in register windows that roll with k; the
+// x / y neighbours are plain loads that the L1 serves for the warp's row.
+template <typename T>
+struct RhsRoll {
+  Grid<T> g;
+  Phys<T> ph;
+  int op, zrun, nchunk;
+  const T *ou, *ov, *ow, *psi;
+  T* rhs;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rhs_roll(RhsRoll<T> a) {
+  const Grid<T>& g = a.g;
+  const Phys<T>& ph = a.ph;
+  const long long ncol = (long long)g.nx * g.ny;
+  const long long nitem = ncol * a.nchunk;
+  const size_t plane = (size_t)ncol;
+  const T hx = T(0.5) * g.idx, hy = T(0.5) * g.idy, hz = T(0.5) * g.idz;
+  const T c4x = T(0.25) * g.idx * g.idx, c4y = T(0.25) * g.idy * g.idy, c4z = T(0.25) * g.idz * g.idz;
+  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < nitem;
+       it += (long long)gridDim.x * blockDim.x) {
+    const long long col = it % ncol;
+    const int chunk = (int)(it / ncol);
+    const int i = (int)(col % g.nx), j = (int)(col / g.nx);
+    const int k0 = chunk * a.zrun, k1 = min(k0 + a.zrun, g.nz);
+    const int xm1 = wrap_any(i - 1, g.nx), xp1 = wrap_any(i + 1, g.nx);
+    const int xm2 = wrap_any(i - 2, g.nx), xp2 = wrap_any(i + 2, g.nx);
+    const size_t rj = (size_t)j * g.nx;
+    const size_t ym1 = (size_t)wrap_any(j - 1, g.ny) * g.nx, yp1 = (size_t)wrap_any(j + 1, g.ny) * g.nx;
+    const size_t ym2 = (size_t)wrap_any(j - 2, g.ny) * g.nx, yp2 = (size_t)wrap_any(j + 2, g.ny) * g.nx;
+    // psi on planes k-2 .. k+2 and w^ on planes k-1 .. k+1 of this column
+    T ps[5], wz[3];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      T sg;
+      ps[q] = __ldg(a.psi + (size_t)zsrc_roll(g, k0 - 2 + q, G_EVEN, sg) * plane + rj + i);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      T sg;
+      const int kk = zsrc_roll(g, k0 - 1 + q, G_ODD, sg);
+      wz[q] = sg * __ldg(a.ow + (size_t)kk * plane + rj + i);
+    }
+    for (int k = k0; k < k1; ++k) {
+      const size_t pk = (size_t)k * plane;
+      const T r0 = g.prof(ph.rho0, k);
+      T div = (r0 * __ldg(a.ou + pk + rj + xp1) - r0 * __ldg(a.ou + pk + rj + xm1)) * hx;
+      div += (r0 * __ldg(a.ov + pk + yp1 + i) - r0 * __ldg(a.ov + pk + ym1 + i)) * hy;
+      div += (g.prof(ph.rho0, k + 1) * wz[2] - g.prof(ph.rho0, k - 1) * wz[0]) * hz;
+      T val;
+      if (a.op == LES_OP_COMPACT) {
+        const T* pp = a.psi + pk;
+        const T c = ps[2];
+        T C = (__ldg(pp + rj + xp2) - T(4) * __ldg(pp + rj + xp1) + T(6) * c - T(4) * __ldg(pp + rj + xm1) +
+               __ldg(pp + rj + xm2)) * c4x;
+        C += (__ldg(pp + yp2 + i) - T(4) * __ldg(pp + yp1 + i) + T(6) * c - T(4) * __ldg(pp + ym1 + i) +
+              __ldg(pp + ym2 + i)) * c4y;
+        C += (ps[4] - T(4) * ps[3] + T(6) * c - T(4) * ps[1] + ps[0]) * c4z;
+        val = __ldg(ph.alpha0 + k) / ph.dt * div - C;
+      } else {
+        val = div / ph.dt;
+      }
+      a.rhs[pk + rj + i] = val;
+      // roll the windows up one plane
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ps[q] = ps[q + 1];
+      wz[0] = wz[1];
+      wz[1] = wz[2];
+      if (k + 1 < k1) {
+        T sg;
+        ps[4] = __ldg(a.psi + (size_t)zsrc_roll(g, k + 3, G_EVEN, sg) * plane + rj + i);
+        const int kk = zsrc_roll(g, k + 2, G_ODD, sg);
+        wz[2] = sg * __ldg(a.ow + (size_t)kk * plane + rj + i);
+      }
+    }
+  }
+}
+
 // z-runs: enough blocks to fill the GPU, runs as long as possible
 inline void roll_runs(int nx, int ny, int nz, int& ntx, int& nty, int& zrun, int& nchunk) {
   ntx = (nx + RX - 1) / RX;
@@ -504,6 +586,32 @@ inline void roll_runs(int nx, int ny, int nz, int& ntx, int& nty, int& zrun, int
 }
 
 }  // namespace
+
+template <typename T>
+cudaError_t launch_rhs_roll(const StageArgs<T>& a, int op, const T* ou, const T* ov, const T* ow, const T* psi,
+                            T* rhs) {
+  RhsRoll<T> r;
+  r.g = a.g;
+  r.ph = a.ph;
+  r.op = op;
+  r.ou = ou;
+  r.ov = ov;
+  r.ow = ow;
+  r.psi = psi;
+  r.rhs = rhs;
+  // one thread per (column, z-run): enough threads for four 256-thread
+  // blocks per SM, runs as long as possible
+  const long long ncol = (long long)a.g.nx * a.g.ny;
+  const long long want = 4LL * 152 * 256;
+  const long long nch = std::max<long long>(1, std::min<long long>(a.g.nz, (want + ncol - 1) / ncol));
+  r.zrun = (int)((a.g.nz + nch - 1) / nch);
+  r.nchunk = (a.g.nz + r.zrun - 1) / r.zrun;
+  const long long nitem = ncol * r.nchunk;
+  const unsigned grid = (unsigned)std::min<long long>((nitem + 255) / 256, 1LL << 20);
+  ProfScope ps(a.prof, KI_RHS, a.st);
+  k_rhs_roll<T><<<grid, 256, 0, a.st>>>(r);
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_scalar_roll(const StageArgs<T>& a, int max_blocks, const T* u, const T* v, const T* w,
@@ -565,6 +673,10 @@ cudaError_t launch_momentum_roll(const StageArgs<T>& a, int max_blocks, const T*
   return cudaGetLastError();
 }
 
+template cudaError_t launch_rhs_roll<float>(const StageArgs<float>&, int, const float*, const float*, const float*,
+                                            const float*, float*);
+template cudaError_t launch_rhs_roll<double>(const StageArgs<double>&, int, const double*, const double*,
+                                             const double*, const double*, double*);
 template cudaError_t launch_scalar_roll<float>(const StageArgs<float>&, int, const float*, const float*,
                                                const float*, const float*, const float*, const float*, const float*,
                                                const float*, const float*, float*, float*);
