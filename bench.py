@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", default="auto", help="oracle sample: auto | full | NXxNY")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain Poisson leg")
+    ap.add_argument("--warm", default="zero", choices=("zero", "prev"),
+                    help="first guess of every Poisson solve of the timed workload")
     ap.add_argument("--learned-seeds", type=int, default=20, help="training runs for the learned leg")
     ap.add_argument("--learned-train-steps", type=int, default=1500)
     return ap.parse_args()
@@ -228,6 +230,8 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return 0
     case = workload(args.workload, 1)
+    if args.warm != case.warm:
+        case = case.replace(warm=args.warm)
     # each of the W + K oracle steps is a ~0.4 M-cell sample so the arm ends in minutes
     sample, desc = oracle_sample(case, args, budget=4.0e5)
     val, secs = time_oracle(sample, args.steps, args.warmup)
@@ -264,6 +268,8 @@ def main():
     les.load_library()
 
     case = workload(args.workload, seed=1 + rank)
+    if args.warm != case.warm:
+        case = case.replace(warm=args.warm)
     st0 = inputs.initial_state(case)
     sim = les.Simulation(case)
     sim.set_state(st0)

@@ -110,19 +110,38 @@ __global__ void __launch_bounds__(NTHREADS) k_thermo_cells(Grid<T> g, Phys<T> ph
 
 // a1 (radiation): per column, longwave flux through the faces
 //   F(k+1/2) = F0 exp(-kappa LWP above) + F1 exp(-kappa LWP below),
-// and the source -(1 / (c_pm Pi)) dF/dz of rho0 theta_l.
+// and the source -(1 / (c_pm Pi)) dF/dz of rho0 theta_l.  A block holds 32
+// columns (threadIdx.x) x RZ segments of each column (threadIdx.y): every
+// thread sums rho0 q_l dz over its segment, a shared-memory scan over the
+// segments gives each one the liquid water below it and the column total,
+// and the thread then forms the face fluxes of its own levels.
+constexpr int RZ = 8;
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS) k_radiation(Grid<T> g, Phys<T> ph, const T* __restrict__ qt,
-                                                        const T* __restrict__ ql, T* __restrict__ srad) {
-  const int i = blockIdx.x * TX + threadIdx.x;
-  const int j = blockIdx.y * TY + threadIdx.y;
-  if (i >= g.nx || j >= g.ny) return;
+__global__ void __launch_bounds__(32 * RZ) k_radiation(Grid<T> g, Phys<T> ph, const T* __restrict__ qt,
+                                                      const T* __restrict__ ql, T* __restrict__ srad) {
+  __shared__ T seg[RZ][32];
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y;
+  const int zs = threadIdx.y;
+  const bool col = i < g.nx;
+  const int per = (g.nz + RZ - 1) / RZ;
+  const int ka = min(zs * per, g.nz), kb = min(ka + per, g.nz);
   const T dz = g.dz;
-  T total = T(0);
-  for (int k = 0; k < g.nz; ++k) total += ph.rho0[k] * ql[g.lin(i, j, k)] * dz;
-  T below = T(0);
-  T Fm = ph.rad_f0 * m_exp(-ph.rad_kappa * total) + ph.rad_f1;
-  for (int k = 0; k < g.nz; ++k) {
+  T part = T(0);
+  if (col)
+    for (int k = ka; k < kb; ++k) part += ph.rho0[k] * ql[g.lin(i, j, k)] * dz;
+  seg[zs][threadIdx.x] = part;
+  __syncthreads();
+  if (!col) return;
+  T below = T(0), total = T(0);
+  for (int q = 0; q < RZ; ++q) {
+    const T v = seg[q][threadIdx.x];
+    if (q < zs) below += v;
+    total += v;
+  }
+  // flux through the face below this segment's first level
+  T Fm = ph.rad_f0 * m_exp(-ph.rad_kappa * (total - below)) + ph.rad_f1 * m_exp(-ph.rad_kappa * below);
+  for (int k = ka; k < kb; ++k) {
     const size_t m = g.lin(i, j, k);
     const T qlc = ql[m], qtc = qt[m];
     below += ph.rho0[k] * qlc * dz;
@@ -514,10 +533,10 @@ cudaError_t launch_thermo(const StageArgs<T>& a, const T* th, const T* qt, T* te
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !(a.ph.flags & LES_PHYS_RAD)) return e;
-  dim3 grid((a.g.nx + TX - 1) / TX, (a.g.ny + TY - 1) / TY);
+  dim3 grid((a.g.nx + 31) / 32, a.g.ny);
   {
     ProfScope ps(a.prof, KI_RADIATION, a.st);
-    k_radiation<T><<<grid, dim3(TX, TY), 0, a.st>>>(a.g, a.ph, qt, ql, srad);
+    k_radiation<T><<<grid, dim3(32, RZ), 0, a.st>>>(a.g, a.ph, qt, ql, srad);
   }
   return cudaGetLastError();
 }
