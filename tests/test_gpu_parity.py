@@ -378,7 +378,7 @@ def test_fused_cg_barrier_timeout_is_reported(les_mod, variant, stream, kern):
     (64, False, (32, 32, 32), 0),     # the learned-guess grid
     (64, True, (64, 7, 11), 0),       # odd brick extents in y and z
     (32, False, (32, 3, 2), 0),       # one-node bricks in y and z
-    (32, True, (32, 128, 4), 4)])     # more ghost rows than one batch of loads
+    (32, True, (32, 256, 4), 4)])     # more ghost rows than one batch of loads
 def test_resident_cg_matches_oracle(les_mod, precision, walls, shape, max_blocks):
     """The shared-memory-resident CG against the FP64 oracle and against the
     one-reduction rolling CG, which follows the same iterates."""
