@@ -12,7 +12,8 @@
  *             method, liquid only
  *   Sec. 2.3  nu_t = (c_s Delta)^2 f_B S, diffusivities nu_t / Pr, nu_t / Sc,
  *             sponge layer in the top of the domain
- *   Sec. 2.4  collocated finite differences, QUICK advection, 2nd-order
+ *   Sec. 2.4  collocated finite differences, QUICK advection (or WENO3 with
+ *             the local Lax-Friedrichs flux, the alternative scheme), 2nd-order
  *             central diffusion, the iterative predictor-corrector scheme
  *             (momentum prediction, pressure-correction Poisson equation,
  *             momentum / pressure correction, scalars staggered half a step)
@@ -281,6 +282,47 @@ static double quick(const orc *s, const double *f, int g, double F, int d, int i
   return (3.0 * f0 + 6.0 * f1 - f2) / 8.0;
 }
 
+/* Third-order WENO face value with the local Lax-Friedrichs flux (Sec. 2.4,
+ * the alternative advection scheme).  With the local speed |F| the
+ * Lax-Friedrichs flux F (phi_L + phi_R) / 2 - |F| (phi_R - phi_L) / 2 takes
+ * the reconstruction from the upwind side: for F >= 0 the left-biased one
+ * from (phi_{n-1}, phi_n, phi_{n+1}), else the right-biased one from
+ * (phi_n, phi_{n+1}, phi_{n+2}).  Each blends the two two-point candidates
+ * (upwind extrapolation and centred average) with the ideal weights 1/3, 2/3
+ * scaled by the inverse squared smoothness indicators; eps is our reading
+ * (the paper gives none): 1e-6 times the squared largest magnitude of the
+ * three values, plus 1e-18. */
+static double weno3_side(double fa, double fb, double fc) {
+  /* fa: the node two before the face on the upwind side, fb: the upwind
+   * node, fc: the node across the face */
+  const double q0 = 0.5 * (3.0 * fb - fa);
+  const double q1 = 0.5 * (fb + fc);
+  const double b0 = (fb - fa) * (fb - fa);
+  const double b1 = (fc - fb) * (fc - fb);
+  double m = fabs(fa);
+  if (fabs(fb) > m) m = fabs(fb);
+  if (fabs(fc) > m) m = fabs(fc);
+  const double eps = 1e-6 * m * m + 1e-18;
+  const double a0 = (1.0 / 3.0) / ((eps + b0) * (eps + b0));
+  const double a1 = (2.0 / 3.0) / ((eps + b1) * (eps + b1));
+  return (a0 * q0 + a1 * q1) / (a0 + a1);
+}
+
+static double weno3(const orc *s, const double *f, int g, double F, int d, int i, int j, int k) {
+  int di = d == 0, dj = d == 1, dk = d == 2;
+  double fm1 = at(s, f, g, i - di, j - dj, k - dk);
+  double f0 = at(s, f, g, i, j, k);
+  double f1 = at(s, f, g, i + di, j + dj, k + dk);
+  double f2 = at(s, f, g, i + 2 * di, j + 2 * dj, k + 2 * dk);
+  if (F >= 0.0) return weno3_side(fm1, f0, f1);
+  return weno3_side(f2, f1, f0);
+}
+
+/* face value of the configured advection scheme */
+static double face_value(const orc *s, const double *f, int g, double F, int d, int i, int j, int k) {
+  return s->p.advection == 1 ? weno3(s, f, g, F, d, i, j, k) : quick(s, f, g, F, d, i, j, k);
+}
+
 /* ---- a1: thermodynamics once per step ------------------------------------- */
 static void thermo(orc *s) {
   const double *th = s->f[ORC_THH], *qt = s->f[ORC_QTH];
@@ -405,7 +447,7 @@ void orc_scalar_stage(void *vs) {
               } else {
                 if (fl & ORC_ADV) {
                   double F = mass_flux(s, vel[d], d, fi, fj, fk);
-                  adv = F * quick(s, bar, GH_EVEN, F, d, fi, fj, fk);
+                  adv = F * face_value(s, bar, GH_EVEN, F, d, fi, fj, fk);
                 }
                 double nuf = 0.5 * (at(s, nu, GH_EVEN, fi, fj, fk) +
                                     at(s, nu, GH_EVEN, fi + di, fj + dj, fk + dk));
@@ -488,7 +530,7 @@ void orc_momentum_stage(void *vs) {
               }
               if ((fl & ORC_ADV) && !is_wall_face(s, d, fk)) {
                 double F = mass_flux(s, uh[d], d, fi, fj, fk);
-                adv = F * quick(s, uh[c], gh[c], F, d, fi, fj, fk);
+                adv = F * face_value(s, uh[c], gh[c], F, d, fi, fj, fk);
               }
               /* SGS stress rho0 nu_t (d_d u_c + d_c u_d) on the face: the normal
                * derivative is compact; the tangential one is the mean of the

@@ -71,7 +71,7 @@ typedef struct orc_params {
   double theta0, p00;
   double sat_tol;         /* secant stop |theta_l* - theta_l| (K)             */
   int32_t sat_maxit;
-  int32_t pad0;
+  int32_t advection;      /* 0 QUICK; 1 WENO3 with the local Lax-Friedrichs flux */
 } orc_params;
 
 void   *orc_create(const orc_params *prm, const double *rho0 /* nz or NULL */);

@@ -49,7 +49,7 @@ class _Params(C.Structure):
         ("subs_div", C.c_double), ("shf", C.c_double), ("lhf", C.c_double),
         ("rad_f0", C.c_double), ("rad_f1", C.c_double), ("rad_kappa", C.c_double),
         ("theta0", C.c_double), ("p00", C.c_double),
-        ("sat_tol", C.c_double), ("sat_maxit", C.c_int32), ("pad0", C.c_int32),
+        ("sat_tol", C.c_double), ("sat_maxit", C.c_int32), ("advection", C.c_int32),
     ]
 
 
@@ -135,7 +135,8 @@ class Oracle:
             rad_f0=case.rad_f0, rad_f1=case.rad_f1, rad_kappa=case.rad_kappa,
             theta0=case.theta0, p00=case.p00,
             sat_tol=1e-10,
-            sat_maxit=case.sat_maxit, pad0=0)
+            sat_maxit=case.sat_maxit,
+            advection={"quick": 0, "weno3": 1}[getattr(case, "advection", "quick")])
         self._params = p
         rho = case.rho0_profile() if hasattr(case, "rho0_profile") else None
         self._rho = _c64(rho) if rho is not None else None

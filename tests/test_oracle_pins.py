@@ -69,6 +69,68 @@ def test_quick_translation_closed_form(u0, K):
 
 
 # --------------------------------------------------------------------------
+# WENO3 with the local Lax-Friedrichs flux (the alternative advection scheme)
+
+
+def _x_profile(c, prof):
+    x = (np.arange(c.nx) + 0.5) / c.nx
+    return prof(x)[None, None, :] * np.ones(c.shape)
+
+
+def _advect(scheme, n, prof, u0=0.7, K=3, steps=None, T=None):
+    c = _base(n, 4, 4, h=1.0 / n, physics=("adv",), K=K, dt=0.3 / n / abs(u0), advection=scheme)
+    o = Oracle(c, {"u": np.full(c.shape, u0), "v": np.zeros(c.shape), "w": np.zeros(c.shape),
+                   "theta_l": _x_profile(c, prof), "q_t": np.zeros(c.shape)})
+    steps = steps if steps is not None else int(round(T / c.dt))
+    o.step(steps)
+    return c, o.get("theta_l"), steps
+
+
+@pytest.mark.parametrize("u0", [0.7, -0.55])
+def test_weno3_smooth_limit_closed_form(u0):
+    """For a smooth wave of small amplitude on a large mean the smoothness
+    indicators are far below eps, the weights take their ideal values 1/3, 2/3
+    and the face value is the linear third-order upwind-biased one,
+    (-phi_{n-1} + 5 phi_n + 2 phi_{n+1}) / 6 (mirrored for u < 0): the mode
+    follows that symbol through the K-sub-iteration scheme."""
+    n, m, steps, K, A = 32, 3, 20, 3, 1e-4
+    c, th, _ = _advect("weno3", n, lambda x: 300.0 + A * np.sin(2 * np.pi * m * x), u0=u0, K=K, steps=steps)
+    t = 2 * np.pi * m / n
+    e = np.exp(1j * t)
+    face = (-1 / e + 5 + 2 * e) / 6 if u0 > 0 else (2 + 5 * e - e * e) / 6
+    lam = -u0 / c.dx * face * (1 - 1 / e)
+    G = _gk(lam * c.dt, K) ** steps
+    i = np.arange(n)
+    expect = A * np.imag(G * np.exp(1j * t * (i + 0.5)))
+    assert np.max(np.abs(th[0, 0] - 300.0 - expect)) < 1e-9
+
+
+def test_weno3_square_wave_is_nearly_non_oscillatory():
+    """A translated step: WENO3 creates far smaller new extrema than QUICK
+    (QUICK is linear and third order, so it overshoots by ~13 % here)."""
+    prof = lambda x: 300.0 + ((x > 0.25) & (x < 0.5)) * 1.0
+    over = {}
+    for s in ("quick", "weno3"):
+        _, th, _ = _advect(s, 64, prof, steps=40)
+        over[s] = max(th.max() - 301.0, 300.0 - th.min())
+    assert over["quick"] > 0.08
+    assert over["weno3"] < 0.05 and over["weno3"] < 0.3 * over["quick"]
+
+
+def test_weno3_self_convergence():
+    """Smooth translation with the nonlinear weights active (amplitude 1): the
+    error against the exact translated wave falls at least 4x per halving of
+    the spacing at fixed Courant number."""
+    errs = []
+    for n in (32, 64, 128):
+        c, th, steps = _advect("weno3", n, lambda x: 300.0 + np.sin(2 * np.pi * x), T=0.5)
+        x = (np.arange(n) + 0.5) / n
+        exact = 300.0 + np.sin(2 * np.pi * (x - 0.7 * steps * c.dt))
+        errs.append(np.sqrt(np.mean((th[0, 0] - exact) ** 2)))
+    assert errs[0] / errs[1] > 4.0 and errs[1] / errs[2] > 4.0
+
+
+# --------------------------------------------------------------------------
 # 2nd-order central diffusion of scalars, Pr for theta_l and Sc for q_t
 
 
@@ -271,10 +333,11 @@ def test_wide_projection_is_divergence_free():
 # conservation (Sec. 2.4: exact discrete conservation without sources)
 
 
-@pytest.mark.parametrize("walls", [False, True])
-def test_scalar_and_momentum_conservation(walls):
+@pytest.mark.parametrize("walls,advection", [(False, "quick"), (True, "quick"), (False, "weno3"),
+                                             (True, "weno3")])
+def test_scalar_and_momentum_conservation(walls, advection):
     c = _base(10, 8, 8, h=0.1, walls=walls, physics=("adv", "sgs"), cs=0.3, dt=0.02, K=3,
-              tol=1e-12, dx=0.1, dy=0.12, dz=0.08)
+              tol=1e-12, dx=0.1, dy=0.12, dz=0.08, advection=advection)
     if walls:
         c = c.replace(rho0_const=None, dz=25.0, dx=40.0, dy=40.0, dt=0.5)
     st = {k: inputs.uniform(4, s, c.n, -1, 1).reshape(c.shape) for k, s in (("u", 0), ("v", 1), ("w", 2))}
