@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain Poisson leg")
     ap.add_argument("--warm", default="zero", choices=("zero", "prev"),
                     help="first guess of every Poisson solve of the timed workload")
+    ap.add_argument("--advection", default="quick", choices=("quick", "weno3"),
+                    help="advection scheme of the timed workload")
     ap.add_argument("--learned-seeds", type=int, default=20, help="training runs for the learned leg")
     ap.add_argument("--learned-train-steps", type=int, default=1500)
     return ap.parse_args()
@@ -232,6 +234,8 @@ def reference_arm(args, rank, world):
     case = workload(args.workload, 1)
     if args.warm != case.warm:
         case = case.replace(warm=args.warm)
+    if args.advection != case.advection:
+        case = case.replace(advection=args.advection)
     # each of the W + K oracle steps is a ~0.4 M-cell sample so the arm ends in minutes
     sample, desc = oracle_sample(case, args, budget=4.0e5)
     val, secs = time_oracle(sample, args.steps, args.warmup)
@@ -270,6 +274,8 @@ def main():
     case = workload(args.workload, seed=1 + rank)
     if args.warm != case.warm:
         case = case.replace(warm=args.warm)
+    if args.advection != case.advection:
+        case = case.replace(advection=args.advection)
     st0 = inputs.initial_state(case)
     sim = les.Simulation(case)
     sim.set_state(st0)
@@ -406,7 +412,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC[args.workload], "grid": [case.nx, case.ny, case.nz],
                        "cells": case.n, "K": case.K, "solver": case.solver, "tol": case.tol,
-                       "warm_start": case.warm, "l2": "flushed (256 MiB write) before every timed step",
+                       "warm_start": case.warm, "advection": case.advection,
+                       "l2": "flushed (256 MiB write) before every timed step",
                        "replicas": world, "seed": 1},
             "roofline": roofline,
             "cpu_baseline": cpu,

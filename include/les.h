@@ -72,6 +72,12 @@ extern "C" {
 #define LES_WARM_ZERO      0
 #define LES_WARM_PREV      1          /* previous step's solve, same sub-iter   */
 #define LES_WARM_LEARNED   2          /* learned network (les_set_warm_model)   */
+/* advection scheme (Sec. 2.4): QUICK, or third-order WENO with the local
+ * Lax-Friedrichs flux (upwind-side WENO3 reconstruction; its smoothness
+ * regulariser eps = 1e-6 max|phi|^2 + 1e-18 over the three values is this
+ * library's reading -- the paper gives none) */
+#define LES_ADV_QUICK      0
+#define LES_ADV_WENO3      1
 
 /* field ids for get / set / offset */
 enum les_field {
@@ -138,7 +144,10 @@ typedef struct les_config {
                                 multiple of 128 floats / 64 doubles, ny a
                                 multiple of the tile rows), else 1;
                                 1: one launch per CG phase               */
-  double   reserved[4];
+  int32_t  advection;        /* LES_ADV_QUICK (paper's default) |
+                                LES_ADV_WENO3 (its alternative, Sec. 2.4)  */
+  int32_t  reserved_i;
+  double   reserved[3];
 } les_config;
 
 typedef struct les_step_stats {

@@ -66,6 +66,7 @@ int validate(const les_config* c, std::string* why) {
   if (c->dt == 0 && !(c->cfl > 0)) return bad("dt = 0 needs cfl > 0");
   if (c->sat_maxit < 0 || c->sat_maxit > 1000) return bad("sat_maxit out of range");
   if (c->solver_path != 0 && c->solver_path != 1) return bad("solver_path must be 0 or 1");
+  if (c->advection != LES_ADV_QUICK && c->advection != LES_ADV_WENO3) return bad("unknown advection scheme");
   return LES_OK;
 }
 
@@ -199,6 +200,7 @@ Phys<T> make_phys(const les_handle* h) {
   ph.p00 = (T)c.p00;
   ph.sat_tol = (T)c.sat_tol;
   ph.sat_maxit = c.sat_maxit;
+  ph.advection = c.advection;
   const T* pr = (const T*)h->profiles;
   ph.rho0 = pr;
   ph.alpha0 = pr + c.nz;

@@ -97,6 +97,35 @@ __device__ __forceinline__ void tile_origin(const Grid<T>& g, long long t, int& 
   k1 = min(k0 + g.zc, g.nz);
 }
 
+// ---- advection face values (Sec. 2.4) ----------------------------------------
+// Value of phi on the face between nodes n and n+1 carried by the face mass
+// flux F, from phi_{n-1}, phi_n, phi_{n+1}, phi_{n+2}.
+//   QUICK: quadratic upstream interpolation, (-phi_{n-1} + 6 phi_n +
+//          3 phi_{n+1}) / 8 for F >= 0, mirrored for F < 0.
+//   WENO3 with the local Lax-Friedrichs flux: the upwind-side third-order
+//          WENO reconstruction -- the candidates (3 phi_up - phi_upup) / 2 and
+//          (phi_up + phi_across) / 2 blended with ideal weights 1/3, 2/3
+//          scaled by 1 / (eps + beta)^2, beta the squared one-sided
+//          differences, eps = 1e-6 max|phi|^2 + 1e-18 (the weights are formed
+//          as d0 (eps+b1)^2 : d1 (eps+b0)^2, which stays finite in FP32).
+template <typename T>
+__device__ __forceinline__ T weno3_side(T fa, T fb, T fc) {
+  const T q0 = T(0.5) * (T(3) * fb - fa);
+  const T q1 = T(0.5) * (fb + fc);
+  const T b0 = (fb - fa) * (fb - fa);
+  const T b1 = (fc - fb) * (fc - fb);
+  const T m = fmax(fabs(fa), fmax(fabs(fb), fabs(fc)));
+  const T eps = T(1e-6) * m * m + T(1e-18);
+  const T e0 = (eps + b0) * (eps + b0), e1 = (eps + b1) * (eps + b1);
+  const T w0 = e1, w1 = T(2) * e0;  // (1/3)/e0 : (2/3)/e1, times 3 e0 e1
+  return (w0 * q0 + w1 * q1) / (w0 + w1);
+}
+template <typename T>
+__device__ __forceinline__ T face_value(int scheme, T F, T fm1, T f0, T f1, T f2) {
+  if (scheme == LES_ADV_WENO3) return F >= T(0) ? weno3_side(fm1, f0, f1) : weno3_side(f2, f1, f0);
+  return F >= T(0) ? (-fm1 + T(6) * f0 + T(3) * f1) * T(0.125) : (T(3) * f0 + T(6) * f1 - f2) * T(0.125);
+}
+
 // ---- reductions -----------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -41,6 +41,7 @@ struct Phys {
   T p00;
   T sat_tol;
   int sat_maxit;
+  int advection;      // LES_ADV_*
   const T* rho0;      // nz
   const T* alpha0;    // nz
   const T* p0;        // nz

@@ -221,10 +221,6 @@ __global__ void __launch_bounds__(NTHREADS) k_nu(Grid<T> g, Phys<T> ph, VelView<
 
 // QUICK face value between node n and n + e_d (Sec. 2.4): for F >= 0
 // (-f[n-1] + 6 f[n] + 3 f[n+1]) / 8, otherwise (3 f[n] + 6 f[n+1] - f[n+2]) / 8
-template <typename T>
-__device__ __forceinline__ T quick(T F, T fm1, T f0, T f1, T f2) {
-  return F >= T(0) ? (-fm1 + T(6) * f0 + T(3) * f1) * T(0.125) : (T(3) * f0 + T(6) * f1 - f2) * T(0.125);
-}
 
 // ---- a3: scalar predictor (Eq. scalar_prediction_step) -----------------------
 // rho0 phi^{k+1} = rho0 phi^{n+1/2} + dt [ -div(rho0 u^k phibar)
@@ -277,7 +273,7 @@ __global__ void __launch_bounds__(NTHREADS)
               if (ph.flags & LES_PHYS_ADV) {
                 const T bm = bar(q, li - di, lj - dj, lk - dk);
                 const T b2 = bar(q, ui + di, uj + dj, uk + dk);
-                adv = F * quick(F, bm, b0, b1, b2);
+                adv = F * face_value(ph.advection, F, bm, b0, b1, b2);
               }
               fl[q] = -adv + rhof * nuf * inv_s[q] * (b1 - b0) * ihd;
             }
@@ -340,7 +336,7 @@ __global__ void __launch_bounds__(NTHREADS)
             if ((ph.flags & LES_PHYS_ADV) && !g.wall_face(d, lk)) {
               const T F = T(0.5) * (g.prof(ph.rho0, lk) * g.at(vel[d], li, lj, lk, vghost(d)) +
                                     g.prof(ph.rho0, uk) * g.at(vel[d], ui, uj, uk, vghost(d)));
-              adv = F * quick(F, g.at(vel[c], li - di, lj - dj, lk - dk, vghost(c)),
+              adv = F * face_value(ph.advection, F, g.at(vel[c], li - di, lj - dj, lk - dk, vghost(c)),
                               g.at(vel[c], li, lj, lk, vghost(c)), g.at(vel[c], ui, uj, uk, vghost(c)),
                               g.at(vel[c], ui + di, uj + dj, uk + dk, vghost(c)));
             }

@@ -51,10 +51,6 @@ __device__ __forceinline__ int zsrc_roll(const Grid<T>& g, int gk, int gh, T& sg
   return gk < 0 ? 0 : (gk >= g.nz ? g.nz - 1 : gk);  // planes beyond one mirror: any valid data (unused)
 }
 
-template <typename T>
-__device__ __forceinline__ T quick_r(T F, T fm1, T f0, T f1, T f2) {
-  return F >= T(0) ? (-fm1 + T(6) * f0 + T(3) * f1) * T(0.125) : (T(3) * f0 + T(6) * f1 - f2) * T(0.125);
-}
 
 template <typename T>
 struct MomRoll {
@@ -65,7 +61,7 @@ struct MomRoll {
   T *ou, *ov, *ow;
 };
 
-template <typename T>
+template <typename T, int ADV>
 __global__ void __launch_bounds__(RX* RY) k_momentum_roll(MomRoll<T> a) {
   extern __shared__ unsigned char smraw[];
   T* U = reinterpret_cast<T*>(smraw);  // [NRING][PN] each
@@ -258,7 +254,7 @@ __global__ void __launch_bounds__(RX* RY) k_momentum_roll(MomRoll<T> a) {
             T adv = T(0);
             if (adv_on[d][side]) {
               const T F = Ff[d][side];
-              adv = F * quick_r(F, S(c, lx - di, ly - dj, lz - dk), cl, cu, S(c, ux + di, uy + dj, uz + dk));
+              adv = F * face_value(ADV, F, S(c, lx - di, ly - dj, lz - dk), cl, cu, S(c, ux + di, uy + dj, uz + dk));
             }
             const T dn = (cu - cl) * ih[d];
             T dtg;
@@ -304,7 +300,7 @@ struct ScaRoll {
   T *tho, *qto;
 };
 
-template <typename T>
+template <typename T, int ADV>
 __global__ void __launch_bounds__(RX* RY) k_scalar_roll(ScaRoll<T> a) {
   extern __shared__ unsigned char smraw[];
   T* U = reinterpret_cast<T*>(smraw);  // u^k rings
@@ -473,7 +469,7 @@ __global__ void __launch_bounds__(RX* RY) k_scalar_roll(ScaRoll<T> a) {
               const T b0 = S(4 + q, lx, ly, lz), b1 = S(4 + q, ux, uy, uz);
               T adv = T(0);
               if (ph.flags & LES_PHYS_ADV)
-                adv = F * quick_r(F, S(4 + q, lx - di, ly - dj, lz - dk), b0, b1, S(4 + q, ux + di, uy + dj, uz + dk));
+                adv = F * face_value(ADV, F, S(4 + q, lx - di, ly - dj, lz - dk), b0, b1, S(4 + q, ux + di, uy + dj, uz + dk));
               fl[q] = -adv + K * inv_s[q] * (b1 - b0) * ih[d];
             }
           }
@@ -633,12 +629,14 @@ cudaError_t launch_scalar_roll(const StageArgs<T>& a, int max_blocks, const T* u
   r.tho = th_out;
   r.qto = qt_out;
   const size_t smem = (size_t)(6 * NRING * PN + 3 * NNP) * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(k_scalar_roll<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the advection scheme is a template parameter: no per-face branch on it
+  auto kern = a.ph.advection == LES_ADV_WENO3 ? k_scalar_roll<T, LES_ADV_WENO3> : k_scalar_roll<T, LES_ADV_QUICK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long nblk = (long long)r.ntx * r.nty * r.nchunk;
   const unsigned grid = (unsigned)std::min<long long>(nblk, (long long)max_blocks * 4);
   ProfScope ps(a.prof, KI_SCALAR, a.st);
-  k_scalar_roll<T><<<grid, dim3(RX, RY), smem, a.st>>>(r);
+  kern<<<grid, dim3(RX, RY), smem, a.st>>>(r);
   return cudaGetLastError();
 }
 
@@ -663,13 +661,13 @@ cudaError_t launch_momentum_roll(const StageArgs<T>& a, int max_blocks, const T*
   m.ov = ov;
   m.ow = ow;
   const size_t smem = (size_t)(5 * NRING * PN + 3 * NNP) * sizeof(T);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_momentum_roll<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = a.ph.advection == LES_ADV_WENO3 ? k_momentum_roll<T, LES_ADV_WENO3> : k_momentum_roll<T, LES_ADV_QUICK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long nblk = ncol * m.nchunk;
   const unsigned grid = (unsigned)std::min<long long>(nblk, (long long)max_blocks * 4);
   ProfScope ps(a.prof, KI_MOMENTUM, a.st);
-  k_momentum_roll<T><<<grid, dim3(RX, RY), smem, a.st>>>(m);
+  kern<<<grid, dim3(RX, RY), smem, a.st>>>(m);
   return cudaGetLastError();
 }
 

@@ -124,10 +124,6 @@ __device__ __forceinline__ void nu_box(T* __restrict__ nu, const T* __restrict__
   }
 }
 
-template <typename T>
-__device__ __forceinline__ T quick4(T F, T fm1, T f0, T f1, T f2) {
-  return F >= T(0) ? (-fm1 + T(6) * f0 + T(3) * f1) * T(0.125) : (T(3) * f0 + T(6) * f1 - f2) * T(0.125);
-}
 
 template <typename T>
 __device__ __forceinline__ void tile_of(const Grid<T>& g, long long t, int& x0, int& y0, int& k0) {
@@ -203,7 +199,7 @@ __global__ void __launch_bounds__(BTX* BTY)
               const T b0 = bar[q][bidx(lx, ly, lz)], b1 = bar[q][bidx(ux, uy, uz)];
               T adv = T(0);
               if (ph.flags & LES_PHYS_ADV)
-                adv = F * quick4(F, bar[q][bidx(lx - di, ly - dj, lz - dk)], b0, b1,
+                adv = F * face_value(ph.advection, F, bar[q][bidx(lx - di, ly - dj, lz - dk)], b0, b1,
                                  bar[q][bidx(ux + di, uy + dj, uz + dk)]);
               fl[q] = -adv + rhof * nuf * inv_s[q] * (b1 - b0) * ih[d];
             }
@@ -294,7 +290,7 @@ __global__ void __launch_bounds__(BTX* BTY)
             if ((ph.flags & LES_PHYS_ADV) && !g.wall_face(d, gkl)) {
               const T F = T(0.5) * (g.prof(ph.rho0, gkl) * vel[d][bidx(lx, ly, lz)] +
                                     g.prof(ph.rho0, gkl + dk) * vel[d][bidx(ux, uy, uz)]);
-              adv = F * quick4(F, vel[c][bidx(lx - di, ly - dj, lz - dk)], vel[c][bidx(lx, ly, lz)],
+              adv = F * face_value(ph.advection, F, vel[c][bidx(lx - di, ly - dj, lz - dk)], vel[c][bidx(lx, ly, lz)],
                                vel[c][bidx(ux, uy, uz)], vel[c][bidx(ux + di, uy + dj, uz + dk)]);
             }
             const T dn = (vel[c][bidx(ux, uy, uz)] - vel[c][bidx(lx, ly, lz)]) * ih[d];

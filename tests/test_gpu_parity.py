@@ -140,12 +140,13 @@ def _moist_case(nx=37, ny=11, nz=12, **kw):
     return c.replace(**kw)
 
 
-@pytest.mark.parametrize("walls,stencil_path", [(True, 0), (False, 0), (True, 1), (False, 1), (True, 2),
-                                                (False, 2)])
-def test_stages_fp64(les_mod, walls, stencil_path):
-    """Stage-by-stage FP64 parity; stencil_path 0 = rolling momentum + tiled
-    scalar predictors, 1 = direct-load predictors, 2 = tiled predictors."""
-    case = _moist_case()
+@pytest.mark.parametrize("walls,stencil_path,advection", [
+    (True, 0, "quick"), (False, 0, "quick"), (True, 1, "quick"), (False, 1, "quick"), (True, 2, "quick"),
+    (False, 2, "quick"), (True, 0, "weno3"), (False, 1, "weno3"), (True, 2, "weno3")])
+def test_stages_fp64(les_mod, walls, stencil_path, advection):
+    """Stage-by-stage FP64 parity; stencil_path 0 = rolling predictors, 1 =
+    direct-load predictors, 2 = tiled predictors; QUICK or WENO3 advection."""
+    case = _moist_case(advection=advection)
     if not walls:
         case = case.replace(walls=False, physics=("adv", "sgs", "fb", "moist", "buoy", "coriolis"))
     st = inputs.initial_state(case)
@@ -256,6 +257,21 @@ def test_cbl_fp32_against_fp64_oracle(les_mod):
     assert errs["theta_l"] < 1e-6 and errs["q_t"] < 1e-5
     assert errs["u"] < 1e-5 and errs["v"] < 1e-5
     assert errs["w"] < 5e-2 and errs["p"] < 5e-2
+
+
+def test_weno3_fp32_steps_against_fp64_oracle(les_mod):
+    """The WENO3 scheme in FP32 (rolling predictors) against the FP64 oracle
+    over a few steps of the capped boundary layer."""
+    case = inputs.cbl(64, 32, 48, precision=32, advection="weno3")
+    sim, ref, _ = pair(les_mod, case)
+    sim.step(3)
+    ref.step(3)
+    errs = {f: rel(sim.get(f), ref.get(f)) for f in ("u", "v", "w", "theta_l", "q_t")}
+    print("WENO3 fp32 vs fp64 relative L2 after 3 steps:", errs)
+    assert rel(sim.get("theta_l"), ref.get("theta_l")) < 1e-6
+    assert rel(sim.get("q_t"), ref.get("q_t")) < 1e-5
+    for f in ("u", "v"):
+        assert rel(sim.get(f), ref.get(f)) < 1e-4, f
 
 
 def test_deterministic(les_mod):
