@@ -49,6 +49,8 @@ def workload(name: str, seed: int):
         return inputs.tgv(32, seed=seed)
     if name == "tgv_large":
         return inputs.tgv(32, nxyz=(1536, 1536, 256), seed=seed, precision=32, steps_tol=1e-6)
+    if name == "ensemble16":
+        return inputs.ensemble(16, seed=seed)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -57,6 +59,8 @@ WORKLOAD_DESC = {
               "K=3, CG to 1e-6",
     "tgv32": "dry triply periodic Taylor-Green 32^3, FP64, K=3, CG to 1e-10",
     "tgv_large": "dry triply periodic Taylor-Green 1536x1536x256, FP32 (FP64 reductions), K=3, CG to 1e-6",
+    "ensemble16": "uneven ensemble of 16 moist capped boundary layers, 64^2..192^2 x 64..128, FP32 (FP64 "
+                  "reductions), seeded inversions, surface fluxes and subsidence, K=3, CG to 1e-6",
 }
 
 
@@ -74,6 +78,7 @@ def parse():
                     help="first guess of every Poisson solve of the timed workload")
     ap.add_argument("--advection", default="quick", choices=("quick", "weno3"),
                     help="advection scheme of the timed workload")
+    ap.add_argument("--no-autotune", action="store_true", help="ensemble workload: keep the default tuning")
     ap.add_argument("--learned-seeds", type=int, default=20, help="training runs for the learned leg")
     ap.add_argument("--learned-train-steps", type=int, default=1500)
     return ap.parse_args()
@@ -253,6 +258,73 @@ def reference_arm(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+def bench_ensemble(args, rank, world, local):
+    """The uneven ensemble: every member tuned by the autotuner, then all
+    stepped together through les_ensemble_step; whole-job cell-steps/s over
+    wall time bracketed by device synchronisation (the members run on their
+    own streams)."""
+    import torch
+
+    from paper_2301_04698_gb300 import inputs, les
+    cases = workload(args.workload, seed=1 + rank)
+    ens = les.Ensemble(cases)
+    ens.set_states([inputs.initial_state(c) for c in cases])
+    tuned = []
+    for m in ens.members:
+        if args.no_autotune:
+            tuned.append(None)
+        else:
+            tuned.append(les.autotune(m)["tuning"])
+    for _ in range(args.warmup):
+        ens.step(1, allow_not_converged=True)
+    torch.cuda.synchronize()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    clocks = Clocks(local)
+    launches0 = sum(m.launch_count() for m in ens.members)
+    total_s = 0.0
+    iters = 0
+    barrier(world)
+    for s in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = ens.step(1, allow_not_converged=True)
+        torch.cuda.synchronize()
+        total_s += time.perf_counter() - t0
+        iters += sum(x["iters_total"] for x in st)
+    barrier(world)
+    clk = clocks.stop()
+    total_s = allmax(world, total_s)
+    launches = sum(m.launch_count() for m in ens.members) - launches0
+    # the same steps member after member, for the gain of stepping them together
+    seq_s = 0.0
+    for s in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for m in ens.members:
+            m.step(1, allow_not_converged=True)
+        torch.cuda.synchronize()
+        seq_s += time.perf_counter() - t0
+    value = world * ens.cells * args.steps / total_s
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC[args.workload], "members": [c.name for c in cases],
+                       "cells": ens.cells, "K": cases[0].K, "tol": cases[0].tol,
+                       "timing": "wall clock between device synchronisations (members on their own streams)",
+                       "l2": "flushed (256 MiB write) before every timed step", "autotuned": tuned},
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk,
+            "poisson": {"iters_per_step": iters / args.steps},
+            "one_after_another_ms_per_step": 1e3 * seq_s / args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    ens.close()
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args.gpus)
@@ -270,6 +342,9 @@ def main():
         B.build()
     barrier(world)
     les.load_library()
+
+    if args.workload == "ensemble16":
+        return bench_ensemble(args, rank, world, local)
 
     case = workload(args.workload, seed=1 + rank)
     if args.warm != case.warm:

@@ -258,6 +258,22 @@ int les_poisson_solve_static(const les_config *cfg, const void *d_rho0, const vo
                              double rtol, int32_t maxit, void *stream, int32_t *iters,
                              double *rel_res, char *err, size_t err_len);
 
+/* ---- ensembles -----------------------------------------------------------------
+ * Independent members -- different grids, seeds and forcings, as in ensembles
+ * of LES runs that produce parameterisation training data -- stepped
+ * together.  les_ensemble_step runs les_step(hs[i], nsteps, &stats[i]) for
+ * the m distinct handles concurrently, one host thread per handle, each on its
+ * own device and stream (give every handle its own stream, les_set_stream,
+ * for the members' kernels to overlap).  The members' persistent CG solves
+ * run one at a time; their stencil kernels overlap.  stats: optional array
+ * of m; failed: optional, the index of the first member whose status is
+ * returned (-1 if none).  Returns LES_OK, LES_ERR_NOT_CONVERGED (state valid)
+ * or the first other error; LES_ERR_INVALID_ARG for m <= 0, m > 1024, a null
+ * or repeated handle.  The paper runs one domain at a time and has no
+ * counterpart. */
+int les_ensemble_step(les_handle *const *hs, int32_t m, int32_t nsteps, les_step_stats *stats,
+                      int32_t *failed);
+
 /* ---- tuning of the persistent CG solve ---------------------------------------
  * The CG solve runs as one persistent cooperative launch when solver_path = 0
  * (compact operator).  For cg_variant 1 and 2 a thread block of

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "les_internal.h"
@@ -112,6 +113,7 @@ int device_sms() {
 
 struct les_handle {
   les_config cfg;
+  int dev = 0;  // the device current at les_init
   cudaStream_t st = nullptr;
   char* ws = nullptr;
   Layout L;
@@ -583,6 +585,7 @@ int les_init(const les_config* cfg, const double* rho0_z, void* workspace, size_
       if (!(rho0_z[k] > 0) || !std::isfinite(rho0_z[k])) return LES_ERR_INVALID_ARG;
   }
   les_handle* h = new (std::nothrow) les_handle();
+  if (h) cudaGetDevice(&h->dev);
   if (!h) return LES_ERR_INVALID_ARG;
   h->cfg = *cfg;
   h->st = (cudaStream_t)stream;
@@ -693,6 +696,41 @@ int les_step(les_handle* h, int32_t nsteps, les_step_stats* stats) {
     if (rc != LES_OK) return rc;
   }
   st->dt = h->dt;
+  return worst;
+}
+
+int les_ensemble_step(les_handle* const* hs, int32_t m, int32_t nsteps, les_step_stats* stats,
+                      int32_t* failed) {
+  if (failed) *failed = -1;
+  if (!hs || m <= 0 || m > 1024 || nsteps < 0) return LES_ERR_INVALID_ARG;
+  for (int i = 0; i < m; ++i) {
+    if (!hs[i]) return LES_ERR_INVALID_ARG;
+    for (int k = 0; k < i; ++k)
+      if (hs[k] == hs[i]) return LES_ERR_INVALID_ARG;  // one thread per handle
+  }
+  std::vector<int> rc(m, LES_OK);
+  std::vector<std::thread> workers;
+  workers.reserve(m);
+  for (int i = 0; i < m; ++i)
+    workers.emplace_back([&, i] {
+      if (cudaSetDevice(hs[i]->dev) != cudaSuccess) {
+        rc[i] = LES_ERR_CUDA;
+        return;
+      }
+      rc[i] = les_step(hs[i], nsteps, stats ? &stats[i] : nullptr);
+    });
+  for (auto& w : workers) w.join();
+  int worst = LES_OK;
+  for (int i = 0; i < m; ++i) {
+    if (rc[i] == LES_OK) continue;
+    if (rc[i] == LES_ERR_NOT_CONVERGED && worst == LES_OK) {
+      worst = rc[i];
+      if (failed) *failed = i;
+    } else if (rc[i] != LES_ERR_NOT_CONVERGED) {
+      if (failed) *failed = i;
+      return rc[i];
+    }
+  }
   return worst;
 }
 

@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <string>
 
+#include <mutex>
+
 #include "les_internal.h"
 
 namespace les {
@@ -299,14 +301,24 @@ cudaError_t launch_apply(const SolverArgs<T>& a, int op, const T* x, T* y) {
   return cudaGetLastError();
 }
 
+std::mutex& persistent_solve_lock() {
+  static std::mutex m;
+  return m;
+}
+
 template <typename T>
 int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxit, int* iters, double* rel,
                   std::string* err) {
   // persistent CG: in shared memory when the grid fits there; else the
   // two-phase streaming kernel on tile-aligned grids (variant 0 or 2) or the
   // one-pass kernel (variant 0 on other grids, or variant 3); variant 1 is
-  // Chronopoulos-Gear
+  // Chronopoulos-Gear.  Persistent solves of different handles (ensemble
+  // members stepped from several host threads) run one at a time: each
+  // grid spins on its own barrier and is sized to fill the GPU, so two of
+  // them must never wait for each other's SMs.
   const bool cg_c = a.op == LES_OP_COMPACT && a.solver == LES_SOLVER_CG;
+  std::unique_lock<std::mutex> one_at_a_time(persistent_solve_lock(), std::defer_lock);
+  if (a.bar && a.fused) one_at_a_time.lock();
   const int var = a.fused ? a.fused->variant : -1;
   const bool tiled = a.fused && fused_cg_eligible(a.g, a.op, a.solver, a.fused->ty);
   if (a.bar && cg_c && var == 0 && a.fused->resident == 0) {

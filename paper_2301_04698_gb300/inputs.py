@@ -40,6 +40,7 @@ PHYSICS = ("adv", "sgs", "const_nu", "moist", "buoy", "coriolis", "sponge",
 # stream ids of the generator
 STREAM_U, STREAM_V, STREAM_W, STREAM_TH, STREAM_QT, STREAM_P = 0, 1, 2, 3, 4, 5
 STREAM_CASE = 16
+STREAM_ENSEMBLE = 17
 
 
 def uniform01(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
@@ -213,4 +214,21 @@ def initial_state(case: Case) -> dict:
     else:
         raise ValueError(f"unknown init {case.init!r}")
     out["p"] = np.zeros(case.shape)
+    return out
+
+
+def ensemble(m: int = 16, seed: int = 1, xy=(64, 96, 128, 160, 192), zs=(64, 96, 128),
+             precision: int = 32) -> list:
+    """Members of an uneven ensemble of capped boundary layers: member i draws
+    its horizontal size from `xy`, its height from `zs`, its own inversion
+    (the cbl seed), and scales of the surface fluxes and of the subsidence
+    divergence in [0.5, 1.5) -- all from the counter generator."""
+    out = []
+    for i in range(m):
+        r = uniform01(seed, STREAM_ENSEMBLE, 5, offset=5 * i)
+        n = xy[int(r[0] * len(xy)) % len(xy)]
+        nz = zs[int(r[1] * len(zs)) % len(zs)]
+        c = cbl(n, n, nz, seed=1000 * seed + i, precision=precision)
+        out.append(c.replace(name=f"member{i}_{n}x{n}x{nz}", shf=c.shf * (0.5 + r[2]),
+                             lhf=c.lhf * (0.5 + r[3]), subs_div=c.subs_div * (0.5 + r[4])))
     return out

@@ -43,7 +43,8 @@ EXPORTED = ("les_config_default", "les_workspace_bytes", "les_init", "les_destro
             "les_set_tuning", "les_unet_param_count", "les_unet_workspace_bytes", "les_unet_create",
             "les_unet_destroy", "les_unet_set_stream", "les_unet_set_weights", "les_unet_get_weights",
             "les_unet_forward", "les_unet_loss_grad", "les_unet_train_step", "les_unet_last_error",
-            "les_set_warm_model", "les_unet_set_output_scale", "les_unet_get_output_scale")
+            "les_set_warm_model", "les_unet_set_output_scale", "les_unet_get_output_scale",
+            "les_ensemble_step")
 
 
 class LesConfig(C.Structure):
@@ -128,6 +129,8 @@ def load_library(path: str = LIB_PATH):
     lib.les_step.argtypes = [vp, i32, statp]
     lib.les_stage.restype = C.c_int
     lib.les_stage.argtypes = [vp, i32, statp]
+    lib.les_ensemble_step.restype = C.c_int
+    lib.les_ensemble_step.argtypes = [C.POINTER(vp), i32, i32, statp, C.POINTER(i32)]
     lib.les_poisson_solve.restype = C.c_int
     lib.les_poisson_solve.argtypes = [vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl)]
     lib.les_apply_poisson.restype = C.c_int
@@ -482,3 +485,88 @@ def attach_model(sim: "Simulation", model) -> None:
     rc = sim.lib.les_set_warm_model(sim.h, model.h if model is not None else None)
     _check(sim.lib, sim.h, rc, "les_set_warm_model")
     sim._model = model
+
+
+class Ensemble:
+    """Independent members (each its own Simulation and stream) stepped
+    together through les_ensemble_step."""
+
+    def __init__(self, cases, device=None):
+        import torch
+        self.torch = torch
+        self.members = [Simulation(c, device=device, stream=torch.cuda.Stream(device=device)) for c in cases]
+        self.lib = self.members[0].lib
+        self.cells = sum(m.n for m in self.members)
+
+    def set_states(self, states) -> None:
+        for m, st in zip(self.members, states):
+            m.set_state(st)
+
+    def step(self, nsteps: int = 1, allow_not_converged: bool = False) -> list:
+        m = len(self.members)
+        hs = (C.c_void_p * m)(*[x.h.value for x in self.members])
+        stats = (LesStepStats * m)()
+        failed = C.c_int32(-1)
+        rc = self.lib.les_ensemble_step(hs, m, int(nsteps), stats, C.byref(failed))
+        allow = (LES_OK, LES_ERR_NOT_CONVERGED) if allow_not_converged else (LES_OK,)
+        if rc not in allow:
+            h = self.members[failed.value].h if failed.value >= 0 else None
+            _check(self.lib, h, rc, f"les_ensemble_step (member {failed.value})", allow)
+        return [st.as_dict() for st in stats]
+
+    def close(self) -> None:
+        for x in self.members:
+            x.close()
+
+
+# candidate tunings for autotune(): the predictor kernels and, for the CG,
+# the on-chip solver, its block cap, and the tiles of the streaming solver
+AUTOTUNE_CANDIDATES = (
+    {"stencil_path": 0},
+    {"stencil_path": 2},
+    {"stencil_path": 0, "cg_max_blocks": 64},
+    {"stencil_path": 0, "cg_resident": 1, "cg_variant": 2, "cg_tile_rows": 4, "cg_tile_planes": 4},
+    {"stencil_path": 0, "cg_resident": 1, "cg_variant": 2, "cg_tile_rows": 2, "cg_tile_planes": 8},
+    {"stencil_path": 0, "cg_resident": 1, "cg_variant": 3},
+)
+
+
+def autotune(sim: "Simulation", candidates=AUTOTUNE_CANDIDATES, steps: int = 2) -> dict:
+    """Time `steps` steps of the simulation under each candidate tuning (after
+    one untimed step) from the same state, keep the fastest and put the state
+    back.  Returns {"tuning": best candidate, "ms_per_step": {i: ms}}."""
+    torch = sim.torch
+    names = ("u", "v", "w", "p", "theta_l", "q_t")
+    torch.cuda.synchronize()
+    snap = {k: sim.view(k).clone() for k in names}
+    base = sim.tuning()
+    dt = sim.dt
+    timings = {}
+
+    def restore():
+        torch.cuda.synchronize()
+        for k in names:
+            sim.view(k).copy_(snap[k])
+        torch.cuda.synchronize()
+
+    for i, cand in enumerate(candidates):
+        t = dict(base)
+        t.update(cand)
+        sim.set_tuning(**t)
+        restore()
+        sim.step(1, allow_not_converged=True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(sim.stream)
+        sim.step(steps, allow_not_converged=True)
+        b.record(sim.stream)
+        b.synchronize()
+        timings[i] = a.elapsed_time(b) / steps
+    best = min(timings, key=timings.get)
+    t = dict(base)
+    t.update(candidates[best])
+    sim.set_tuning(**t)
+    restore()
+    if dt:
+        sim.dt = dt
+    return {"tuning": dict(candidates[best]), "ms_per_step": timings}

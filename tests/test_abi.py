@@ -66,3 +66,17 @@ def test_workspace_bytes_and_validation(lib):
     assert lib.les_init(C.byref(good), None, None, 0, None, C.byref(h)) == les.LES_ERR_INVALID_ARG
     assert lib.les_status_string(3) == b"Poisson solve did not converge"
     assert lib.les_last_error(None) == b"no handle"
+
+
+def test_ensemble_members_are_seeded_and_uneven():
+    from paper_2301_04698_gb300 import inputs
+    a = inputs.ensemble(16, seed=1)
+    b = inputs.ensemble(16, seed=1)
+    c = inputs.ensemble(16, seed=2)
+    assert [(x.nx, x.ny, x.nz, x.shf, x.seed) for x in a] == [(x.nx, x.ny, x.nz, x.shf, x.seed) for x in b]
+    assert [(x.nx, x.nz) for x in a] != [(x.nx, x.nz) for x in c]
+    assert len({(x.nx, x.nz) for x in a}) > 4
+    for x in a:
+        assert x.nx in (64, 96, 128, 160, 192) and x.nz in (64, 96, 128) and x.nx == x.ny
+        assert 0.5 * 15.0 <= x.shf < 1.5 * 15.0 and 0.5 * 3.75e-6 <= x.subs_div < 1.5 * 3.75e-6
+    assert len({inputs.cbl_draws(x)["zi"] for x in a}) == 16   # every member its own inversion

@@ -1,0 +1,87 @@
+"""Ensembles of independent members stepped together (les_ensemble_step) and
+the autotuner: every member reaches exactly the state of the same member run
+alone, and the autotuner leaves the state it tunes on unchanged."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2301_04698_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def les_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2301_04698_gb300 import build, les
+    build.build()
+    les.load_library()
+    return les
+
+
+def _members():
+    return inputs.ensemble(4, seed=3, xy=(32, 48, 64), zs=(16, 24))
+
+
+def test_ensemble_matches_solo_runs(les_mod):
+    cases = _members()
+    assert len({(c.nx, c.nz) for c in cases}) > 1          # uneven grids
+    ens = les_mod.Ensemble(cases)
+    ens.set_states([inputs.initial_state(c) for c in cases])
+    stats = ens.step(2)
+    assert all(s["not_converged"] == 0 and s["solves"] == 2 * c.K for s, c in zip(stats, cases))
+    torch.cuda.synchronize()
+    for c, m in zip(cases, ens.members):
+        solo = les_mod.Simulation(c)
+        solo.set_state(inputs.initial_state(c))
+        solo.step(2)
+        for f in ("u", "v", "w", "p", "theta_l", "q_t"):
+            assert np.array_equal(m.get(f), solo.get(f)), (c.name, f)
+        solo.close()
+    ens.close()
+
+
+def test_ensemble_member_against_oracle(les_mod):
+    from oracle import Oracle
+    c = _members()[1]
+    ens = les_mod.Ensemble([c, _members()[0]])
+    st = inputs.initial_state(c)
+    ens.set_states([st, inputs.initial_state(_members()[0])])
+    ens.step(1)
+    ref = Oracle(c.replace(precision=64), st)
+    ref.step(1)
+    sim = ens.members[0]
+    for f in ("u", "v", "theta_l", "q_t"):
+        a, b = sim.get(f), ref.get(f)
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5, f
+    ens.close()
+
+
+def test_ensemble_rejects_repeated_handles(les_mod):
+    c = _members()[0]
+    sim = les_mod.Simulation(c)
+    hs = (C.c_void_p * 2)(sim.h.value, sim.h.value)
+    failed = C.c_int32(0)
+    rc = sim.lib.les_ensemble_step(hs, 2, 1, None, C.byref(failed))
+    assert rc == les_mod.LES_ERR_INVALID_ARG
+    sim.close()
+
+
+def test_autotune_keeps_the_state(les_mod):
+    c = _members()[2]
+    sim = les_mod.Simulation(c)
+    sim.set_state(inputs.initial_state(c))
+    sim.step(1)
+    before = {f: sim.get(f) for f in ("u", "v", "w", "p", "theta_l", "q_t")}
+    res = les_mod.autotune(sim)
+    assert res["tuning"] in [dict(x) for x in les_mod.AUTOTUNE_CANDIDATES]
+    assert len(res["ms_per_step"]) == len(les_mod.AUTOTUNE_CANDIDATES)
+    for f, v in before.items():
+        assert np.array_equal(sim.get(f), v), f
+    # and it keeps stepping with the chosen tuning
+    st = sim.step(1)
+    assert st["not_converged"] == 0
+    sim.close()
