@@ -82,8 +82,6 @@ struct FusedArgs {
   long long spin_cycles;
   unsigned expected;
   int guard;  // arrivals per barrier: gridDim.x (+ the test hook's missing ones)
-  int async_a;          // phase A stages through cp.async (raw buffers after the staging buffer)
-  long long raw_off;    // element offset of the raw buffers in dynamic shared memory
 };
 
 __device__ __forceinline__ int zmap(int k, int nz, int walls) {
@@ -171,137 +169,10 @@ __device__ __forceinline__ void stencil_sweep(const FusedArgs<T>& f, T* sm, cons
   }
 }
 
-// ---- phase A with asynchronous staging ------------------------------------------
-// The tile's planes of r and p_old are copied raw into shared memory with
-// cp.async -- every copy of a tile in flight at once, and the next tile's
-// while this one is computed (two raw buffers) -- and combined there into
-// p = r + beta p_old.  Raw rows hold the tile's W nodes at offset VW with
-// the x-halo nodes beside them, so every interior copy is 16 bytes, aligned.
-__device__ __forceinline__ void cpa16(void* dst, const void* src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cpa_el(float* dst, const float* src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cpa_el(double* dst, const double* src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cpa_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// raw staging floats per block for tile rows ty and planes zc (two buffers,
-// two fields)
-template <typename T>
-__host__ __device__ constexpr size_t async_raw_elems(int ty, int zc) {
-  return (size_t)2 * 2 * (zc + 2) * (ty + 2) * (VT<T>::W + 2 * VT<T>::VW);
-}
-
-template <typename T, typename Emit>
-__device__ __forceinline__ void sweep_phase_a(const FusedArgs<T>& f, T* sm, T* raw, const T* r, const T* po,
-                                              T tb, bool first, const Emit& emit) {
-  constexpr int VW = VT<T>::VW, W = VT<T>::W, CH = W / VW;
-  const int tx = threadIdx.x, ty = threadIdx.y, TY = blockDim.y;
-  const int tid = tx + 32 * ty, nthr = 32 * TY;
-  const int SW = W + 2, SP = (TY + 2) * SW;         // combined buffer strides
-  const int RW = W + 2 * VW, RP = (TY + 2) * RW;    // raw buffer strides
-  const int NPL = (f.zc + 2) * RP;                  // one field of one raw buffer
-  auto lin = [&](int xx, int yy, int kk) -> size_t { return ((size_t)kk * f.ny + yy) * f.nx + xx; };
-  auto origin = [&](long long t, int& x0, int& y0, int& k0, int& nzt) {
-    const int ti = (int)(t % f.ntx);
-    const long long rr = t / f.ntx;
-    x0 = ti * W;
-    y0 = (int)(rr % f.nty) * TY;
-    k0 = (int)(rr / f.nty) * f.zc;
-    nzt = min(k0 + f.zc, f.nz) - k0;
-  };
-  // copies of tile t into raw buffer b: planes k0-1 .. k0+nzt, rows y0-1 ..
-  // y0+TY, CH 16-byte chunks plus the two x-halo nodes per row
-  auto issue = [&](long long t, int b) {
-    int x0, y0, k0, nzt;
-    origin(t, x0, y0, k0, nzt);
-    T* rb = raw + (size_t)b * 2 * NPL;
-    const int xl = x0 == 0 ? f.nx - 1 : x0 - 1;
-    const int xr = x0 + W == f.nx ? 0 : x0 + W;
-    // one warp per (plane, row); lanes over the row's chunks and halo nodes
-    const int lane = tid & 31, nwarp = nthr >> 5;
-    for (int qr = tid >> 5; qr < (nzt + 2) * (TY + 2); qr += nwarp) {
-      const int q = qr / (TY + 2), row = qr - q * (TY + 2);
-      const int kk = zmap(k0 - 1 + q, f.nz, f.walls);
-      int yy = y0 - 1 + row;
-      yy = yy < 0 ? yy + f.ny : (yy >= f.ny ? yy - f.ny : yy);
-      T* d = rb + q * RP + row * RW;
-      const size_t mrow = lin(0, yy, kk);
-      for (int c = lane; c < CH + 2; c += 32) {
-        if (c < CH) {
-          const size_t m = mrow + x0 + c * VW;
-          cpa16(d + VW + c * VW, r + m);
-          if (!first) cpa16(d + NPL + VW + c * VW, po + m);
-        } else {
-          const size_t m = mrow + (c == CH ? xl : xr);
-          const int o = c == CH ? VW - 1 : VW + W;
-          cpa_el(d + o, r + m);
-          if (!first) cpa_el(d + NPL + o, po + m);
-        }
-      }
-    }
-    cpa_commit();
-  };
-  long long t = blockIdx.x;
-  int b = 0;
-  __syncthreads();  // earlier readers of the buffers are done
-  if (t < f.ntiles) issue(t, 0);
-  for (; t < f.ntiles; t += gridDim.x, b ^= 1) {
-    const long long tn = t + gridDim.x;
-    if (tn < f.ntiles) {
-      issue(tn, b ^ 1);
-      cpa_wait<1>();
-    } else {
-      cpa_wait<0>();
-    }
-    __syncthreads();
-    int x0, y0, k0, nzt;
-    origin(t, x0, y0, k0, nzt);
-    const T* rb = raw + (size_t)b * 2 * NPL;
-    {
-      const int lane = tid & 31, nwarp = nthr >> 5;
-      for (int qr = tid >> 5; qr < (nzt + 2) * (TY + 2); qr += nwarp) {
-        const int q = qr / (TY + 2), row = qr - q * (TY + 2);
-        const T* src = rb + q * RP + row * RW + VW - 1;
-        T* dst = sm + q * SP + row * SW;
-        if (first)
-          for (int col = lane; col < SW; col += 32) dst[col] = src[col];
-        else
-          for (int col = lane; col < SW; col += 32) dst[col] = src[col] + tb * src[NPL + col];
-      }
-    }
-    __syncthreads();
-    const int xs = x0 + tx * VW, y = y0 + ty;
-    for (int q = 1; q <= nzt; ++q) {
-      const T* row = sm + q * SP + (1 + ty) * SW + 1 + tx * VW;
-      T P[VW], qv[VW];
-#pragma unroll
-      for (int e = 0; e < VW; ++e) {
-        const T c = row[e];
-        P[e] = c;
-        qv[e] = (row[e - 1] + row[e + 1] - T(2) * c) * f.cx + (row[e - SW] + row[e + SW] - T(2) * c) * f.cy +
-                (row[e - SP] + row[e + SP] - T(2) * c) * f.cz;
-      }
-      emit(lin(xs, y, k0 + q - 1), P, qv);
-    }
-    __syncthreads();  // the combined buffer and raw buffer b are free again
-  }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(256, 2) k_cg_fused(FusedArgs<T> f) {
   constexpr int VW = VT<T>::VW;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const long long gstride = (long long)gridDim.x * blockDim.x * blockDim.y;
@@ -397,8 +268,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_fused(FusedArgs<T> f) {
       stv(f.q + m, qv);
       sa[0] += vdot(P, qv);
     };
-    if (f.async_a) sweep_phase_a(f, sm, sm + f.raw_off, r, po, tb, first, emitQ);
-    else stencil_sweep(f, sm, loadP, loadP1, emitQ);
+    stencil_sweep(f, sm, loadP, loadP1, emitQ);
     if (!grid_sum<1>(sa, gs)) {
       status = 5;
       break;
@@ -736,20 +606,7 @@ int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, 
   f.maxit = maxit;
   f.spin_cycles = fc.spin_cycles;
   const dim3 block(32, fc.ty);
-  size_t smem = (size_t)(f.zc + 2) * (fc.ty + 2) * (W + 2) * sizeof(T);
-  // the standard CG stages phase A asynchronously when both raw buffers fit
-  // beside the staging buffer for two blocks per SM
-  f.async_a = 0;
-  f.raw_off = 0;
-  {
-    const size_t al = (smem + 15) / 16 * 16;
-    const size_t tot = al + async_raw_elems<T>(fc.ty, f.zc) * sizeof(T);
-    if (fc.variant != 1 && tot <= 113 * 1024) {
-      f.async_a = 1;
-      f.raw_off = (long long)(al / sizeof(T));
-      smem = tot;
-    }
-  }
+  const size_t smem = (size_t)(f.zc + 2) * (fc.ty + 2) * (W + 2) * sizeof(T);
   const bool cgg = fc.variant == 1 && a.e0 && a.e1 && a.e2;
   const void* kern = cgg ? (const void*)k_cg_cgg<T> : (const void*)k_cg_fused<T>;
   int per_sm = 0, dev = 0, nsm = 0;
