@@ -377,7 +377,8 @@ int stage_momentum(les_handle* h) {
       return h->cuda_fail(e, "momentum predictor");
   }
   if ((e = h->fused.stencil_path == 0
-               ? launch_rhs_roll<T>(a, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI], F[B_RHS])
+               ? launch_rhs_roll<T>(a, h->L.max_blocks, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI],
+                                    F[B_RHS])
                : launch_rhs<T>(a, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI], F[B_RHS])) !=
       cudaSuccess)
     return h->cuda_fail(e, "poisson rhs");

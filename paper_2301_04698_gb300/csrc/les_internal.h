@@ -86,8 +86,9 @@ struct FusedBar {
 
 // Tile shape and limits of the persistent solver.
 struct FusedCfg {
-  int ty = 4;                           // thread rows per block (block = 32 x ty)
-  int zc = 4;                           // z-planes per tile
+  int ty = 2;                           // thread rows per block (block = 32 x ty)
+  int zc = 8;                           // z-planes per tile (2 x 8: fastest of a sweep at 1024^2 x 128
+                                        // and 1536^2 x 256, FP32)
   int max_blocks = 1 << 30;             // cap on the cooperative grid
   long long spin_cycles = 4000000000LL; // barrier wait limit (~2 s at 2 GHz)
   double timeout_ms = 2000.0;
@@ -230,8 +231,8 @@ cudaError_t launch_momentum_tiled(const StageArgs<T>& a, int max_blocks, const T
                                   T* ow);
 // rolling-window predictors and Poisson right side (les_stencil_roll.cu)
 template <typename T>
-cudaError_t launch_rhs_roll(const StageArgs<T>& a, int op, const T* ou, const T* ov, const T* ow, const T* psi,
-                            T* rhs);
+cudaError_t launch_rhs_roll(const StageArgs<T>& a, int max_blocks, int op, const T* ou, const T* ov, const T* ow,
+                            const T* psi, T* rhs);
 template <typename T>
 cudaError_t launch_scalar_roll(const StageArgs<T>& a, int max_blocks, const T* u, const T* v, const T* w,
                                const T* b, const T* thk, const T* qtk, const T* thh, const T* qth, const T* srad,

@@ -571,12 +571,13 @@ __global__ void __launch_bounds__(256) k_rhs_roll(RhsRoll<T> a) {
   }
 }
 
-// z-runs: enough blocks to fill the GPU, runs as long as possible
-inline void roll_runs(int nx, int ny, int nz, int& ntx, int& nty, int& zrun, int& nchunk) {
+// z-runs: at least `blocks` (column, run) items to fill the GPU, runs as
+// long as possible
+inline void roll_runs(int nx, int ny, int nz, long long blocks, int& ntx, int& nty, int& zrun, int& nchunk) {
   ntx = (nx + RX - 1) / RX;
   nty = (ny + RY - 1) / RY;
   const long long ncol = (long long)ntx * nty;
-  const int want = (int)std::max<long long>(1, std::min<long long>((long long)nz, (4LL * 152 + ncol - 1) / ncol));
+  const int want = (int)std::max<long long>(1, std::min<long long>((long long)nz, (blocks + ncol - 1) / ncol));
   zrun = (nz + want - 1) / want;
   nchunk = (nz + zrun - 1) / zrun;
 }
@@ -584,8 +585,8 @@ inline void roll_runs(int nx, int ny, int nz, int& ntx, int& nty, int& zrun, int
 }  // namespace
 
 template <typename T>
-cudaError_t launch_rhs_roll(const StageArgs<T>& a, int op, const T* ou, const T* ov, const T* ow, const T* psi,
-                            T* rhs) {
+cudaError_t launch_rhs_roll(const StageArgs<T>& a, int max_blocks, int op, const T* ou, const T* ov, const T* ow,
+                            const T* psi, T* rhs) {
   RhsRoll<T> r;
   r.g = a.g;
   r.ph = a.ph;
@@ -596,9 +597,9 @@ cudaError_t launch_rhs_roll(const StageArgs<T>& a, int op, const T* ou, const T*
   r.psi = psi;
   r.rhs = rhs;
   // one thread per (column, z-run): enough threads for four 256-thread
-  // blocks per SM, runs as long as possible
+  // blocks per SM (max_blocks is eight per SM), runs as long as possible
   const long long ncol = (long long)a.g.nx * a.g.ny;
-  const long long want = 4LL * 152 * 256;
+  const long long want = (long long)(max_blocks / 2) * 256;
   const long long nch = std::max<long long>(1, std::min<long long>(a.g.nz, (want + ncol - 1) / ncol));
   r.zrun = (int)((a.g.nz + nch - 1) / nch);
   r.nchunk = (a.g.nz + r.zrun - 1) / r.zrun;
@@ -616,7 +617,8 @@ cudaError_t launch_scalar_roll(const StageArgs<T>& a, int max_blocks, const T* u
   ScaRoll<T> r;
   r.g = a.g;
   r.ph = a.ph;
-  roll_runs(a.g.nx, a.g.ny, a.g.nz, r.ntx, r.nty, r.zrun, r.nchunk);
+  // max_blocks is eight blocks per SM: aim at four resident per SM
+  roll_runs(a.g.nx, a.g.ny, a.g.nz, max_blocks / 2, r.ntx, r.nty, r.zrun, r.nchunk);
   r.u = u;
   r.v = v;
   r.w = w;
@@ -647,7 +649,7 @@ cudaError_t launch_momentum_roll(const StageArgs<T>& a, int max_blocks, const T*
   MomRoll<T> m;
   m.g = a.g;
   m.ph = a.ph;
-  roll_runs(a.g.nx, a.g.ny, a.g.nz, m.ntx, m.nty, m.zrun, m.nchunk);
+  roll_runs(a.g.nx, a.g.ny, a.g.nz, max_blocks / 2, m.ntx, m.nty, m.zrun, m.nchunk);
   const long long ncol = (long long)m.ntx * m.nty;
   m.uk = uk;
   m.vk = vk;
@@ -671,9 +673,9 @@ cudaError_t launch_momentum_roll(const StageArgs<T>& a, int max_blocks, const T*
   return cudaGetLastError();
 }
 
-template cudaError_t launch_rhs_roll<float>(const StageArgs<float>&, int, const float*, const float*, const float*,
-                                            const float*, float*);
-template cudaError_t launch_rhs_roll<double>(const StageArgs<double>&, int, const double*, const double*,
+template cudaError_t launch_rhs_roll<float>(const StageArgs<float>&, int, int, const float*, const float*,
+                                            const float*, const float*, float*);
+template cudaError_t launch_rhs_roll<double>(const StageArgs<double>&, int, int, const double*, const double*,
                                              const double*, const double*, double*);
 template cudaError_t launch_scalar_roll<float>(const StageArgs<float>&, int, const float*, const float*,
                                                const float*, const float*, const float*, const float*, const float*,
