@@ -17,10 +17,13 @@
 //            published; q = L_c p; p.q
 //   phase B  x += alpha p, r -= alpha q; r faces published; r.r
 // each followed by a grid-wide sum (les_gridsync.cuh; FP32 dot products are
-// accumulated as compensated FP32 pairs, FP64 ones in FP64).  Ghost loads
-// are issued in batches so that each costs one round of memory latency.
+// accumulated as compensated FP32 pairs, FP64 ones in FP64).  After the
+// second grid sum the ghost loads of r and p_old are issued in one batch
+// whose latency overlaps the end of the iteration in thread 0 (beta and the
+// convergence test) and the owned update.
 #include <algorithm>
 #include <string>
+#include <type_traits>
 
 #include "les_gridsync.cuh"
 #include "les_internal.h"
@@ -60,8 +63,10 @@ __device__ __forceinline__ int zghost(int k, int nz, int walls) {
 template <typename T, int BX>
 __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
   constexpr int L = BX / 32;  // nodes per lane along a brick row
-  // ghost rows per warp whose loads are in flight together (within the registers)
-  constexpr int RB = sizeof(T) == 4 ? 4 : (L >= 4 ? 1 : (L >= 2 ? 2 : 4));
+  // ghost rows per warp (and x-face ghosts per thread) whose loads are in
+  // flight together, within the registers
+  constexpr int RB = sizeof(T) == 4 ? (L >= 4 ? 2 : 4) : (L >= 2 ? 1 : 2);
+  constexpr int XB = sizeof(T) == 4 ? 4 : 2;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int by = f.by, bz = f.bz;
   const int SY = BX + 2, SZ = (BX + 2) * (by + 2);  // strides of the haloed p brick
@@ -119,12 +124,14 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
       }
     }
   };
-  // fill the ghost layer of P: val(g) for each face-neighbour node outside
-  // the brick (edges and corners are not used by the 7-point stencil).  Rows
-  // along x: the two z faces (2 by rows), then the two y faces (2 bz rows);
-  // the two x faces are strided single nodes.  When one batch of loads per
-  // thread covers all of them, between() runs while the loads are in flight.
-  constexpr int XB = 4;
+  // fill the ghost layer of P with a + coef b (or a) for each face-neighbour
+  // node outside the brick (edges and corners are not used by the 7-point
+  // stencil).  Rows along x: the two z faces (2 by rows), then the two y faces
+  // (2 bz rows); the two x faces are strided single nodes.  Every load of a
+  // batch is issued before any loaded value is used, so a batch costs one
+  // round of memory latency; when one batch per thread covers all ghosts,
+  // between() runs while the loads are in flight, and coef is read after it
+  // (between() may set it).
   const int nr = 2 * by + 2 * bz;
   const bool one_round = nr <= RB * nwarp && 2 * nrow <= XB * nthr;
   auto ghost_row = [&](int row, int& ly, int& lz) {
@@ -136,9 +143,11 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
       ly = (row & 1) ? by : -1;
     }
   };
-  auto ghosts = [&](auto&& val, auto&& between) {
+  auto ghosts = [&](auto two, const T* A, const T* B, const T& coef, auto&& between) {
+    constexpr bool TWO = decltype(two)::value;
+    constexpr int RB2 = TWO ? RB : 1, L2 = TWO ? L : 1, XB2 = TWO ? XB : 1;
     if (one_round) {
-      T v[RB][L], xv[XB];
+      T va[RB][L], vb[RB2][L2], xa[XB], xb[XB2];
       int pr[RB], xpi[XB];
 #pragma unroll
       for (int q = 0; q < RB; ++q) {
@@ -150,7 +159,10 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
           pr[q] = (lz + 1) * SZ + (ly + 1) * SY + 1;
           const size_t g0 = gidx(0, ly, lz);
 #pragma unroll
-          for (int u = 0; u < L; ++u) v[q][u] = val(g0 + lane + 32 * u);
+          for (int u = 0; u < L; ++u) {
+            va[q][u] = __ldcg(A + g0 + lane + 32 * u);
+            if constexpr (TWO) vb[q][u] = __ldcg(B + g0 + lane + 32 * u);
+          }
         }
       }
 #pragma unroll
@@ -160,23 +172,33 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
         if (c < 2 * nrow) {
           const int row = c >> 1, ly = row % by, lz = row / by, lx = (c & 1) ? BX : -1;
           xpi[q] = (lz + 1) * SZ + (ly + 1) * SY + 1 + lx;
-          xv[q] = val(gidx(lx, ly, lz));
+          const size_t g = gidx(lx, ly, lz);
+          xa[q] = __ldcg(A + g);
+          if constexpr (TWO) xb[q] = __ldcg(B + g);
         }
       }
       between();
+      const T cf = coef;
 #pragma unroll
       for (int q = 0; q < RB; ++q)
         if (pr[q] >= 0)
 #pragma unroll
-          for (int u = 0; u < L; ++u) P[pr[q] + lane + 32 * u] = v[q][u];
+          for (int u = 0; u < L; ++u) {
+            if constexpr (TWO) P[pr[q] + lane + 32 * u] = va[q][u] + cf * vb[q][u];
+            else P[pr[q] + lane + 32 * u] = va[q][u];
+          }
 #pragma unroll
       for (int q = 0; q < XB; ++q)
-        if (xpi[q] >= 0) P[xpi[q]] = xv[q];
+        if (xpi[q] >= 0) {
+          if constexpr (TWO) P[xpi[q]] = xa[q] + cf * xb[q];
+          else P[xpi[q]] = xa[q];
+        }
       return;
     }
     between();
+    const T cf = coef;
     for (int r0 = warp; r0 < nr; r0 += RB * nwarp) {
-      T v[RB][L];
+      T va[RB][L], vb[RB2][L2];
       int pr[RB];
 #pragma unroll
       for (int q = 0; q < RB; ++q) {
@@ -188,17 +210,23 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
           pr[q] = (lz + 1) * SZ + (ly + 1) * SY + 1;
           const size_t g0 = gidx(0, ly, lz);
 #pragma unroll
-          for (int u = 0; u < L; ++u) v[q][u] = val(g0 + lane + 32 * u);
+          for (int u = 0; u < L; ++u) {
+            va[q][u] = __ldcg(A + g0 + lane + 32 * u);
+            if constexpr (TWO) vb[q][u] = __ldcg(B + g0 + lane + 32 * u);
+          }
         }
       }
 #pragma unroll
       for (int q = 0; q < RB; ++q)
         if (pr[q] >= 0)
 #pragma unroll
-          for (int u = 0; u < L; ++u) P[pr[q] + lane + 32 * u] = v[q][u];
+          for (int u = 0; u < L; ++u) {
+            if constexpr (TWO) P[pr[q] + lane + 32 * u] = va[q][u] + cf * vb[q][u];
+            else P[pr[q] + lane + 32 * u] = va[q][u];
+          }
     }
     for (int c0 = tid; c0 < 2 * nrow; c0 += XB * nthr) {
-      T v[XB];
+      T xa[XB], xb[XB2];
       int pi[XB];
 #pragma unroll
       for (int q = 0; q < XB; ++q) {
@@ -207,12 +235,17 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
         if (c < 2 * nrow) {
           const int row = c >> 1, ly = row % by, lz = row / by, lx = (c & 1) ? BX : -1;
           pi[q] = (lz + 1) * SZ + (ly + 1) * SY + 1 + lx;
-          v[q] = val(gidx(lx, ly, lz));
+          const size_t g = gidx(lx, ly, lz);
+          xa[q] = __ldcg(A + g);
+          if constexpr (TWO) xb[q] = __ldcg(B + g);
         }
       }
 #pragma unroll
       for (int q = 0; q < XB; ++q)
-        if (pi[q] >= 0) P[pi[q]] = v[q];
+        if (pi[q] >= 0) {
+          if constexpr (TWO) P[pi[q]] = xa[q] + cf * xb[q];
+          else P[pi[q]] = xa[q];
+        }
     }
   };
   auto nothing = [] {};
@@ -253,7 +286,8 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
       X[c] = v;
       P[pi] = v;
     });
-    ghosts([&](size_t g) { return __ldcg(f.x + g); }, nothing);
+    const T one = T(1);
+    ghosts(std::false_type{}, f.x, nullptr, one, nothing);
     __syncthreads();
     Dot<T> a2[2];
     own([&](int c, int pi, size_t g, bool face) {
@@ -305,79 +339,99 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
   __syncthreads();
   status = sc.status;
 
+  // convergence: |r| <= tol |b - mean| tested as r.r <= tol^2 |b - mean|^2,
+  // so that no square root sits between two iterations
+  const double rr_stop = f.tol * f.tol * bb;  // meaningful in thread 0
   int iter = 0;
   T tb = T(0);
-  while (!status) {
-    const bool first = iter == 0;
-    T* pw = (iter & 1) ? f.pg1 : f.pg0;         // this iteration's p faces
-    const T* po = (iter & 1) ? f.pg0 : f.pg1;   // the previous iteration's
-    // phase A: p = r + beta p (owned in place, ghosts from published faces;
-    // the owned update runs while the ghost loads are in flight)
-    auto update = [&] {
-      own([&](int c, int pi, size_t g, bool face) {
-        const T pv = first ? R[c] : R[c] + tb * P[pi];
-        P[pi] = pv;
-        if (face) __stcg(pw + g, pv);
-      });
-    };
-    if (first) ghosts([&](size_t g) { return __ldcg(f.rg + g); }, update);
-    else ghosts([&](size_t g) { return __ldcg(f.rg + g) + tb * __ldcg(po + g); }, update);
-    __syncthreads();
-    Dot<T> apq[1];
-    own([&](int c, int pi, size_t, bool) {
-      const T qv = Lc(pi);
-      Q[c] = qv;
-      apq[0].add(P[pi] * qv);
-    });
-    {
-      double t[1];
-      const bool ok = grid_dot_t0<1>(apq, gs, t);
-      if (tid == 0) {
-        const double pq = t[0];
-        if (!ok) status = 5;
-        else if (pq == 0.0 || !isfinite(pq)) status = 3;
-        else sc.ta = (T)(rr / pq);
-        sc.status = status;
+  double rr_new = 0.0;  // thread 0: r.r of the grid sum that closed the last iteration
+  bool sum_ok = true;   // thread 0: that grid sum completed
+  // the end of an iteration in thread 0 (beta, convergence, status),
+  // broadcast to the block
+  auto close_iter = [&] {
+    if (tid == 0) {
+      if (!sum_ok) {
+        status = 5;
+      } else {
+        beta = rr_new / rr;
+        rr = rr_new;
+        if (rr_new <= rr_stop) status = 1;
+        else if (iter >= f.maxit) status = 2;
+        else if (!isfinite(rr_new)) status = 3;
+        sc.tb = (T)beta;
       }
-      __syncthreads();
-      status = sc.status;
-      if (status) break;
+      sc.status = status;
     }
-    const T ta = sc.ta;
-    // phase B: x += alpha p, r -= alpha q, r faces published, r.r
-    Dot<T> ar[1];
-    own([&](int c, int pi, size_t g, bool face) {
-      const T pv = P[pi];
-      X[c] += ta * pv;
-      const T rv = R[c] - ta * Q[c];
-      R[c] = rv;
-      if (face) __stcg(f.rg + g, rv);
-      ar[0].add(rv * rv);
-    });
-    {
+    __syncthreads();
+    status = sc.status;
+    tb = sc.tb;
+  };
+  if (!status) {
+    for (;;) {
+      const bool first = iter == 0;
+      T* pw = (iter & 1) ? f.pg1 : f.pg0;        // this iteration's p faces
+      const T* po = (iter & 1) ? f.pg0 : f.pg1;  // the previous iteration's
+      // phase A: p = r + beta p (owned in place, ghosts from published faces
+      // as r + beta p_old).  The ghost loads are issued first; while they are
+      // in flight thread 0 closes the previous iteration (beta, status) and
+      // the block updates its owned nodes.
+      auto update = [&] {
+        if (!first) close_iter();
+        if (status) return;
+        own([&](int c, int pi, size_t g, bool face) {
+          const T pv = first ? R[c] : R[c] + tb * P[pi];
+          P[pi] = pv;
+          if (face) __stcg(pw + g, pv);
+        });
+      };
+      if (first) ghosts(std::false_type{}, f.rg, nullptr, tb, update);
+      else ghosts(std::true_type{}, f.rg, po, tb, update);
+      if (status) break;  // the ghosts just written are not used
+      __syncthreads();
+      Dot<T> apq[1];
+      own([&](int c, int pi, size_t, bool) {
+        const T qv = Lc(pi);
+        Q[c] = qv;
+        apq[0].add(P[pi] * qv);
+      });
+      {
+        double t[1];
+        const bool ok = grid_dot_t0<1>(apq, gs, t);
+        if (tid == 0) {
+          const double pq = t[0];
+          if (!ok) status = 5;
+          else if (pq == 0.0 || !isfinite(pq)) status = 3;
+          else sc.ta = (T)(rr / pq);
+          sc.status = status;
+        }
+        __syncthreads();
+        status = sc.status;
+        if (status) break;
+      }
+      const T ta = sc.ta;
+      // phase B: x += alpha p, r -= alpha q, r faces published, r.r
+      Dot<T> ar[1];
+      own([&](int c, int pi, size_t g, bool face) {
+        const T pv = P[pi];
+        X[c] += ta * pv;
+        const T rv = R[c] - ta * Q[c];
+        R[c] = rv;
+        if (face) __stcg(f.rg + g, rv);
+        ar[0].add(rv * rv);
+      });
       double t[1];
       const bool ok = grid_dot_t0<1>(ar, gs, t);
       iter += 1;
       if (tid == 0) {
-        if (!ok) {
-          status = 5;
-        } else {
-          const double rr_new = t[0];
-          rel = sqrt(rr_new / bb);
-          beta = rr_new / rr;
-          rr = rr_new;
-          if (rel <= f.tol) status = 1;
-          else if (iter >= f.maxit) status = 2;
-          else if (!isfinite(rr_new)) status = 3;
-          sc.tb = (T)beta;
-        }
-        sc.status = status;
+        sum_ok = ok;
+        rr_new = t[0];
       }
+      // the grid sum has completed (or timed out, which close_iter reports):
+      // from here every thread may read the faces the other blocks published
       __syncthreads();
-      status = sc.status;
-      tb = sc.tb;
     }
   }
+  if (tid == 0 && iter > 0 && bb > 0.0) rel = sqrt(rr / bb);
 
   // zero-mean gauge (or zero for a zero right side), written back to x
   if (status != 5) {

@@ -42,21 +42,6 @@ size_t roll_smem() {
   return (size_t)(2 * D * SN + D * CX * CY + 8 * SN) * sizeof(T);
 }
 
-// element-wise asynchronous global -> shared copies (cp.async, L1-allocating)
-__device__ __forceinline__ void cp_async(float* dst, const float* src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async(double* dst, const double* src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 template <typename T>
 struct RollArgs {
   int nx, ny, nz, walls;
