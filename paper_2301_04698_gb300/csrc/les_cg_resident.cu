@@ -17,10 +17,11 @@
 //            published; q = L_c p; p.q
 //   phase B  x += alpha p, r -= alpha q; r faces published; r.r
 // each followed by a grid-wide sum (les_gridsync.cuh; FP32 dot products are
-// accumulated as compensated FP32 pairs, FP64 ones in FP64).  After the
-// second grid sum the ghost loads of r and p_old are issued in one batch
-// whose latency overlaps the end of the iteration in thread 0 (beta and the
-// convergence test) and the owned update.
+// accumulated as compensated FP32 pairs, FP64 ones in FP64).  The p_old
+// faces are copied into the ghost layer asynchronously while the second grid
+// sum is in flight, so that after it only the r faces are loaded, in one
+// batch whose latency overlaps the end of the iteration in thread 0 (beta
+// and the convergence test) and the owned update.
 #include <algorithm>
 #include <string>
 #include <type_traits>
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
   constexpr int L = BX / 32;  // nodes per lane along a brick row
   // ghost rows per warp (and x-face ghosts per thread) whose loads are in
   // flight together, within the registers
-  constexpr int RB = sizeof(T) == 4 ? (L >= 4 ? 2 : 4) : (L >= 2 ? 1 : 2);
+  constexpr int RB = sizeof(T) == 4 ? (L >= 4 ? 3 : 4) : (L >= 2 ? 1 : 2);
   constexpr int XB = sizeof(T) == 4 ? 4 : 2;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int by = f.by, bz = f.bz;
@@ -100,8 +101,13 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
     return (P[pi - 1] + P[pi + 1] - c2) * cx + (P[pi - SY] + P[pi + SY] - c2) * cy +
            (P[pi - SZ] + P[pi + SZ] - c2) * cz;
   };
+  // A brick spanning the periodic x extent is its own x neighbour: its x
+  // ghosts are copies of its own end nodes, written with them, and its x
+  // faces are not published.
+  const bool xself = f.px == 1;
   // body(c, pi, g, face) for every owned node: c its index in R / X, pi in P,
-  // g in global memory; face: the node lies on the brick surface
+  // g in global memory; face: the node lies on a brick surface that a
+  // neighbour reads
   // the row table: row index arithmetic once per launch, not once per pass
   const size_t gbase = ((size_t)k0 * f.ny + j0) * f.nx + i0;
   for (int row = tid; row < nrow; row += nthr) {
@@ -111,6 +117,16 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
     ROWS[row] = make_int2(prow | (rface ? (int)0x80000000u : 0), (lz * f.ny + ly) * f.nx);
   }
   __syncthreads();
+  // store p at owned node (c, pi), and at its periodic x image in the ghost
+  // layer for a brick that is its own x neighbour
+  auto put_p = [&](int c, int pi, T v) {
+    P[pi] = v;
+    if (xself) {
+      const int lx = c & (BX - 1);
+      if (lx == 0) P[pi + BX] = v;
+      else if (lx == BX - 1) P[pi - BX] = v;
+    }
+  };
   auto own = [&](auto&& body) {
     for (int row = warp; row < nrow; row += nwarp) {
       const int2 t = ROWS[row];
@@ -120,20 +136,23 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
 #pragma unroll
       for (int u = 0; u < L; ++u) {
         const int lx = lane + 32 * u;
-        body(row * BX + lx, prow + lx, grow + lx, rface || lx == 0 || lx == BX - 1);
+        body(row * BX + lx, prow + lx, grow + lx, rface || (!xself && (lx == 0 || lx == BX - 1)));
       }
     }
   };
-  // fill the ghost layer of P with a + coef b (or a) for each face-neighbour
-  // node outside the brick (edges and corners are not used by the 7-point
-  // stencil).  Rows along x: the two z faces (2 by rows), then the two y faces
-  // (2 bz rows); the two x faces are strided single nodes.  Every load of a
-  // batch is issued before any loaded value is used, so a batch costs one
-  // round of memory latency; when one batch per thread covers all ghosts,
-  // between() runs while the loads are in flight, and coef is read after it
-  // (between() may set it).
+  // fill the ghost layer of P with a, or with a + coef P where the ghost
+  // layer already holds a staged second operand (stage() below), for each
+  // face-neighbour node outside the brick (edges and corners are not used by
+  // the 7-point stencil).  Rows along x: the two z faces (2 by rows), then
+  // the two y faces (2 bz rows); the two x faces are strided single nodes.
+  // Every load of a batch is issued before any loaded value is used, so a
+  // batch costs one round of memory latency; when one batch per thread covers
+  // all ghosts, between() runs while the loads are in flight, and coef is
+  // read after it (between() may set it and must make the staged operand
+  // visible block-wide).
   const int nr = 2 * by + 2 * bz;
-  const bool one_round = nr <= RB * nwarp && 2 * nrow <= XB * nthr;
+  const int nxg = xself ? 0 : 2 * nrow;  // x-face ghosts loaded from neighbours
+  const bool one_round = nr <= RB * nwarp && nxg <= XB * nthr;
   auto ghost_row = [&](int row, int& ly, int& lz) {
     if (row < 2 * by) {
       ly = row >> 1;
@@ -143,11 +162,10 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
       ly = (row & 1) ? by : -1;
     }
   };
-  auto ghosts = [&](auto two, const T* A, const T* B, const T& coef, auto&& between) {
+  auto ghosts = [&](auto two, const T* A, const T& coef, auto&& between) {
     constexpr bool TWO = decltype(two)::value;
-    constexpr int RB2 = TWO ? RB : 1, L2 = TWO ? L : 1, XB2 = TWO ? XB : 1;
     if (one_round) {
-      T va[RB][L], vb[RB2][L2], xa[XB], xb[XB2];
+      T va[RB][L], xa[XB];
       int pr[RB], xpi[XB];
 #pragma unroll
       for (int q = 0; q < RB; ++q) {
@@ -161,7 +179,6 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
 #pragma unroll
           for (int u = 0; u < L; ++u) {
             va[q][u] = __ldcg(A + g0 + lane + 32 * u);
-            if constexpr (TWO) vb[q][u] = __ldcg(B + g0 + lane + 32 * u);
           }
         }
       }
@@ -169,12 +186,11 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
       for (int q = 0; q < XB; ++q) {
         const int c = tid + q * nthr;
         xpi[q] = -1;
-        if (c < 2 * nrow) {
+        if (c < nxg) {
           const int row = c >> 1, ly = row % by, lz = row / by, lx = (c & 1) ? BX : -1;
           xpi[q] = (lz + 1) * SZ + (ly + 1) * SY + 1 + lx;
           const size_t g = gidx(lx, ly, lz);
           xa[q] = __ldcg(A + g);
-          if constexpr (TWO) xb[q] = __ldcg(B + g);
         }
       }
       between();
@@ -184,13 +200,14 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
         if (pr[q] >= 0)
 #pragma unroll
           for (int u = 0; u < L; ++u) {
-            if constexpr (TWO) P[pr[q] + lane + 32 * u] = va[q][u] + cf * vb[q][u];
-            else P[pr[q] + lane + 32 * u] = va[q][u];
+            T& d = P[pr[q] + lane + 32 * u];
+            if constexpr (TWO) d = va[q][u] + cf * d;
+            else d = va[q][u];
           }
 #pragma unroll
       for (int q = 0; q < XB; ++q)
         if (xpi[q] >= 0) {
-          if constexpr (TWO) P[xpi[q]] = xa[q] + cf * xb[q];
+          if constexpr (TWO) P[xpi[q]] = xa[q] + cf * P[xpi[q]];
           else P[xpi[q]] = xa[q];
         }
       return;
@@ -198,7 +215,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
     between();
     const T cf = coef;
     for (int r0 = warp; r0 < nr; r0 += RB * nwarp) {
-      T va[RB][L], vb[RB2][L2];
+      T va[RB][L];
       int pr[RB];
 #pragma unroll
       for (int q = 0; q < RB; ++q) {
@@ -212,7 +229,6 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
 #pragma unroll
           for (int u = 0; u < L; ++u) {
             va[q][u] = __ldcg(A + g0 + lane + 32 * u);
-            if constexpr (TWO) vb[q][u] = __ldcg(B + g0 + lane + 32 * u);
           }
         }
       }
@@ -221,34 +237,53 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
         if (pr[q] >= 0)
 #pragma unroll
           for (int u = 0; u < L; ++u) {
-            if constexpr (TWO) P[pr[q] + lane + 32 * u] = va[q][u] + cf * vb[q][u];
-            else P[pr[q] + lane + 32 * u] = va[q][u];
+            T& d = P[pr[q] + lane + 32 * u];
+            if constexpr (TWO) d = va[q][u] + cf * d;
+            else d = va[q][u];
           }
     }
-    for (int c0 = tid; c0 < 2 * nrow; c0 += XB * nthr) {
-      T xa[XB], xb[XB2];
+    for (int c0 = tid; c0 < nxg; c0 += XB * nthr) {
+      T xa[XB];
       int pi[XB];
 #pragma unroll
       for (int q = 0; q < XB; ++q) {
         const int c = c0 + q * nthr;
         pi[q] = -1;
-        if (c < 2 * nrow) {
+        if (c < nxg) {
           const int row = c >> 1, ly = row % by, lz = row / by, lx = (c & 1) ? BX : -1;
           pi[q] = (lz + 1) * SZ + (ly + 1) * SY + 1 + lx;
           const size_t g = gidx(lx, ly, lz);
           xa[q] = __ldcg(A + g);
-          if constexpr (TWO) xb[q] = __ldcg(B + g);
         }
       }
 #pragma unroll
       for (int q = 0; q < XB; ++q)
         if (pi[q] >= 0) {
-          if constexpr (TWO) P[pi[q]] = xa[q] + cf * xb[q];
+          if constexpr (TWO) P[pi[q]] = xa[q] + cf * P[pi[q]];
           else P[pi[q]] = xa[q];
         }
     }
   };
   auto nothing = [] {};
+  // stage B at every ghost node into P's ghost layer with asynchronous copies
+  // (one commit group), spread over warps w = 0 .. nw-1 of the caller's
+  // choosing; the caller waits for the group and synchronises the block
+  // before the ghosts are read
+  auto stage = [&](const T* B, int w, int nw) {
+    for (int row = w; row < nr; row += nw) {
+      int ly, lz;
+      ghost_row(row, ly, lz);
+      const int pr = (lz + 1) * SZ + (ly + 1) * SY + 1;
+      const size_t g0 = gidx(0, ly, lz);
+#pragma unroll
+      for (int u = 0; u < L; ++u) cp_async(P + pr + lane + 32 * u, B + g0 + lane + 32 * u);
+    }
+    for (int c = 32 * w + lane; c < nxg; c += 32 * nw) {
+      const int row = c >> 1, ly = row % by, lz = row / by, lx = (c & 1) ? BX : -1;
+      cp_async(P + (lz + 1) * SZ + (ly + 1) * SY + 1 + lx, B + gidx(lx, ly, lz));
+    }
+    cp_commit();
+  };
 
   GridSync gs{f.bar, f.partials, f.spin_cycles, f.expected, 0u};
   // The scalar recurrences of CG run in thread 0 (FP64 division and square
@@ -284,10 +319,10 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
     own([&](int c, int pi, size_t g, bool) {
       const T v = __ldcg(f.x + g);
       X[c] = v;
-      P[pi] = v;
+      put_p(c, pi, v);
     });
     const T one = T(1);
-    ghosts(std::false_type{}, f.x, nullptr, one, nothing);
+    ghosts(std::false_type{}, f.x, one, nothing);
     __syncthreads();
     Dot<T> a2[2];
     own([&](int c, int pi, size_t g, bool face) {
@@ -369,23 +404,29 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
   if (!status) {
     for (;;) {
       const bool first = iter == 0;
-      T* pw = (iter & 1) ? f.pg1 : f.pg0;        // this iteration's p faces
-      const T* po = (iter & 1) ? f.pg0 : f.pg1;  // the previous iteration's
+      // this iteration's p faces; the previous iteration's (the other parity)
+      // may still be in flight to a neighbour's ghost layer until the next
+      // grid sum
+      T* pw = (iter & 1) ? f.pg1 : f.pg0;
       // phase A: p = r + beta p (owned in place, ghosts from published faces
-      // as r + beta p_old).  The ghost loads are issued first; while they are
-      // in flight thread 0 closes the previous iteration (beta, status) and
-      // the block updates its owned nodes.
+      // as r + beta p_old, p_old staged in the ghost layer while the previous
+      // grid sum was in flight).  The loads of r are issued first; while they
+      // are in flight thread 0 closes the previous iteration (beta, status)
+      // and the block updates its owned nodes.
       auto update = [&] {
-        if (!first) close_iter();
+        if (!first) {
+          cp_wait<0>();  // the staged p_old; close_iter's barrier shares it
+          close_iter();
+        }
         if (status) return;
         own([&](int c, int pi, size_t g, bool face) {
           const T pv = first ? R[c] : R[c] + tb * P[pi];
-          P[pi] = pv;
+          put_p(c, pi, pv);
           if (face) __stcg(pw + g, pv);
         });
       };
-      if (first) ghosts(std::false_type{}, f.rg, nullptr, tb, update);
-      else ghosts(std::true_type{}, f.rg, po, tb, update);
+      if (first) ghosts(std::false_type{}, f.rg, tb, update);
+      else ghosts(std::true_type{}, f.rg, tb, update);
       if (status) break;  // the ghosts just written are not used
       __syncthreads();
       Dot<T> apq[1];
@@ -419,8 +460,11 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
         if (face) __stcg(f.rg + g, rv);
         ar[0].add(rv * rv);
       });
+      // while the grid sum is in flight (after this block's release), warps
+      // 1.. stage this iteration's p faces -- complete everywhere since the
+      // previous grid sum -- into the ghost layer for the next phase A
       double t[1];
-      const bool ok = grid_dot_t0<1>(ar, gs, t);
+      const bool ok = grid_dot_t0<1>(ar, gs, t, [&](int w, int nw) { stage(pw, w, nw); });
       iter += 1;
       if (tid == 0) {
         sum_ok = ok;
@@ -431,6 +475,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
       __syncthreads();
     }
   }
+  cp_wait<0>();  // no staging copy outlives the loop
   if (tid == 0 && iter > 0 && bb > 0.0) rel = sqrt(rr / bb);
 
   // zero-mean gauge (or zero for a zero right side), written back to x
@@ -488,8 +533,9 @@ bool make_plan(const Grid<T>& g, int nsm, size_t smem_max, int max_blocks, Plan&
         const size_t smem = resident_smem<T>(bx, by, bz);
         if (smem > smem_max) continue;
         const long long cells = (long long)bx * by * bz;
-        // x-face ghosts are strided single nodes: weighted as four
-        const long long ghosts = 2LL * bx * by + 2LL * bx * bz + 8LL * by * bz;
+        // x-face ghosts are strided single nodes, one 32-byte sector each:
+        // weighted as eight; a brick as wide as the grid loads none
+        const long long ghosts = 2LL * bx * by + 2LL * bx * bz + (bx == g.nx ? 0LL : 16LL * by * bz);
         const long long score = cells + ghosts + 4 * G;
         if (best_score < 0 || score < best_score) {
           best_score = score;

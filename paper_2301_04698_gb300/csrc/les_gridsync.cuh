@@ -20,6 +20,8 @@
 // ones, and the compensated pair keeps about 48 significant bits.
 #pragma once
 
+#include <type_traits>
+
 #include "les_common.cuh"
 #include "les_internal.h"
 
@@ -269,8 +271,16 @@ __device__ __forceinline__ F2 acc_load(const F2* slot) {
 }
 __device__ __forceinline__ double acc_load(const double* slot) { return __ldcg(slot); }
 
-template <int NV, typename A>
-__device__ bool grid_sum_t0(A (&v)[NV], GridSync& gs, double (&tot)[NV]) {
+struct NoWork {
+  __device__ void operator()(int, int) const {}
+};
+// work(w, nw) runs in warps 1 .. nw-1 (w = warp - 1 of nw - 1 warps) once
+// warp 0 has issued this block's release, i.e. while the grid sum is in
+// flight; it must not depend on the sum.  Memory operations it starts cannot
+// delay the release, which is why it waits for warp 0 (named barrier 1).
+template <int NV, typename A, typename W>
+__device__ bool grid_sum_t0(A (&v)[NV], GridSync& gs, double (&tot)[NV], W&& work) {
+  constexpr bool kWork = !std::is_same<std::decay_t<W>, NoWork>::value;
   __shared__ A sh[NV][32];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int lane = tid & 31, warp = tid >> 5;
@@ -292,8 +302,10 @@ __device__ bool grid_sum_t0(A (&v)[NV], GridSync& gs, double (&tot)[NV]) {
       a = acc_warp(a);
       if (lane == 0) acc_store(slot + (size_t)q * G + blockIdx.x, a);
     }
+    if (lane == 0) red_release_add(&gs.bar->count.v, 1u);
+    __syncwarp();
+    if (kWork && nw > 1) asm volatile("bar.arrive 1, %0;" ::"r"(nw * 32) : "memory");
     if (lane == 0) {
-      red_release_add(&gs.bar->count.v, 1u);
       const unsigned target = (gs.epoch + 1u) * gs.expected;
       const long long t0 = clock64();
       unsigned spins = 0;
@@ -315,9 +327,16 @@ __device__ bool grid_sum_t0(A (&v)[NV], GridSync& gs, double (&tot)[NV]) {
         if (lane == 0) tot[q] = acc_value(a);
       }
     }
+  } else if (kWork) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nw * 32) : "memory");
+    work(warp - 1, nw - 1);
   }
   gs.epoch += 1u;
   return ok;
+}
+template <int NV, typename A>
+__device__ __forceinline__ bool grid_sum_t0(A (&v)[NV], GridSync& gs, double (&tot)[NV]) {
+  return grid_sum_t0<NV>(v, gs, tot, NoWork{});
 }
 
 // one grid sum of a Dot<T> accumulator per value
@@ -335,12 +354,16 @@ __device__ __forceinline__ bool grid_dot(Dot<double> (&d)[NV], GridSync& gs, dou
   return grid_sum<NV>(tot, gs);
 }
 
-template <int NV, typename T>
-__device__ __forceinline__ bool grid_dot_t0(Dot<T> (&d)[NV], GridSync& gs, double (&tot)[NV]) {
+template <int NV, typename T, typename W>
+__device__ __forceinline__ bool grid_dot_t0(Dot<T> (&d)[NV], GridSync& gs, double (&tot)[NV], W&& work) {
   decltype(d[0].acc()) v[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) v[q] = d[q].acc();
-  return grid_sum_t0<NV>(v, gs, tot);
+  return grid_sum_t0<NV>(v, gs, tot, work);
+}
+template <int NV, typename T>
+__device__ __forceinline__ bool grid_dot_t0(Dot<T> (&d)[NV], GridSync& gs, double (&tot)[NV]) {
+  return grid_dot_t0<NV>(d, gs, tot, NoWork{});
 }
 
 }  // namespace les
