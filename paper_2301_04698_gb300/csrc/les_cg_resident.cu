@@ -4,27 +4,25 @@
 // psi returned with zero mean).
 //
 // When the whole grid fits in the GPU's shared memory (a 128 x 128 x 96 FP32
-// grid needs about 27 MB of the 34 MB on 152 SMs), every iteration of the
+// grid needs about 31 MB of the 34 MB on 152 SMs), every iteration of the
 // streaming solver is dominated by the latency of its passes through L2, not
 // by their bytes.  Here each block of one persistent cooperative launch owns
-// a brick of bx x by x bz nodes for the whole solve and keeps x, r, p and
-// q = L_c p of its brick (p with a one-node ghost layer) in shared memory.  The only
-// global traffic of an iteration is the exchange of brick faces:
-//   phase A  p = r + beta p in place; the ghost layer is filled from the
-//            neighbours' published faces of r (this iteration) and p (the
-//            previous one, double-buffered by parity) as r + beta p_old, so
-//            no barrier separates the p update from the matvec; p faces
-//            published; q = L_c p; p.q
-//   phase B  x += alpha p, r -= alpha q; r faces published; r.r
-// each followed by a grid-wide sum (les_gridsync.cuh; FP32 dot products are
-// accumulated as compensated FP32 pairs, FP64 ones in FP64).  The p_old
-// faces are copied into the ghost layer asynchronously while the second grid
-// sum is in flight, so that after it only the r faces are loaded, in one
-// batch whose latency overlaps the end of the iteration in thread 0 (beta
-// and the convergence test) and the owned update.
+// a brick of bx x by x bz nodes for the whole solve and keeps x, r, p (with a
+// one-node ghost layer), q = L_c p and r at the ghost nodes in shared memory.
+// An iteration is two passes over the brick and one grid-wide sum:
+//   matvec   q = L_c p, q faces published; p.q, r.r, r.q and q.q
+//   (grid-wide sum: alpha, and beta from |r - alpha q|^2 expanded in the
+//   four sums, so that no second sum is needed for r_{i+1}.r_{i+1})
+//   update   x += alpha p, r -= alpha q, p = r + beta p; at the ghost nodes
+//            r -= alpha q with the neighbours' published q faces, then
+//            p = r + beta p
+// The only global traffic is the exchange of q faces (double-buffered by
+// parity) and the first residual's faces.  The grid sum (les_gridsync.cuh)
+// accumulates FP32 dot products as compensated FP32 pairs, FP64 ones in
+// FP64.  Ghost loads are issued in one batch whose latency overlaps the
+// owned update.
 #include <algorithm>
 #include <string>
-#include <type_traits>
 
 #include "les_gridsync.cuh"
 #include "les_internal.h"
@@ -38,15 +36,15 @@ template <typename T>
 struct ResArgs {
   int nx, ny, nz, walls;
   T cx, cy, cz;      // 1/dx^2, 1/dy^2, 1/dz^2
-  int by, bz;        // brick extent in y and z (x extent: the template BX)
-  int px, py;        // bricks along x and y
+  int by;            // brick extent in y (x extent: the template BX)
+  int px, py, pz;    // bricks along x, y and z (z extents differ by at most one)
   long long n;
   const T* b;
   T* x;
-  T* rg;             // published faces of r
-  T* pg0;            // published faces of p, even iterations
-  T* pg1;            // ... odd iterations
-  double* partials;  // [4][gridDim.x]
+  T* rg;             // published faces of the first residual
+  T* qg0;            // published faces of q = L_c p, even iterations
+  T* qg1;            // ... odd iterations
+  double* partials;  // [2][4][gridDim.x]
   FusedBar* bar;
   SolverCtl* ctl;
   double tol;
@@ -69,21 +67,30 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
   constexpr int RB = sizeof(T) == 4 ? (L >= 4 ? 3 : 4) : (L >= 2 ? 1 : 2);
   constexpr int XB = sizeof(T) == 4 ? 4 : 2;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int by = f.by, bz = f.bz;
-  const int SY = BX + 2, SZ = (BX + 2) * (by + 2);  // strides of the haloed p brick
-  const int nrow = by * bz;
-  const int bcells = BX * nrow;
-  T* P = reinterpret_cast<T*>(smraw);  // (BX + 2)(by + 2)(bz + 2)
-  T* R = P + SZ * (bz + 2);            // BX by bz
-  T* X = R + bcells;                   // BX by bz
-  T* Q = X + bcells;                   // BX by bz: L_c p of this iteration
-  // per brick row: P offset | face bit, global offset (8-byte aligned: the
-  // T arrays above hold an even number of elements)
-  int2* ROWS = reinterpret_cast<int2*>(Q + bcells);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
   const int bi = blockIdx.x % f.px, bj = (blockIdx.x / f.px) % f.py, bk = blockIdx.x / (f.px * f.py);
-  const int i0 = bi * BX, j0 = bj * by, k0 = bk * bz;
+  // z extents: the first nz mod pz bricks hold one plane more
+  const int zbase = f.nz / f.pz, zrem = f.nz % f.pz;
+  const int by = f.by, bz = zbase + (bk < zrem ? 1 : 0);
+  const int i0 = bi * BX, j0 = bj * by, k0 = bk * zbase + min(bk, zrem);
+  const int SY = BX + 2, SZ = (BX + 2) * (by + 2);  // strides of the haloed p brick
+  const int nrow = by * bz;
+  const int bcells = BX * nrow;
+  // A brick spanning the periodic x extent is its own x neighbour: its x
+  // ghosts are copies of its own end nodes, written with them, and its x
+  // faces are not published.
+  const bool xself = f.px == 1;
+  const int nr = 2 * by + 2 * bz;          // ghost rows along x (z faces, then y faces)
+  const int nxg = xself ? 0 : 2 * nrow;    // strided x-face ghosts
+  T* P = reinterpret_cast<T*>(smraw);      // (BX + 2)(by + 2)(bz + 2): p with its ghost layer
+  T* R = P + SZ * (bz + 2);                // BX by bz
+  T* X = R + bcells;                       // BX by bz
+  T* Q = X + bcells;                       // BX by bz: L_c p of this iteration
+  T* RG = Q + bcells;                      // r at the ghost nodes: nr BX rows, then nxg x-face nodes
+  // per brick row: P offset | face bit, global offset (8-byte aligned: the
+  // T arrays above hold an even number of elements)
+  int2* ROWS = reinterpret_cast<int2*>(RG + nr * BX + nxg);
   const T cx = f.cx, cy = f.cy, cz = f.cz;
 
   // global index of local node (lx, ly, lz), at most one node outside the brick
@@ -101,20 +108,23 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
     return (P[pi - 1] + P[pi + 1] - c2) * cx + (P[pi - SY] + P[pi + SY] - c2) * cy +
            (P[pi - SZ] + P[pi + SZ] - c2) * cz;
   };
-  // A brick spanning the periodic x extent is its own x neighbour: its x
-  // ghosts are copies of its own end nodes, written with them, and its x
-  // faces are not published.
-  const bool xself = f.px == 1;
-  // body(c, pi, g, face) for every owned node: c its index in R / X, pi in P,
-  // g in global memory; face: the node lies on a brick surface that a
-  // neighbour reads
-  // the row table: row index arithmetic once per launch, not once per pass
+  // the row table: row index arithmetic once per launch, not once per pass.
+  // Surface rows come first, so that the face stores of a pass are issued
+  // early and have landed by the grid sum's release at its end.
   const size_t gbase = ((size_t)k0 * f.ny + j0) * f.nx + i0;
-  for (int row = tid; row < nrow; row += nthr) {
-    const int ly = row % by, lz = row / by;
-    const bool rface = ly == 0 || ly == by - 1 || lz == 0 || lz == bz - 1;
-    const int prow = (lz + 1) * SZ + (ly + 1) * SY + 1;
-    ROWS[row] = make_int2(prow | (rface ? (int)0x80000000u : 0), (lz * f.ny + ly) * f.nx);
+  {
+    const int by2 = max(by - 2, 0), bz2 = max(bz - 2, 0);
+    const int nface = nrow - by2 * bz2;
+    for (int row = tid; row < nrow; row += nthr) {
+      const int ly = row % by, lz = row / by;
+      const bool zin = lz >= 1 && lz <= bz - 2;
+      const bool rface = !(zin && ly >= 1 && ly <= by - 2);
+      // interior rows before this one in (ly, lz) order
+      const int before = min(max(lz - 1, 0), bz2) * by2 + (zin ? min(max(ly - 1, 0), by2) : 0);
+      const int pos = rface ? row - before : nface + before;
+      const int prow = (lz + 1) * SZ + (ly + 1) * SY + 1;
+      ROWS[pos] = make_int2(prow | (rface ? (int)0x80000000u : 0), (lz * f.ny + ly) * f.nx);
+    }
   }
   __syncthreads();
   // store p at owned node (c, pi), and at its periodic x image in the ghost
@@ -127,6 +137,9 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
       else if (lx == BX - 1) P[pi - BX] = v;
     }
   };
+  // body(c, pi, g, face) for every owned node: c its index in R / X / Q, pi in
+  // P, g in global memory; face: the node lies on a brick surface that a
+  // neighbour reads
   auto own = [&](auto&& body) {
     for (int row = warp; row < nrow; row += nwarp) {
       const int2 t = ROWS[row];
@@ -140,18 +153,12 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
       }
     }
   };
-  // fill the ghost layer of P with a, or with a + coef P where the ghost
-  // layer already holds a staged second operand (stage() below), for each
-  // face-neighbour node outside the brick (edges and corners are not used by
-  // the 7-point stencil).  Rows along x: the two z faces (2 by rows), then
-  // the two y faces (2 bz rows); the two x faces are strided single nodes.
-  // Every load of a batch is issued before any loaded value is used, so a
-  // batch costs one round of memory latency; when one batch per thread covers
-  // all ghosts, between() runs while the loads are in flight, and coef is
-  // read after it (between() may set it and must make the staged operand
-  // visible block-wide).
-  const int nr = 2 * by + 2 * bz;
-  const int nxg = xself ? 0 : 2 * nrow;  // x-face ghosts loaded from neighbours
+  // For each face-neighbour node outside the brick (edges and corners are
+  // not used by the 7-point stencil) load a = A at its global node and call
+  // put(pi, k, a) with its index pi in P and k in RG.  Every load of a batch
+  // is issued before any loaded value is used, so a batch costs one round of
+  // memory latency; when one batch per thread covers all ghosts, between()
+  // runs while the loads are in flight.
   const bool one_round = nr <= RB * nwarp && nxg <= XB * nthr;
   auto ghost_row = [&](int row, int& ly, int& lz) {
     if (row < 2 * by) {
@@ -162,8 +169,13 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
       ly = (row & 1) ? by : -1;
     }
   };
-  auto ghosts = [&](auto two, const T* A, const T& coef, auto&& between) {
-    constexpr bool TWO = decltype(two)::value;
+  auto xghost = [&](int c, int& ly, int& lz, int& lx) {
+    const int row = c >> 1;
+    ly = row % by;
+    lz = row / by;
+    lx = (c & 1) ? BX : -1;
+  };
+  auto ghosts = [&](const T* A, auto&& between, auto&& put) {
     if (one_round) {
       T va[RB][L], xa[XB];
       int pr[RB], xpi[XB];
@@ -177,9 +189,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
           pr[q] = (lz + 1) * SZ + (ly + 1) * SY + 1;
           const size_t g0 = gidx(0, ly, lz);
 #pragma unroll
-          for (int u = 0; u < L; ++u) {
-            va[q][u] = __ldcg(A + g0 + lane + 32 * u);
-          }
+          for (int u = 0; u < L; ++u) va[q][u] = __ldcg(A + g0 + lane + 32 * u);
         }
       }
 #pragma unroll
@@ -187,33 +197,24 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
         const int c = tid + q * nthr;
         xpi[q] = -1;
         if (c < nxg) {
-          const int row = c >> 1, ly = row % by, lz = row / by, lx = (c & 1) ? BX : -1;
+          int ly, lz, lx;
+          xghost(c, ly, lz, lx);
           xpi[q] = (lz + 1) * SZ + (ly + 1) * SY + 1 + lx;
-          const size_t g = gidx(lx, ly, lz);
-          xa[q] = __ldcg(A + g);
+          xa[q] = __ldcg(A + gidx(lx, ly, lz));
         }
       }
       between();
-      const T cf = coef;
 #pragma unroll
       for (int q = 0; q < RB; ++q)
         if (pr[q] >= 0)
 #pragma unroll
-          for (int u = 0; u < L; ++u) {
-            T& d = P[pr[q] + lane + 32 * u];
-            if constexpr (TWO) d = va[q][u] + cf * d;
-            else d = va[q][u];
-          }
+          for (int u = 0; u < L; ++u) put(pr[q] + lane + 32 * u, (warp + q * nwarp) * BX + lane + 32 * u, va[q][u]);
 #pragma unroll
       for (int q = 0; q < XB; ++q)
-        if (xpi[q] >= 0) {
-          if constexpr (TWO) P[xpi[q]] = xa[q] + cf * P[xpi[q]];
-          else P[xpi[q]] = xa[q];
-        }
+        if (xpi[q] >= 0) put(xpi[q], nr * BX + tid + q * nthr, xa[q]);
       return;
     }
     between();
-    const T cf = coef;
     for (int r0 = warp; r0 < nr; r0 += RB * nwarp) {
       T va[RB][L];
       int pr[RB];
@@ -227,20 +228,14 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
           pr[q] = (lz + 1) * SZ + (ly + 1) * SY + 1;
           const size_t g0 = gidx(0, ly, lz);
 #pragma unroll
-          for (int u = 0; u < L; ++u) {
-            va[q][u] = __ldcg(A + g0 + lane + 32 * u);
-          }
+          for (int u = 0; u < L; ++u) va[q][u] = __ldcg(A + g0 + lane + 32 * u);
         }
       }
 #pragma unroll
       for (int q = 0; q < RB; ++q)
         if (pr[q] >= 0)
 #pragma unroll
-          for (int u = 0; u < L; ++u) {
-            T& d = P[pr[q] + lane + 32 * u];
-            if constexpr (TWO) d = va[q][u] + cf * d;
-            else d = va[q][u];
-          }
+          for (int u = 0; u < L; ++u) put(pr[q] + lane + 32 * u, (r0 + q * nwarp) * BX + lane + 32 * u, va[q][u]);
     }
     for (int c0 = tid; c0 < nxg; c0 += XB * nthr) {
       T xa[XB];
@@ -250,40 +245,18 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
         const int c = c0 + q * nthr;
         pi[q] = -1;
         if (c < nxg) {
-          const int row = c >> 1, ly = row % by, lz = row / by, lx = (c & 1) ? BX : -1;
+          int ly, lz, lx;
+          xghost(c, ly, lz, lx);
           pi[q] = (lz + 1) * SZ + (ly + 1) * SY + 1 + lx;
-          const size_t g = gidx(lx, ly, lz);
-          xa[q] = __ldcg(A + g);
+          xa[q] = __ldcg(A + gidx(lx, ly, lz));
         }
       }
 #pragma unroll
       for (int q = 0; q < XB; ++q)
-        if (pi[q] >= 0) {
-          if constexpr (TWO) P[pi[q]] = xa[q] + cf * P[pi[q]];
-          else P[pi[q]] = xa[q];
-        }
+        if (pi[q] >= 0) put(pi[q], nr * BX + c0 + q * nthr, xa[q]);
     }
   };
   auto nothing = [] {};
-  // stage B at every ghost node into P's ghost layer with asynchronous copies
-  // (one commit group), spread over warps w = 0 .. nw-1 of the caller's
-  // choosing; the caller waits for the group and synchronises the block
-  // before the ghosts are read
-  auto stage = [&](const T* B, int w, int nw) {
-    for (int row = w; row < nr; row += nw) {
-      int ly, lz;
-      ghost_row(row, ly, lz);
-      const int pr = (lz + 1) * SZ + (ly + 1) * SY + 1;
-      const size_t g0 = gidx(0, ly, lz);
-#pragma unroll
-      for (int u = 0; u < L; ++u) cp_async(P + pr + lane + 32 * u, B + g0 + lane + 32 * u);
-    }
-    for (int c = 32 * w + lane; c < nxg; c += 32 * nw) {
-      const int row = c >> 1, ly = row % by, lz = row / by, lx = (c & 1) ? BX : -1;
-      cp_async(P + (lz + 1) * SZ + (ly + 1) * SY + 1 + lx, B + gidx(lx, ly, lz));
-    }
-    cp_commit();
-  };
 
   GridSync gs{f.bar, f.partials, f.spin_cycles, f.expected, 0u};
   // The scalar recurrences of CG run in thread 0 (FP64 division and square
@@ -293,7 +266,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
     T ta, tb, mean;
     int status, restart;
   } sc;
-  double rr = 0.0, bb = 0.0, rel = 0.0, beta = 0.0;  // meaningful in thread 0
+  double rr = 0.0, bb = 0.0, rel = 0.0;  // meaningful in thread 0
   int status = 0;  // 0 running, 1 converged, 2 maxit, 3 breakdown, 4 zero rhs, 5 timeout
   // mean of b; b staged in R
   {
@@ -321,8 +294,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
       X[c] = v;
       put_p(c, pi, v);
     });
-    const T one = T(1);
-    ghosts(std::false_type{}, f.x, one, nothing);
+    ghosts(f.x, nothing, [&](int pi, int, T v) { P[pi] = v; });
     __syncthreads();
     Dot<T> a2[2];
     own([&](int c, int pi, size_t g, bool face) {
@@ -374,109 +346,120 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
   __syncthreads();
   status = sc.status;
 
-  // convergence: |r| <= tol |b - mean| tested as r.r <= tol^2 |b - mean|^2,
-  // so that no square root sits between two iterations
-  const double rr_stop = f.tol * f.tol * bb;  // meaningful in thread 0
+  // The iterations, one grid-wide sum each.  With r = r_i, p = p_i and
+  // q = L_c p_i, the sum yields p.q, r.r, r.q and q.q; then
+  //   alpha = r.r / p.q,   |r_{i+1}|^2 = r.r - 2 alpha r.q + alpha^2 q.q,
+  //   beta = |r_{i+1}|^2 / r.r,
+  // and one pass forms x += alpha p, r_{i+1} = r - alpha q and
+  // p_{i+1} = r_{i+1} + beta p.  The neighbours' r enters through the ghost
+  // layer: each brick keeps r at its ghost nodes and updates it with the q
+  // faces its neighbours published before the sum, so no second exchange is
+  // needed.  Convergence is judged on the r.r of each sum (the residual of
+  // the current x) as r.r <= tol^2 |b - mean|^2, in the sums' precision.
+  using Acc = decltype(Dot<T>().acc());   // FP32 pair (FP32 solve) or FP64
+  Acc rr_stop, rr_last;                   // meaningful in thread 0
+  acc_from(f.tol * f.tol * bb, rr_stop);  // compared in the totals' own precision
+  acc_from(rr, rr_last);
   int iter = 0;
-  T tb = T(0);
-  double rr_new = 0.0;  // thread 0: r.r of the grid sum that closed the last iteration
-  bool sum_ok = true;   // thread 0: that grid sum completed
-  // the end of an iteration in thread 0 (beta, convergence, status),
-  // broadcast to the block
-  auto close_iter = [&] {
-    if (tid == 0) {
-      if (!sum_ok) {
-        status = 5;
-      } else {
-        beta = rr_new / rr;
-        rr = rr_new;
-        if (rr_new <= rr_stop) status = 1;
-        else if (iter >= f.maxit) status = 2;
-        else if (!isfinite(rr_new)) status = 3;
-        sc.tb = (T)beta;
-      }
-      sc.status = status;
+  // alpha and beta from the totals (p.q, r.r, r.q, q.q); false on a zero or
+  // non-finite p.q or r.r.  An FP32 solve takes them in FP32 from the high
+  // parts of the compensated totals: those carry the dot products' own
+  // precision, and the chain of FP64 operations through one thread would
+  // cost about a microsecond per iteration on this GPU.
+  auto scalars = [&](const auto(&t)[4], T& ta, T& tb) -> bool {
+    if constexpr (sizeof(T) == 4) {
+      const float pq = t[0].hi, r2 = t[1].hi, rq = t[2].hi, q2 = t[3].hi;
+      if (!(pq != 0.f) || !isfinite(pq) || !isfinite(r2)) return false;
+      const float alpha = r2 / pq;
+      const float rn = fmaf(alpha * alpha, q2, fmaf(-2.f * alpha, rq, r2));  // |r - alpha q|^2
+      ta = alpha;
+      tb = rn / r2;
+    } else {
+      const double pq = t[0], r2 = t[1], rq = t[2], q2 = t[3];
+      if (!(pq != 0.0) || !isfinite(pq) || !isfinite(r2)) return false;
+      const double inv = 1.0 / (r2 * pq);  // one FP64 division for both
+      const double alpha = r2 * r2 * inv;
+      const double rn = fma(alpha * alpha, q2, fma(-2.0 * alpha, rq, r2));
+      ta = alpha;
+      tb = rn * (pq * inv);
     }
-    __syncthreads();
-    status = sc.status;
-    tb = sc.tb;
+    return true;
   };
   if (!status) {
-    for (;;) {
-      const bool first = iter == 0;
-      // this iteration's p faces; the previous iteration's (the other parity)
-      // may still be in flight to a neighbour's ghost layer until the next
-      // grid sum
-      T* pw = (iter & 1) ? f.pg1 : f.pg0;
-      // phase A: p = r + beta p (owned in place, ghosts from published faces
-      // as r + beta p_old, p_old staged in the ghost layer while the previous
-      // grid sum was in flight).  The loads of r are issued first; while they
-      // are in flight thread 0 closes the previous iteration (beta, status)
-      // and the block updates its owned nodes.
-      auto update = [&] {
-        if (!first) {
-          cp_wait<0>();  // the staged p_old; close_iter's barrier shares it
-          close_iter();
-        }
-        if (status) return;
-        own([&](int c, int pi, size_t g, bool face) {
-          const T pv = first ? R[c] : R[c] + tb * P[pi];
-          put_p(c, pi, pv);
-          if (face) __stcg(pw + g, pv);
+    // p_0 = r_0 with the ghosts of r_0
+    ghosts(
+        f.rg,
+        [&] { own([&](int c, int pi, size_t, bool) { put_p(c, pi, R[c]); }); },
+        [&](int pi, int k, T v) {
+          RG[k] = v;
+          P[pi] = v;
         });
-      };
-      if (first) ghosts(std::false_type{}, f.rg, tb, update);
-      else ghosts(std::true_type{}, f.rg, tb, update);
-      if (status) break;  // the ghosts just written are not used
-      __syncthreads();
-      Dot<T> apq[1];
-      own([&](int c, int pi, size_t, bool) {
-        const T qv = Lc(pi);
-        Q[c] = qv;
-        apq[0].add(P[pi] * qv);
-      });
-      {
-        double t[1];
-        const bool ok = grid_dot_t0<1>(apq, gs, t);
-        if (tid == 0) {
-          const double pq = t[0];
-          if (!ok) status = 5;
-          else if (pq == 0.0 || !isfinite(pq)) status = 3;
-          else sc.ta = (T)(rr / pq);
-          sc.status = status;
-        }
-        __syncthreads();
-        status = sc.status;
-        if (status) break;
-      }
-      const T ta = sc.ta;
-      // phase B: x += alpha p, r -= alpha q, r faces published, r.r
-      Dot<T> ar[1];
+    __syncthreads();
+    for (;;) {
+      T* qw = (iter & 1) ? f.qg1 : f.qg0;  // this iteration's q faces
+      Dot<T> d[4];                         // p.q, r.r, r.q, q.q
       own([&](int c, int pi, size_t g, bool face) {
-        const T pv = P[pi];
-        X[c] += ta * pv;
-        const T rv = R[c] - ta * Q[c];
-        R[c] = rv;
-        if (face) __stcg(f.rg + g, rv);
-        ar[0].add(rv * rv);
+        const T qv = Lc(pi);
+        const T rv = R[c];
+        Q[c] = qv;
+        if (face) __stcg(qw + g, qv);
+        d[0].add(P[pi] * qv);
+        d[1].add(rv * rv);
+        d[2].add(rv * qv);
+        d[3].add(qv * qv);
       });
-      // while the grid sum is in flight (after this block's release), warps
-      // 1.. stage this iteration's p faces -- complete everywhere since the
-      // previous grid sum -- into the ghost layer for the next phase A
-      double t[1];
-      const bool ok = grid_dot_t0<1>(ar, gs, t, [&](int w, int nw) { stage(pw, w, nw); });
+      Acc v[4], t[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = d[q].acc();
+      const bool ok = grid_sum_t0_acc<4>(v, gs, t, NoWork{});
+      // the sum has completed (or timed out): from here every thread may read
+      // the q faces the other blocks published before it
+      __syncthreads();
+      // the update pass.  The loads of the neighbours' q faces are issued
+      // first; while they are in flight thread 0 forms alpha, beta and the
+      // status, then the owned nodes are updated.
+      T ta = T(0), tb = T(0);
+      ghosts(
+          qw,
+          [&] {
+            if (tid == 0) {
+              if (!ok) {
+                status = 5;
+              } else {
+                rr_last = t[1];
+                if (acc_le(t[1], rr_stop)) status = 1;
+                else if (iter >= f.maxit) status = 2;
+                else if (!scalars(t, sc.ta, sc.tb)) status = 3;
+              }
+              sc.status = status;
+            }
+            __syncthreads();
+            status = sc.status;
+            if (status) return;
+            ta = sc.ta;
+            tb = sc.tb;
+            own([&](int c, int pi, size_t, bool) {
+              const T pv = P[pi];
+              X[c] += ta * pv;
+              const T rv = R[c] - ta * Q[c];
+              R[c] = rv;
+              put_p(c, pi, rv + tb * pv);
+            });
+          },
+          [&](int pi, int k, T qv) {
+            const T rv = RG[k] - ta * qv;
+            RG[k] = rv;
+            P[pi] = rv + tb * P[pi];
+          });
+      if (status) break;  // the ghosts just written are not used
       iter += 1;
-      if (tid == 0) {
-        sum_ok = ok;
-        rr_new = t[0];
-      }
-      // the grid sum has completed (or timed out, which close_iter reports):
-      // from here every thread may read the faces the other blocks published
       __syncthreads();
     }
   }
-  cp_wait<0>();  // no staging copy outlives the loop
-  if (tid == 0 && iter > 0 && bb > 0.0) rel = sqrt(rr / bb);
+  if (tid == 0 && iter > 0 && bb > 0.0) {
+    rr = acc_value(rr_last);
+    rel = sqrt(rr / bb);
+  }
 
   // zero-mean gauge (or zero for a zero right side), written back to x
   if (status != 5) {
@@ -504,38 +487,42 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
 }
 
 struct Plan {
-  int bx = 0, by = 0, bz = 0, px = 0, py = 0, pz = 0;
+  int bx = 0, by = 0, bz = 0, px = 0, py = 0, pz = 0;  // bz: the largest brick extent in z
   size_t smem = 0;
 };
 
 template <typename T>
-size_t resident_smem(int bx, int by, int bz) {
-  return ((size_t)(bx + 2) * (by + 2) * (bz + 2) + 3 * (size_t)bx * by * bz) * sizeof(T) +
+size_t resident_smem(int bx, int by, int bz, bool xself) {
+  const size_t ghosts = (size_t)(2 * by + 2 * bz) * bx + (xself ? 0 : 2 * (size_t)by * bz);
+  return ((size_t)(bx + 2) * (by + 2) * (bz + 2) + 3 * (size_t)bx * by * bz + ghosts) * sizeof(T) +
          (size_t)by * bz * sizeof(int2);
 }
 
-// Brick decomposition: bx in {128, 64, 32} dividing nx, by | ny, bz | nz,
-// at most one brick per SM and within the per-block shared memory; among
-// those the one with the least work per block (owned nodes + ghost nodes +
-// a per-block barrier cost).
+// Brick decomposition: bx in {128, 64, 32} dividing nx, by | ny, pz bricks
+// along z of nz / pz planes (rounded up or down), at most one brick per SM and
+// within the per-block shared memory; among those the one with the least
+// work for its largest brick (owned nodes + ghost nodes + a per-block
+// barrier cost).
 template <typename T>
 bool make_plan(const Grid<T>& g, int nsm, size_t smem_max, int max_blocks, Plan& best) {
   long long best_score = -1;
   const int gmax = std::min(nsm, max_blocks);
   for (int bx : {128, 64, 32}) {
     if (g.nx % bx) continue;
+    const bool xself = bx == g.nx;
     for (int by = 1; by <= g.ny; ++by) {
       if (g.ny % by) continue;
-      for (int bz = 1; bz <= g.nz; ++bz) {
-        if (g.nz % bz) continue;
-        const long long G = (long long)(g.nx / bx) * (g.ny / by) * (g.nz / bz);
-        if (G > gmax) continue;
-        const size_t smem = resident_smem<T>(bx, by, bz);
+      for (int pz = 1; pz <= g.nz; ++pz) {
+        const int bz = (g.nz + pz - 1) / pz;
+        if (pz > 1 && (g.nz + pz - 2) / (pz - 1) == bz) continue;  // as large, with more bricks
+        const long long G = (long long)(g.nx / bx) * (g.ny / by) * pz;
+        if (G > gmax) break;
+        const size_t smem = resident_smem<T>(bx, by, bz, xself);
         if (smem > smem_max) continue;
         const long long cells = (long long)bx * by * bz;
         // x-face ghosts are strided single nodes, one 32-byte sector each:
         // weighted as eight; a brick as wide as the grid loads none
-        const long long ghosts = 2LL * bx * by + 2LL * bx * bz + (bx == g.nx ? 0LL : 16LL * by * bz);
+        const long long ghosts = 2LL * bx * by + 2LL * bx * bz + (xself ? 0LL : 16LL * by * bz);
         const long long score = cells + ghosts + 4 * G;
         if (best_score < 0 || score < best_score) {
           best_score = score;
@@ -544,7 +531,7 @@ bool make_plan(const Grid<T>& g, int nsm, size_t smem_max, int max_blocks, Plan&
           best.bz = bz;
           best.px = g.nx / bx;
           best.py = g.ny / by;
-          best.pz = g.nz / bz;
+          best.pz = pz;
           best.smem = smem;
         }
       }
@@ -580,8 +567,8 @@ int poisson_solve_resident(const SolverArgs<T>& a, const FusedCfg& fc, const T* 
     return LES_ERR_CUDA;
   }
   Plan pl;
-  // leave room for the reductions' static shared memory (about 1 KB)
-  if (!make_plan(a.g, nsm, (size_t)std::max(0, smem_optin - 2048), fc.max_blocks, pl)) return LES_OK;
+  // leave room for the reductions' static shared memory (about 2 KB)
+  if (!make_plan(a.g, nsm, (size_t)std::max(0, smem_optin - 3072), fc.max_blocks, pl)) return LES_OK;
   const void* kern = resident_kernel<T>(pl.bx);
   int per_sm = 0;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem)) != cudaSuccess ||
@@ -600,15 +587,15 @@ int poisson_solve_resident(const SolverArgs<T>& a, const FusedCfg& fc, const T* 
   f.cy = a.g.idy * a.g.idy;
   f.cz = a.g.idz * a.g.idz;
   f.by = pl.by;
-  f.bz = pl.bz;
   f.px = pl.px;
   f.py = pl.py;
+  f.pz = pl.pz;
   f.n = (long long)f.nx * f.ny * f.nz;
   f.b = b;
   f.x = x;
   f.rg = a.r;
-  f.pg0 = a.p0;
-  f.pg1 = a.p1;
+  f.qg0 = a.p0;
+  f.qg1 = a.p1;
   f.partials = a.partials;
   f.bar = a.bar;
   f.ctl = a.ctl;

@@ -108,7 +108,7 @@ __device__ __forceinline__ bool grid_long_t0(LongSum<T> (&d)[NV], GridSync& gs, 
     d[q].flush();
     v[q] = d[q].acc();
   }
-  return grid_sum_t0<NV>(v, gs, tot);
+  return grid_sum_t0<NV, 2>(v, gs, tot);  // two partials per lane in flight: within 80 registers
 }
 
 template <typename T>

@@ -261,6 +261,16 @@ __device__ __forceinline__ F2 acc_zero(F2) { return F2{0.f, 0.f}; }
 __device__ __forceinline__ double acc_zero(double) { return 0.0; }
 __device__ __forceinline__ double acc_value(F2 a) { return f2_value(a); }
 __device__ __forceinline__ double acc_value(double a) { return a; }
+// a <= b without leaving the accumulator's precision (normalised pairs:
+// |lo| <= ulp(hi) / 2, so the high parts decide unless they are equal)
+__device__ __forceinline__ bool acc_le(F2 a, F2 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+__device__ __forceinline__ bool acc_le(double a, double b) { return a <= b; }
+// an FP64 value as an accumulator: a normalised FP32 pair, or itself
+__device__ __forceinline__ void acc_from(double x, F2& a) {
+  a.hi = (float)x;
+  a.lo = (float)(x - (double)a.hi);
+}
+__device__ __forceinline__ void acc_from(double x, double& a) { a = x; }
 __device__ __forceinline__ void acc_store(F2* slot, F2 a) {
   *reinterpret_cast<float2*>(slot) = make_float2(a.hi, a.lo);
 }
@@ -278,8 +288,10 @@ struct NoWork {
 // warp 0 has issued this block's release, i.e. while the grid sum is in
 // flight; it must not depend on the sum.  Memory operations it starts cannot
 // delay the release, which is why it waits for warp 0 (named barrier 1).
-template <int NV, typename A, typename W>
-__device__ bool grid_sum_t0(A (&v)[NV], GridSync& gs, double (&tot)[NV], W&& work) {
+// U: partials per lane and sum loaded together when folding.  The totals
+// come back as accumulators (an FP32 pair or an FP64 value) in thread 0.
+template <int NV, int U = 5, typename A, typename W>
+__device__ bool grid_sum_t0_acc(A (&v)[NV], GridSync& gs, A (&tot)[NV], W&& work) {
   constexpr bool kWork = !std::is_same<std::decay_t<W>, NoWork>::value;
   __shared__ A sh[NV][32];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
@@ -319,12 +331,28 @@ __device__ bool grid_sum_t0(A (&v)[NV], GridSync& gs, double (&tot)[NV], W&& wor
     }
     ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
     if (ok) {
+      // the partials of all NV sums, U per lane and sum in flight at once
+      // (a fold that waited for each load would pay one memory round trip
+      // per 32 blocks and sum)
+      A a[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) a[q] = acc_zero(v[q]);
+      for (unsigned b0 = lane; b0 < G; b0 += 32 * U) {
+        A w[NV][U];
+#pragma unroll
+        for (int q = 0; q < NV; ++q)
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            w[q][u] = b0 + 32 * u < G ? acc_load(slot + (size_t)q * G + b0 + 32 * u) : acc_zero(v[q]);
+#pragma unroll
+        for (int q = 0; q < NV; ++q)
+#pragma unroll
+          for (int u = 0; u < U; ++u) a[q] = acc_add(a[q], w[q][u]);
+      }
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
-        A a = acc_zero(v[q]);
-        for (unsigned b = lane; b < G; b += 32) a = acc_add(a, acc_load(slot + (size_t)q * G + b));
-        a = acc_warp(a);
-        if (lane == 0) tot[q] = acc_value(a);
+        const A t = acc_warp(a[q]);
+        if (lane == 0) tot[q] = t;
       }
     }
   } else if (kWork) {
@@ -334,9 +362,18 @@ __device__ bool grid_sum_t0(A (&v)[NV], GridSync& gs, double (&tot)[NV], W&& wor
   gs.epoch += 1u;
   return ok;
 }
-template <int NV, typename A>
+template <int NV, int U = 5, typename A, typename W>
+__device__ __forceinline__ bool grid_sum_t0(A (&v)[NV], GridSync& gs, double (&tot)[NV], W&& work) {
+  A t[NV];
+  const bool ok = grid_sum_t0_acc<NV, U>(v, gs, t, work);
+  if (threadIdx.x + blockDim.x * threadIdx.y == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] = acc_value(t[q]);
+  return ok;
+}
+template <int NV, int U = 5, typename A>
 __device__ __forceinline__ bool grid_sum_t0(A (&v)[NV], GridSync& gs, double (&tot)[NV]) {
-  return grid_sum_t0<NV>(v, gs, tot, NoWork{});
+  return grid_sum_t0<NV, U>(v, gs, tot, NoWork{});
 }
 
 // one grid sum of a Dot<T> accumulator per value
