@@ -153,6 +153,17 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
       }
     }
   };
+  // body(c0, prow, grow, rface) for every owned row: the row's nodes are
+  // c0 + lx in R / X / Q, prow + lx in P and grow + lx in global memory.  The
+  // passes of the iteration handle a row's L nodes per lane together, with
+  // every shared-memory load issued before the first store (the compiler
+  // cannot reorder them across stores to the other arrays of the block).
+  auto own_rows = [&](auto&& body) {
+    for (int row = warp; row < nrow; row += nwarp) {
+      const int2 t = ROWS[row];
+      body(row * BX, t.x & 0x7fffffff, gbase + (unsigned)t.y, t.x < 0);
+    }
+  };
   // For each face-neighbour node outside the brick (edges and corners are
   // not used by the 7-point stencil) load a = A at its global node and call
   // put(pi, k, a) with its index pi in P and k in RG.  Every load of a batch
@@ -398,15 +409,32 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
     for (;;) {
       T* qw = (iter & 1) ? f.qg1 : f.qg0;  // this iteration's q faces
       Dot<T> d[4];                         // p.q, r.r, r.q, q.q
-      own([&](int c, int pi, size_t g, bool face) {
-        const T qv = Lc(pi);
-        const T rv = R[c];
-        Q[c] = qv;
-        if (face) __stcg(qw + g, qv);
-        d[0].add(P[pi] * qv);
-        d[1].add(rv * rv);
-        d[2].add(rv * qv);
-        d[3].add(qv * qv);
+      own_rows([&](int c0, int prow, size_t grow, bool rface) {
+        T pc[L], pw[L], pe[L], ps[L], pn[L], pd[L], pu[L], rv[L];
+#pragma unroll
+        for (int u = 0; u < L; ++u) {
+          const int pi = prow + lane + 32 * u;
+          pc[u] = P[pi];
+          pw[u] = P[pi - 1];
+          pe[u] = P[pi + 1];
+          ps[u] = P[pi - SY];
+          pn[u] = P[pi + SY];
+          pd[u] = P[pi - SZ];
+          pu[u] = P[pi + SZ];
+          rv[u] = R[c0 + lane + 32 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < L; ++u) {
+          const int lx = lane + 32 * u;
+          const T c2 = T(2) * pc[u];
+          const T qv = (pw[u] + pe[u] - c2) * cx + (ps[u] + pn[u] - c2) * cy + (pd[u] + pu[u] - c2) * cz;
+          Q[c0 + lx] = qv;
+          if (rface || (!xself && (lx == 0 || lx == BX - 1))) __stcg(qw + grow + lx, qv);
+          d[0].add(pc[u] * qv);
+          d[1].add(rv[u] * rv[u]);
+          d[2].add(rv[u] * qv);
+          d[3].add(qv * qv);
+        }
       });
       Acc v[4], t[4];
 #pragma unroll
@@ -438,12 +466,24 @@ __global__ void __launch_bounds__(kResThreads, 1) k_cg_resident(ResArgs<T> f) {
             if (status) return;
             ta = sc.ta;
             tb = sc.tb;
-            own([&](int c, int pi, size_t, bool) {
-              const T pv = P[pi];
-              X[c] += ta * pv;
-              const T rv = R[c] - ta * Q[c];
-              R[c] = rv;
-              put_p(c, pi, rv + tb * pv);
+            own_rows([&](int c0, int prow, size_t, bool) {
+              T pv[L], xv[L], rv[L], qv[L];
+#pragma unroll
+              for (int u = 0; u < L; ++u) {
+                const int lx = lane + 32 * u;
+                pv[u] = P[prow + lx];
+                xv[u] = X[c0 + lx];
+                rv[u] = R[c0 + lx];
+                qv[u] = Q[c0 + lx];
+              }
+#pragma unroll
+              for (int u = 0; u < L; ++u) {
+                const int lx = lane + 32 * u;
+                X[c0 + lx] = xv[u] + ta * pv[u];
+                const T r1 = rv[u] - ta * qv[u];
+                R[c0 + lx] = r1;
+                put_p(c0 + lx, prow + lx, r1 + tb * pv[u]);
+              }
             });
           },
           [&](int pi, int k, T qv) {
