@@ -160,6 +160,50 @@ def cbl(nx: int = 128, ny: int = 128, nz: int = 96, dx: float = 35.0, dz: float 
     return c.replace(**kw) if kw else c
 
 
+def density_current(dx: float = 200.0, ny: int = 4, precision: int = 64, **kw) -> Case:
+    """Dry negatively buoyant bubble impinging on the surface (Sec. 3,
+    density current): a -15 K perturbation of radii 4 km (horizontal) and
+    2 km (vertical) in a uniform 300 K potential temperature, 51.2 km x 6.4
+    km, periodic in x, uniform kinematic viscosity 10 m^2/s.  Two-dimensional
+    as a thin periodic y extent with y-independent fields.  Readings (the
+    paper does not state them): centre at mid-domain, 3 km up; cosine-squared
+    bell; scalar diffusivity equal to the viscosity; the walls of the solver
+    (free-slip surface, no-slip lid); a fixed step of dx / 200 s."""
+    nx, nz = int(round(51200.0 / dx)), int(round(6400.0 / dx))
+    c = Case(name=f"density_current{dx:g}m", nx=nx, ny=ny, nz=nz, dx=dx, dy=dx, dz=dx, walls=True,
+             precision=precision, dt=dx / 200.0, K=3, tol=1e-10 if precision == 64 else 1e-6,
+             maxit=20000, physics=("adv", "const_nu", "buoy"), nu_const=10.0, pr=1.0, sc=1.0,
+             theta0=300.0, init="bubble",
+             init_args={"theta": 300.0, "amp": -15.0, "xc": 25600.0, "zc": 3000.0, "xr": 4000.0, "zr": 2000.0})
+    return c.replace(**kw) if kw else c
+
+
+def rising_bubble(dx: float = 200.0, ny: int = 4, precision: int = 64, **kw) -> Case:
+    """Dry warm bubble (Sec. 3, rising bubble): a +2 K perturbation in a
+    uniform 300 K potential temperature, 20 km x 10 km, periodic in x,
+    uniform kinematic viscosity 1 m^2/s.  Readings: radius 2 km, centre at
+    mid-domain, 2 km up; cosine-squared bell; otherwise as the density
+    current."""
+    nx, nz = int(round(20000.0 / dx)), int(round(10000.0 / dx))
+    c = Case(name=f"rising_bubble{dx:g}m", nx=nx, ny=ny, nz=nz, dx=dx, dy=dx, dz=dx, walls=True,
+             precision=precision, dt=dx / 200.0, K=3, tol=1e-10 if precision == 64 else 1e-6,
+             maxit=20000, physics=("adv", "const_nu", "buoy"), nu_const=1.0, pr=1.0, sc=1.0,
+             theta0=300.0, init="bubble",
+             init_args={"theta": 300.0, "amp": 2.0, "xc": 10000.0, "zc": 2000.0, "xr": 2000.0, "zr": 2000.0})
+    return c.replace(**kw) if kw else c
+
+
+def bubble_perturbation(case: Case) -> np.ndarray:
+    """theta' of a bubble case on the nodes, (nz, ny, nx): amp cos^2(pi L / 2)
+    for L <= 1, L the distance from the centre in units of the radii."""
+    a = case.init_args
+    x = (np.arange(case.nx) + 0.5) * case.dx
+    z = (np.arange(case.nz) + 0.5) * case.dz
+    L = np.sqrt(((x[None, :] - a["xc"]) / a["xr"]) ** 2 + ((z[:, None] - a["zc"]) / a["zr"]) ** 2)
+    th = np.where(L <= 1.0, a["amp"] * np.cos(0.5 * np.pi * np.minimum(L, 1.0)) ** 2, 0.0)
+    return np.broadcast_to(th[:, None, :], case.shape).copy()
+
+
 # ----------------------------------------------------------------------------
 # initial fields
 
@@ -208,6 +252,10 @@ def initial_state(case: Case) -> dict:
         out["u"] = np.full(case.shape, case.ug)
         out["v"] = np.full(case.shape, case.vg)
         out["w"] = np.zeros(case.shape)
+    elif case.init == "bubble":
+        out["theta_l"] = case.init_args["theta"] + bubble_perturbation(case)
+        for k in ("u", "v", "w", "q_t"):
+            out[k] = np.zeros(case.shape)
     elif case.init == "zero":
         for k in ("u", "v", "w", "theta_l", "q_t"):
             out[k] = np.zeros(case.shape)
