@@ -645,13 +645,12 @@ int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, 
   const SolverCtl& c = *a.ctl_host;
   if (iters) *iters = c.iter;
   if (rel) *rel = c.rel;
-  // algorithmic traffic of the solve, each field touched once per pass:
-  // mean of b (1), r = b - L_c x0 (b, x in, r out: 3), per iteration phase A
-  // (r, p_old in, p, q out: 4) + phase B (x, p, r, q in, x, r out: 6), and
-  // the gauge (x twice in, x out: 3)
-  // (Chronopoulos-Gear: the same 10 fields per iteration -- r, w, s, p, x in;
-  // p, s, x, r, w out -- plus one more sweep, w0 = A r0, in the prologue)
-  if (a.prof) a.prof->bytes[KI_CG_FUSED] += ((cgg ? 9.0 : 7.0) + 10.0 * c.iter) * (double)f.n * sizeof(T);
+  // algorithmic traffic of the solve (kCgIterFields per iteration; this
+  // kernel streams 10: phase A r, p_old in, p, q out; phase B x, p, r, q in,
+  // x, r out; Chronopoulos-Gear adds one prologue sweep, w0 = A r0)
+  if (a.prof)
+    a.prof->bytes[KI_CG_FUSED] +=
+        (kCgSetupFields + (cgg ? 2.0 : 0.0) + kCgIterFields * c.iter) * (double)f.n * sizeof(T);
   switch (c.done) {
     case 1:
     case 4: return LES_OK;

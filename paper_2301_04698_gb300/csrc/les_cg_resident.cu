@@ -666,9 +666,10 @@ int poisson_solve_resident(const SolverArgs<T>& a, const FusedCfg& fc, const T* 
   const SolverCtl& c = *a.ctl_host;
   if (iters) *iters = c.iter;
   if (rel) *rel = c.rel;
-  // algorithmic traffic of the same CG written as streaming passes (as for
-  // the streaming solver), so that the two report comparable rates
-  if (a.prof) a.prof->bytes[KI_CG_RESIDENT] += (7.0 + 10.0 * c.iter) * (double)f.n * sizeof(T);
+  // algorithmic traffic of the solve (kCgIterFields per iteration), so that
+  // every CG kernel reports a comparable rate; this one keeps its vectors
+  // on chip and moves only b, x and the brick faces through DRAM
+  if (a.prof) a.prof->bytes[KI_CG_RESIDENT] += (kCgSetupFields + kCgIterFields * c.iter) * (double)f.n * sizeof(T);
   switch (c.done) {
     case 1:
     case 4: return LES_OK;

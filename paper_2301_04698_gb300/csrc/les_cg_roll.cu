@@ -498,10 +498,10 @@ int poisson_solve_roll(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T
   const SolverCtl& c = *a.ctl_host;
   if (iters) *iters = c.iter;
   if (rel) *rel = c.rel;
-  // algorithmic traffic, each field touched once per pass: mean of b (1),
-  // r_0 (b, x in, r out: 3), alpha_0 (r: 1), per iteration (r, p_old, x in;
-  // p, r, x out: 6), gauge (x twice in, x out: 3)
-  if (a.prof) a.prof->bytes[KI_CG_ROLL] += (8.0 + 6.0 * c.iter) * (double)f.n * sizeof(T);
+  // algorithmic traffic of the solve (kCgIterFields per iteration; this
+  // kernel streams 6: r, p_old, x in; p, r, x out; plus one set-up sweep
+  // for alpha_0)
+  if (a.prof) a.prof->bytes[KI_CG_ROLL] += (kCgSetupFields + 1.0 + kCgIterFields * c.iter) * (double)f.n * sizeof(T);
   switch (c.done) {
     case 1:
     case 4: return LES_OK;

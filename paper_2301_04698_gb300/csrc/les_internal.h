@@ -48,6 +48,14 @@ struct Phys {
 };
 
 // Device-side solver control block (lives in the workspace).
+// Algorithmic traffic of a CG solve in fields per node, the same for every
+// CG kernel whatever it moves: the set-up (mean of b: 1; r = b - L_c x0:
+// b, x in, r out: 3; the gauge: x twice in, x out: 3) and, per iteration,
+// the matvec with its dot product (p in, q out: 2) and the update (x, p, r,
+// q in; x, r out: 6).  A kernel's DRAM traffic is measured separately.
+constexpr double kCgSetupFields = 7.0;
+constexpr double kCgIterFields = 8.0;
+
 struct SolverCtl {
   double sum;       // result of the last mean reduction
   double bn2;       // ||b - mean(b)||^2
