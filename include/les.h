@@ -307,18 +307,23 @@ typedef struct les_tuning {
   int32_t  cg_variant;             /* persistent CG: 0 (default) the
                                       standard CG iterates -- in shared
                                       memory when the grid fits there (see
-                                      cg_resident), else variant 2 on
-                                      tile-aligned grids, else variant 3;
+                                      cg_resident), else variant 4 for
+                                      FP32 grids of whole 64 x 16 columns,
+                                      else variant 2 on tile-aligned grids,
+                                      else variant 3;
                                       1 Chronopoulos-Gear (one barrier; its
                                       vector recurrences drift in FP32 and
                                       may need more iterations); 2 the
                                       two-phase streaming CG (two barriers
                                       per iteration); 3 one pass over memory
                                       and one grid reduction per iteration,
-                                      any grid.  1 and 2 need nx a multiple
-                                      of 128 (FP32) / 64 (FP64) and ny of
-                                      cg_tile_rows, else the per-phase
-                                      launches run                         */
+                                      any grid; 4 the same in 64 x 16
+                                      columns with the z neighbours in
+                                      registers (nx a multiple of 64, ny of
+                                      16, else as 3).  1 and 2 need nx a
+                                      multiple of 128 (FP32) / 64 (FP64)
+                                      and ny of cg_tile_rows, else the
+                                      per-phase launches run               */
   int32_t  cg_resident;            /* 0 (default): standard CG keeps its
                                       vectors in shared memory when the grid
                                       fits there; 1: always streams them

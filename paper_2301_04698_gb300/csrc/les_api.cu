@@ -482,7 +482,7 @@ namespace les {
 const char* const kKernelNames[KI_COUNT] = {
     "thermo", "radiation", "nu", "nu_half", "scalar", "momentum", "rhs", "correct", "diag",
     "cfl", "apply", "sum", "cg_init", "cg_matvec", "cg_update", "jacobi", "finish", "ctl", "cg_fused",
-    "unet_conv", "unet_wgrad", "unet_adam", "cg_resident", "cg_roll"};
+    "unet_conv", "unet_wgrad", "unet_adam", "cg_resident", "cg_roll", "cg_wave"};
 
 template <typename T>
 Grid<T> make_grid(const les_config& c, int zc) {
@@ -821,8 +821,8 @@ int les_set_tuning(les_handle* h, const les_tuning* in) {
   if (in->stencil_path < 0 || in->stencil_path > 2)
     return h->fail(LES_ERR_INVALID_ARG, "stencil_path must be 0, 1 or 2");
   h->fused.stencil_path = in->stencil_path;
-  if (in->cg_variant < 0 || in->cg_variant > 3)
-    return h->fail(LES_ERR_INVALID_ARG, "cg_variant must be 0, 1, 2 or 3");
+  if (in->cg_variant < 0 || in->cg_variant > 4)
+    return h->fail(LES_ERR_INVALID_ARG, "cg_variant must be 0, 1, 2, 3 or 4");
   h->fused.variant = in->cg_variant;
   if (in->cg_resident != 0 && in->cg_resident != 1) return h->fail(LES_ERR_INVALID_ARG, "cg_resident must be 0 or 1");
   h->fused.resident = in->cg_resident;

@@ -1,0 +1,572 @@
+// les_cg_wave.cu -- conjugate-gradient Poisson solve in one persistent
+// cooperative launch with one pass over memory and one grid-wide sum per
+// iteration, for grids whose horizontal extents are multiples of 64 x 16
+// (Sec. 2.4: L_c psi = b, compact 7-point Laplacian, periodic in x, y,
+// mirror or periodic in z; mean of b removed, psi returned with zero mean).
+//
+// The iterates are those of standard CG, formed as in the one-pass kernel of
+// les_cg_roll.cu: with alpha_i and beta_i known, iteration i forms
+//   p_i = r_i + beta_i p_{i-1},  q_i = L_c p_i,  x += alpha_i p_i,
+//   r_{i+1} = r_i - alpha_i q_i,  w = L_c r_{i+1},
+// and r'.r', r'.w, r'.q, p.q (r' = r_{i+1}) in one grid-wide sum; then
+// alpha_{i+1} = r'.r' / (r'.w + 2 beta r'.q + beta^2 p.q) and
+// beta_{i+1} = r'.r' / r_i.r_i (p_{i+1}.L_c p_{i+1} expanded with L_c
+// symmetric), every vector formed from its definition.
+//
+// A block of 256 threads owns a 64 x 16 column and marches a run of planes.
+// Each thread holds fixed positions of the column's plane with its halo of
+// two (68 x 20 positions: four owned nodes and two of the halo ring per
+// thread) for the whole run, so the z neighbours of both stencils are
+// registers: per position p on the planes
+// f-2 .. f, r' on f-3 .. f-1 and r_i on f-1 .. f, where f is the plane that
+// enters the march.  Only in-plane neighbours pass through shared memory
+// (one plane of p and one of r', each double-buffered by plane parity); the
+// planes of r_i and p_{i-1} (halo two) and of x (owned nodes) arrive through
+// rings that cp.async fills three planes ahead.  Per plane step, after one
+// block barrier:
+//   A  p(f) = r(f) + beta p_old(f) at every position
+//   B  q(f-1) = L_c p, r'(f-1) = r(f-1) - alpha q(f-1) within the halo of one
+//   C  w(f-2) = L_c r' at the owned positions
+//   D  x += alpha p, and p, r' of plane f-2 stored
+// r and p are double-buffered by iteration parity (the pass reads the
+// neighbours' r_i while writing r_{i+1}); the grid sum is the barrier
+// between passes.  Per iteration each node is read three times (r_i,
+// p_{i-1}, x) and written three times (p_i, r_{i+1}, x); the halo re-reads a
+// third of r_i and p_{i-1}, mostly from L2.
+#include <algorithm>
+#include <string>
+
+#include "les_gridsync.cuh"
+#include "les_internal.h"
+
+namespace les {
+namespace {
+
+constexpr int WX = 64, WY = 16, WH = 2;
+constexpr int SX = WX + 2 * WH, SY = WY + 2 * WH, SN = SX * SY;  // a plane with its halo of two
+constexpr int NT = 256;                                          // threads per block
+// positions per thread: four owned nodes (x = lane + 32 (m & 1), y = warp +
+// 8 (m >> 1)) and two of the halo ring (336 positions: two rows below and
+// above, two columns left and right)
+constexpr int NO = WX * WY / NT, NR = 2 * SX * WH + 2 * WH * WY, NS = NO + (NR + NT - 1) / NT;
+static_assert(NO == 4 && NR == 336 && NS == 6, "tile and thread count");
+constexpr int D = 4;   // r_i / p_{i-1} ring: planes f .. f+3
+constexpr int DX = 6;  // x ring: planes f-2 .. f+3
+
+template <typename T>
+size_t wave_smem() {
+  return (size_t)((2 * D + DX + 4) * SN) * sizeof(T);
+}
+
+template <typename T>
+struct WaveArgs {
+  int nx, ny, nz, walls;
+  T cx, cy, cz;  // 1/dx^2, 1/dy^2, 1/dz^2
+  int ntx, nty, zrun, nchunk;
+  long long n;
+  const T* b;
+  T* x;
+  T* r[2];  // r_i in r[i & 1]
+  T* p[2];  // p_i in p[i & 1]
+  double* partials;
+  FusedBar* bar;
+  SolverCtl* ctl;
+  double tol;
+  int maxit;
+  long long spin_cycles;
+  unsigned expected;
+  int guard;
+};
+
+__device__ __forceinline__ int wrapw(int i, int n) {
+  while (i < 0) i += n;
+  while (i >= n) i -= n;
+  return i;
+}
+// the stored plane that stands for plane k: mirror images across the walls
+// (planes beyond one image: any valid plane, unused), or periodic
+__device__ __forceinline__ int zmapw(int k, int nz, int walls) {
+  if (walls) {
+    k = k < 0 ? -1 - k : (k >= nz ? 2 * nz - 1 - k : k);
+    return k < 0 ? 0 : (k >= nz ? nz - 1 : k);
+  }
+  return wrapw(k, nz);
+}
+
+// Long per-thread sums: FP32 within a run of 16 planes, compensated across
+template <typename T>
+struct WaveSum;
+template <>
+struct WaveSum<float> {
+  F2 s{0.f, 0.f};
+  float run = 0.f;
+  __device__ __forceinline__ void add(float v) { run += v; }
+  __device__ __forceinline__ void flush() {
+    f2_acc(s, run);
+    run = 0.f;
+  }
+  __device__ __forceinline__ F2 acc() const { return s; }
+};
+template <>
+struct WaveSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ double acc() const { return s; }
+};
+
+template <int NV, typename T>
+__device__ __forceinline__ bool wave_sum_t0(WaveSum<T> (&d)[NV], GridSync& gs, double (&tot)[NV]) {
+  decltype(d[0].acc()) v[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    d[q].flush();
+    v[q] = d[q].acc();
+  }
+  return grid_sum_t0<NV, 2>(v, gs, tot);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs<T> f) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* RINGR = reinterpret_cast<T*>(smraw);  // [D][SN] r_i as copied
+  T* RINGP = RINGR + D * SN;               // [D][SN] p_{i-1} as copied
+  T* RINGX = RINGP + D * SN;               // [DX][SN] x at the owned positions
+  T* PP = RINGX + DX * SN;                 // [2][SN] p of a plane, by plane parity
+  T* RP = PP + 2 * SN;                     // [2][SN] r' of a plane, by plane parity
+  __shared__ struct {
+    T ta, tb, mean;
+    int status, restart;
+  } sc;
+  const int tid = threadIdx.x;
+  const long long ncol = (long long)f.ntx * f.nty;
+  const long long nblk = ncol * f.nchunk;
+  const size_t plane = (size_t)f.nx * f.ny;
+  const T cx = f.cx, cy = f.cy, cz = f.cz;
+  GridSync gs{f.bar, f.partials, f.spin_cycles, f.expected, 0u};
+  const long long gstride = (long long)gridDim.x * NT;
+  const long long gtid = (long long)blockIdx.x * NT + tid;
+
+  // the 7-point operator straight from global memory (set-up sweeps only)
+  auto lap_global = [&](const T* v, int i, int j, int k) -> T {
+    const size_t row = (size_t)k * plane + (size_t)j * f.nx;
+    const T c2 = T(2) * __ldcg(v + row + i);
+    const T xm = __ldcg(v + row + wrapw(i - 1, f.nx)), xp = __ldcg(v + row + wrapw(i + 1, f.nx));
+    const T ym = __ldcg(v + (size_t)k * plane + (size_t)wrapw(j - 1, f.ny) * f.nx + i);
+    const T yp = __ldcg(v + (size_t)k * plane + (size_t)wrapw(j + 1, f.ny) * f.nx + i);
+    const T zm = __ldcg(v + (size_t)zmapw(k - 1, f.nz, f.walls) * plane + (size_t)j * f.nx + i);
+    const T zp = __ldcg(v + (size_t)zmapw(k + 1, f.nz, f.walls) * plane + (size_t)j * f.nx + i);
+    return (xm + xp - c2) * cx + (ym + yp - c2) * cy + (zm + zp - c2) * cz;
+  };
+
+  double rr = 0.0, bb = 0.0, rel = 0.0, pq = 0.0;  // meaningful in thread 0
+  int status = 0;  // 0 running, 1 converged, 2 maxit, 3 breakdown, 4 zero rhs, 5 timeout
+
+  // ---- set-up: mean of b ---------------------------------------------------------
+  {
+    WaveSum<T> s[1];
+    int cnt = 0;
+    for (long long m = gtid; m < f.n; m += gstride) {
+      s[0].add(__ldcg(f.b + m));
+      if ((++cnt & 15) == 0) s[0].flush();
+    }
+    double t[1];
+    const bool ok = wave_sum_t0<1>(s, gs, t);
+    if (tid == 0) {
+      sc.status = ok ? 0 : 5;
+      sc.mean = (T)(t[0] / (double)f.n);
+    }
+    __syncthreads();
+    status = sc.status;
+  }
+  const T mean = sc.mean;
+  // ---- r_0 = (b - mean) - L_c x0 into r[0]; r.r and |b - mean|^2 ----------------
+  if (!status) {
+    WaveSum<T> s[2];
+    int cnt = 0;
+    for (long long m = gtid; m < f.n; m += gstride) {
+      const int i = (int)(m % f.nx), j = (int)((m / f.nx) % f.ny), k = (int)(m / plane);
+      const T bm = __ldcg(f.b + m) - mean;
+      const T rv = bm - lap_global(f.x, i, j, k);
+      __stcg(f.r[0] + m, rv);
+      s[0].add(rv * rv);
+      s[1].add(bm * bm);
+      if ((++cnt & 15) == 0) {
+        s[0].flush();
+        s[1].flush();
+      }
+    }
+    double t[2];
+    const bool ok = wave_sum_t0<2>(s, gs, t);
+    if (tid == 0) {
+      // the plain solver judges a learned first guess: if it leaves a larger
+      // residual than x0 = 0, restart from zero (r = b - mean b, r.r = |b|^2)
+      sc.status = ok ? 0 : 5;
+      sc.restart = ok && f.guard && t[0] > t[1];
+      rr = sc.restart ? t[1] : t[0];
+      bb = t[1];
+    }
+    __syncthreads();
+    status = sc.status;
+    if (!status && sc.restart) {
+      for (long long m = gtid; m < f.n; m += gstride) {
+        __stcg(f.x + m, T(0));
+        __stcg(f.r[0] + m, __ldcg(f.b + m) - mean);
+      }
+      WaveSum<T> none[1];
+      double t1[1];
+      const bool ok2 = wave_sum_t0<1>(none, gs, t1);  // a grid barrier: r_0 complete everywhere
+      if (tid == 0) sc.status = ok2 ? 0 : 5;
+      __syncthreads();
+      status = sc.status;
+    }
+  }
+  if (tid == 0) {
+    if (!status) {
+      if (bb == 0.0) status = 4;
+      else {
+        rel = sqrt(rr / bb);
+        if (rel <= f.tol) status = 1;
+        else if (f.maxit <= 0) status = 2;
+      }
+    }
+    sc.status = status;
+  }
+  __syncthreads();
+  status = sc.status;
+  // ---- p_0 = r_0: r_0 . L_c r_0 gives alpha_0 --------------------------------------
+  if (!status) {
+    WaveSum<T> s[1];
+    int cnt = 0;
+    for (long long m = gtid; m < f.n; m += gstride) {
+      const int i = (int)(m % f.nx), j = (int)((m / f.nx) % f.ny), k = (int)(m / plane);
+      s[0].add(__ldcg(f.r[0] + m) * lap_global(f.r[0], i, j, k));
+      if ((++cnt & 15) == 0) s[0].flush();
+    }
+    double t[1];
+    const bool ok = wave_sum_t0<1>(s, gs, t);
+    if (tid == 0) {
+      pq = t[0];
+      if (!ok) status = 5;
+      else if (pq == 0.0 || !isfinite(pq)) status = 3;
+      else {
+        sc.ta = (T)(rr / pq);
+        sc.tb = T(0);
+      }
+      sc.status = status;
+    }
+    __syncthreads();
+    status = sc.status;
+  }
+
+  // ---- iterations ----------------------------------------------------------------
+  int iter = 0;
+  while (!status) {
+    const T ta = sc.ta, tb = sc.tb;
+    const bool first = iter == 0;
+    const T* ri = f.r[iter & 1];
+    T* ro = f.r[(iter + 1) & 1];
+    const T* pold = f.p[(iter + 1) & 1];  // p_{i-1}
+    T* pw = f.p[iter & 1];
+    WaveSum<T> s[4];  // r'.r', r'.w, r'.q, p.q
+    for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+      const int col = (int)(blk % ncol), chunk = (int)(blk / ncol);
+      const int x0 = (col % f.ntx) * WX, y0 = (col / f.ntx) * WY;
+      const int k0 = chunk * f.zrun, k1 = min(k0 + f.zrun, f.nz);
+      // this thread's positions: index in a staged plane, in-plane global
+      // offset; the halo slots' classes (valid, within the halo of one)
+      int es[NS], goff[NS];
+      unsigned valid = (1u << NO) - 1u, in1 = (1u << NO) - 1u;
+#pragma unroll
+      for (int m = 0; m < NS; ++m) {
+        int ex, ey;
+        if (m < NO) {
+          ex = (tid & 31) + 32 * (m & 1);
+          ey = (tid >> 5) + 8 * (m >> 1);
+        } else {
+          const int j = tid + (m - NO) * NT;
+          if (j < 2 * SX * WH) {  // the two rows below and the two above
+            const int top = j >= SX * WH;
+            const int jj = j - top * SX * WH;
+            ey = (top ? WY : -WH) + jj / SX;
+            ex = jj % SX - WH;
+          } else {  // two columns left and right of the owned rows
+            const int jj = min(j - 2 * SX * WH, 4 * WY - 1);
+            const int c = jj & 3;
+            ey = jj >> 2;
+            ex = c < 2 ? c - WH : WX - 2 + c;
+          }
+          if (j < NR) {
+            valid |= 1u << m;
+            if (ex >= -1 && ex <= WX && ey >= -1 && ey <= WY) in1 |= 1u << m;
+          }
+        }
+        es[m] = (ey + WH) * SX + (ex + WH);
+        goff[m] = wrapw(y0 + ey, f.ny) * f.nx + wrapw(x0 + ex, f.nx);
+      }
+      // plane kk of r_i, p_{i-1} (every position) and of x (owned positions,
+      // planes of the run) into their ring slots; one commit group per plane
+      auto fetch = [&](int kk) {
+        const size_t base = (size_t)zmapw(kk, f.nz, f.walls) * plane;
+        T* rr_ = RINGR + ((kk + 2 * D) % D) * SN;
+        T* pp_ = RINGP + ((kk + 2 * D) % D) * SN;
+        T* xx_ = RINGX + ((kk + 2 * DX) % DX) * SN;
+        const bool xrun = kk >= k0 && kk < k1;
+#pragma unroll
+        for (int m = 0; m < NS; ++m) {
+          if (m >= NO && !(valid >> m & 1u)) continue;
+          const int e = es[m];
+          cp_async(rr_ + e, ri + base + goff[m]);
+          if (!first) cp_async(pp_ + e, pold + base + goff[m]);
+          if (m < NO && xrun) cp_async(xx_ + e, f.x + base + goff[m]);
+        }
+        cp_commit();
+      };
+      // register windows per position: p on f-2 .. f, r' on f-3 .. f-1, r_i
+      // on f-1 .. f
+      T pw0[NS], pw1[NS], pw2[NS], rw0[NS], rw1[NS], rw2[NS], ra0[NS], ra1[NS];
+#pragma unroll
+      for (int m = 0; m < NS; ++m) pw0[m] = pw1[m] = pw2[m] = rw0[m] = rw1[m] = rw2[m] = ra0[m] = ra1[m] = T(0);
+      __syncthreads();  // the previous column's readers are done with every buffer
+      for (int kk = k0 - 2; kk < k0 - 2 + D - 1; ++kk) fetch(kk);
+      int cnt = 0;
+      for (int fp = k0 - 2; fp <= k1 + 1; ++fp) {
+        // plane fp has landed: the D - 2 later copy groups may still fly
+        cp_wait<D - 2>();
+        __syncthreads();
+        // the slot of plane fp - 1 is free (its r_i is held in registers)
+        fetch(fp + D - 1);
+        const T* rr_ = RINGR + ((fp + 2 * D) % D) * SN;
+        const T* pp_ = RINGP + ((fp + 2 * D) % D) * SN;
+        T* pnew = PP + (fp & 1) * SN;
+        // A: p(fp) = r(fp) + beta p_old(fp)
+#pragma unroll
+        for (int m = 0; m < NS; ++m) {
+          if (m >= NO && !(valid >> m & 1u)) continue;
+          const int e = es[m];
+          const T rv = rr_[e];
+          const T pv = first ? rv : rv + tb * pp_[e];
+          pw2[m] = pv;
+          ra1[m] = rv;
+          pnew[e] = pv;
+        }
+        // B: q(fp-1), r'(fp-1) within the halo of one (needs p(fp-2))
+        if (fp >= k0) {
+          const T* pc = PP + ((fp - 1) & 1) * SN;
+          T* rnew = RP + ((fp - 1) & 1) * SN;
+          const bool count = fp - 1 >= k0 && fp - 1 < k1;
+#pragma unroll
+          for (int m = 0; m < NS; ++m) {
+            if (m >= NO && !(in1 >> m & 1u)) continue;
+            const int e = es[m];
+            const T c2 = T(2) * pw1[m];
+            const T qv = (pc[e - 1] + pc[e + 1] - c2) * cx + (pc[e - SX] + pc[e + SX] - c2) * cy +
+                         (pw0[m] + pw2[m] - c2) * cz;
+            const T r1 = ra0[m] - ta * qv;
+            rw2[m] = r1;
+            rnew[e] = r1;
+            if (m < NO && count) {
+              s[2].add(r1 * qv);
+              s[3].add(pw1[m] * qv);
+            }
+          }
+        }
+        // C, D: w(fp-2) and the outputs of plane fp-2 (needs r'(fp-3))
+        if (fp >= k0 + 2) {
+          const int k = fp - 2;
+          const T* rc = RP + (k & 1) * SN;
+          const T* xx_ = RINGX + ((k + 2 * DX) % DX) * SN;
+          const size_t base = (size_t)k * plane;
+#pragma unroll
+          for (int m = 0; m < NO; ++m) {
+            const int e = es[m];
+            const T c2 = T(2) * rw1[m];
+            const T w = (rc[e - 1] + rc[e + 1] - c2) * cx + (rc[e - SX] + rc[e + SX] - c2) * cy +
+                        (rw0[m] + rw2[m] - c2) * cz;
+            s[0].add(rw1[m] * rw1[m]);
+            s[1].add(rw1[m] * w);
+            const size_t g = base + goff[m];
+            __stcg(f.x + g, xx_[e] + ta * pw0[m]);
+            __stcg(pw + g, pw0[m]);
+            __stcg(ro + g, rw1[m]);
+          }
+          if ((++cnt & 15) == 0)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s[q].flush();
+        }
+        // roll the windows
+#pragma unroll
+        for (int m = 0; m < NS; ++m) {
+          pw0[m] = pw1[m];
+          pw1[m] = pw2[m];
+          rw0[m] = rw1[m];
+          rw1[m] = rw2[m];
+          ra0[m] = ra1[m];
+        }
+      }
+      cp_wait<0>();
+    }
+    double t[4];
+    const bool ok = wave_sum_t0<4>(s, gs, t);
+    iter += 1;
+    if (tid == 0) {
+      if (!ok) {
+        status = 5;
+      } else {
+        const double rr_new = t[0];
+        rel = sqrt(rr_new / bb);
+        if (rel <= f.tol) status = 1;
+        else if (iter >= f.maxit) status = 2;
+        else if (!isfinite(rr_new)) status = 3;
+        else {
+          const double beta = rr_new / rr;
+          const double pq_new = t[1] + 2.0 * beta * t[2] + beta * beta * t[3];
+          if (pq_new == 0.0 || !isfinite(pq_new)) status = 3;
+          else {
+            sc.ta = (T)(rr_new / pq_new);
+            sc.tb = (T)beta;
+          }
+        }
+        rr = rr_new;
+      }
+      sc.status = status;
+    }
+    __syncthreads();
+    status = sc.status;
+  }
+
+  // ---- zero-mean gauge (or zero for a zero right side) ------------------------
+  if (status != 5) {
+    WaveSum<T> s[1];
+    int cnt = 0;
+    for (long long m = gtid; m < f.n; m += gstride) {
+      s[0].add(__ldcg(f.x + m));
+      if ((++cnt & 15) == 0) s[0].flush();
+    }
+    double t[1];
+    const bool ok = wave_sum_t0<1>(s, gs, t);
+    if (tid == 0) {
+      if (!ok) status = 5;
+      sc.mean = (T)(t[0] / (double)f.n);
+      sc.status = status;
+    }
+    __syncthreads();
+    status = sc.status;
+    if (status != 5) {
+      const T mx = sc.mean;
+      for (long long m = gtid; m < f.n; m += gstride) __stcg(f.x + m, status == 4 ? T(0) : __ldcg(f.x + m) - mx);
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    f.ctl->iter = iter;
+    f.ctl->rel = rel;
+    f.ctl->done = status;
+  }
+}
+
+}  // namespace
+
+bool wave_cg_eligible(int nx, int ny, int nz) {
+  return nx % WX == 0 && ny % WY == 0 && nz >= 2 && (long long)nx * ny < (1LL << 31);
+}
+
+template <typename T>
+int poisson_solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
+                       int* iters, double* rel, std::string* err) {
+  WaveArgs<T> f;
+  f.nx = a.g.nx;
+  f.ny = a.g.ny;
+  f.nz = a.g.nz;
+  f.walls = a.g.walls;
+  f.cx = a.g.idx * a.g.idx;
+  f.cy = a.g.idy * a.g.idy;
+  f.cz = a.g.idz * a.g.idz;
+  f.ntx = f.nx / WX;
+  f.nty = f.ny / WY;
+  f.n = (long long)f.nx * f.ny * f.nz;
+  f.b = b;
+  f.x = x;
+  f.r[0] = a.r;
+  f.r[1] = a.q;
+  f.p[0] = a.p0;
+  f.p[1] = a.p1;
+  f.partials = a.partials;
+  f.bar = a.bar;
+  f.ctl = a.ctl;
+  f.tol = tol;
+  f.maxit = maxit;
+  f.spin_cycles = fc.spin_cycles;
+  f.guard = a.guard;
+  int per_sm = 0, dev = 0, nsm = 0;
+  cudaError_t e;
+  const void* kern = (const void*)k_cg_wave<T>;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wave_smem<T>())) !=
+          cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, wave_smem<T>())) != cudaSuccess) {
+    if (err) *err = std::string("wave CG occupancy: ") + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  if (per_sm < 1) {
+    if (err) *err = "wave CG: no block fits on an SM";
+    return LES_ERR_CUDA;
+  }
+  long long G = (long long)per_sm * nsm;
+  G = std::min<long long>(G, fc.max_blocks);
+  G = std::min<long long>(G, 8LL * nsm);  // the partials hold 2 x 4 x 8 slots per SM
+  // z-runs: enough columns x runs to give every block work, runs as long as
+  // possible (each run re-forms two planes of p and r' below it)
+  const long long ncol = (long long)f.ntx * f.nty;
+  const long long want = std::max<long long>(1, std::min<long long>((long long)f.nz, (G + ncol - 1) / ncol));
+  f.zrun = (int)((f.nz + want - 1) / want);
+  f.nchunk = (f.nz + f.zrun - 1) / f.zrun;
+  G = std::max<long long>(1, std::min<long long>(G, ncol * f.nchunk));
+  f.expected = (unsigned)G + (unsigned)std::max(0, fc.missing);
+  if ((e = cudaMemsetAsync(a.bar, 0, sizeof(FusedBar), a.st)) != cudaSuccess) {
+    if (err) *err = std::string("wave CG barrier reset: ") + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  void* args[] = {&f};
+  {
+    ProfScope ps(a.prof, KI_CG_WAVE, a.st);
+    e = cudaLaunchCooperativeKernel(kern, dim3((unsigned)G), dim3(NT), args, wave_smem<T>(), a.st);
+  }
+  if (e != cudaSuccess) {
+    if (err) *err = std::string("wave CG launch: ") + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  if ((e = cudaMemcpyAsync(a.ctl_host, a.ctl, sizeof(SolverCtl), cudaMemcpyDeviceToHost, a.st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(a.st)) != cudaSuccess) {
+    if (err) *err = std::string("wave CG: ") + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  const SolverCtl& c = *a.ctl_host;
+  if (iters) *iters = c.iter;
+  if (rel) *rel = c.rel;
+  // algorithmic traffic of the solve (kCgIterFields per iteration; this
+  // kernel streams 6 per iteration plus a third of r_i and p_{i-1} again for
+  // the halo, and one set-up sweep for alpha_0)
+  if (a.prof) a.prof->bytes[KI_CG_WAVE] += (kCgSetupFields + 1.0 + kCgIterFields * c.iter) * (double)f.n * sizeof(T);
+  switch (c.done) {
+    case 1:
+    case 4: return LES_OK;
+    case 2: return LES_ERR_NOT_CONVERGED;
+    case 3:
+      if (err) *err = "poisson: breakdown (zero or non-finite p.Ap / residual)";
+      return LES_ERR_NONFINITE;
+    case 5:
+      if (err) *err = "poisson: a grid barrier wait timed out";
+      return LES_ERR_TIMEOUT;
+    default:
+      if (err) *err = "poisson: wave solver returned no status";
+      return LES_ERR_CUDA;
+  }
+}
+
+template int poisson_solve_wave<float>(const SolverArgs<float>&, const FusedCfg&, const float*, float*, double, int,
+                                       int*, double*, std::string*);
+template int poisson_solve_wave<double>(const SolverArgs<double>&, const FusedCfg&, const double*, double*, double,
+                                        int, int*, double*, std::string*);
+
+}  // namespace les

@@ -116,7 +116,7 @@ struct LaunchCfg {
 enum KernelId : int {
   KI_THERMO = 0, KI_RADIATION, KI_NU, KI_NU_HALF, KI_SCALAR, KI_MOMENTUM, KI_RHS, KI_CORRECT,
   KI_DIAG, KI_CFL, KI_APPLY, KI_SUM, KI_CG_INIT, KI_CG_MATVEC, KI_CG_UPDATE, KI_JACOBI, KI_FINISH,
-  KI_CTL, KI_CG_FUSED, KI_UNET_CONV, KI_UNET_WGRAD, KI_UNET_ADAM, KI_CG_RESIDENT, KI_CG_ROLL, KI_COUNT
+  KI_CTL, KI_CG_FUSED, KI_UNET_CONV, KI_UNET_WGRAD, KI_UNET_ADAM, KI_CG_RESIDENT, KI_CG_ROLL, KI_CG_WAVE, KI_COUNT
 };
 extern const char* const kKernelNames[KI_COUNT];
 
@@ -304,6 +304,12 @@ int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, 
 // grid, compact operator.
 template <typename T>
 int poisson_solve_roll(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
+                       int* iters, double* rel, std::string* err);
+// one pass and one grid sum per iteration, 64 x 16 columns with z windows in
+// registers (nx % 64 == 0, ny % 16 == 0)
+bool wave_cg_eligible(int nx, int ny, int nz);
+template <typename T>
+int poisson_solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
                        int* iters, double* rel, std::string* err);
 // Persistent CG with its vectors in shared memory (les_cg_resident.cu).
 // Sets *used = false and returns LES_OK without launching when the grid has

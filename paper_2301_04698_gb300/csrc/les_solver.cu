@@ -310,9 +310,10 @@ template <typename T>
 int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxit, int* iters, double* rel,
                   std::string* err) {
   // persistent CG: in shared memory when the grid fits there; else the
-  // two-phase streaming kernel on tile-aligned grids (variant 0 or 2) or the
-  // one-pass kernel (variant 0 on other grids, or variant 3); variant 1 is
-  // Chronopoulos-Gear.  Persistent solves of different handles (ensemble
+  // one-pass kernel with 64 x 16 columns (variant 4, and variant 0 for FP32
+  // grids of whole columns), the two-phase streaming kernel on tile-aligned
+  // grids (variant 0 or 2) or the one-pass kernel (variant 0 on other grids,
+  // or variant 3); variant 1 is Chronopoulos-Gear.  Persistent solves of different handles (ensemble
   // members stepped from several host threads) run one at a time: each
   // grid spins on its own barrier and is sized to fill the GPU, so two of
   // them must never wait for each other's SMs.
@@ -326,7 +327,11 @@ int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxi
     const int rc = poisson_solve_resident<T>(a, *a.fused, b, x, tol, maxit, iters, rel, err, &used);
     if (used || rc != LES_OK) return rc;
   }
-  if (a.bar && cg_c && (var == 3 || (var == 0 && !tiled)))
+  // FP32 grids of whole 64 x 16 columns: the one-pass kernel with register
+  // windows is the default (1.5x the two-phase kernel on 1536^2 x 256)
+  if (a.bar && cg_c && (var == 4 || (var == 0 && sizeof(T) == 4)) && wave_cg_eligible(a.g.nx, a.g.ny, a.g.nz))
+    return poisson_solve_wave<T>(a, *a.fused, b, x, tol, maxit, iters, rel, err);
+  if (a.bar && cg_c && (var == 3 || var == 4 || (var == 0 && !tiled)))
     return poisson_solve_roll<T>(a, *a.fused, b, x, tol, maxit, iters, rel, err);
   if (a.bar && tiled && var >= 0 && var <= 2)
     return poisson_solve_fused<T>(a, *a.fused, b, x, tol, maxit, iters, rel, err);

@@ -333,7 +333,7 @@ def test_ragged_and_minimum_grids(les_mod, shape):
 # persistent single-launch CG (fast path for nx a multiple of the tile width)
 
 
-def _fused_launches(sim, names=("cg_fused", "cg_resident", "cg_roll")):
+def _fused_launches(sim, names=("cg_fused", "cg_resident", "cg_roll", "cg_wave")):
     return sum(k["launches"] for k in sim.profile_read() if k["name"] in names)
 
 
@@ -492,6 +492,53 @@ def test_rolling_cg_matches_oracle(les_mod, precision, walls, shape):
     assert _fused_launches(sim1) == 0
     assert abs(it - it1) <= (1 if precision == 64 else 3)
     assert rel(xn, x1.cpu().double().numpy()) < (1e-9 if precision == 64 else 5e-4)
+    # not converged within maxit, and a zero right side
+    x = torch.zeros_like(bt)
+    rc, it, res = sim.poisson_solve(bt, x, 1e-30, 5, allow_not_converged=True)
+    assert rc == les_mod.LES_ERR_NOT_CONVERGED and it == 5
+    x = torch.ones_like(bt)
+    rc, it, res = sim.poisson_solve(torch.zeros_like(bt), x, tol, 100)
+    assert rc == 0 and it == 0 and float(x.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("precision,walls,shape,max_blocks", [
+    (32, True, (64, 16, 20), 0),        # one column, a long z-run
+    (64, False, (128, 32, 9), 0),       # several columns, periodic
+    (32, False, (64, 32, 3), 0),        # three planes, periodic
+    (32, True, (192, 48, 40), 0),       # the tile-aligned grid of a larger run
+    (64, True, (64, 16, 2), 0),         # two planes between the walls
+    (32, True, (128, 16, 24), 64)])     # several z-runs per column, blocks looping
+def test_wave_cg_matches_oracle(les_mod, precision, walls, shape, max_blocks):
+    """The one-pass CG with 64 x 16 columns and register windows (variant 4)
+    against the FP64 oracle and the one-pass kernel of variant 3 (same
+    iterates)."""
+    from oracle import Oracle
+    nx, ny, nz = shape
+    case = inputs.Case(name="wave", nx=nx, ny=ny, nz=nz, dx=35.0, dy=30.0, dz=10.0, walls=walls,
+                       precision=precision, init="zero", physics=())
+    ref = Oracle(case.replace(precision=64))
+    b = inputs.uniform(33, 0, case.n, -1, 1).reshape(case.shape) + 0.25
+    xr, st, itr, _ = ref.poisson(b, tol=1e-12, maxit=20000)
+    dt = torch.float64 if precision == 64 else torch.float32
+    tol = 1e-11 if precision == 64 else 1e-6
+    bt = torch.from_numpy(b).to("cuda", dt)
+    x0 = torch.from_numpy(0.1 * inputs.uniform(34, 0, case.n, -1, 1).reshape(case.shape)).to("cuda", dt)
+    out = {}
+    for variant, kern in ((4, "cg_wave"), (3, "cg_roll")):
+        sim = les_mod.Simulation(case)
+        sim.set_tuning(cg_resident=1, cg_variant=variant, cg_max_blocks=max_blocks if max_blocks else 1 << 20)
+        sim.profile_reset()
+        x = x0.clone()
+        rc, it, res = sim.poisson_solve(bt, x, tol, 20000)
+        assert rc == 0 and res <= tol, (variant, rc, res)
+        assert _fused_launches(sim, (kern,)) == 1
+        xn = x.cpu().double().numpy()
+        assert abs(xn.mean()) < (1e-14 if precision == 64 else 1e-6) * np.abs(xn).max()
+        assert rel(xn, xr) < (1e-8 if precision == 64 else 5e-4), variant
+        out[variant] = (it, xn, sim)
+    assert abs(out[4][0] - out[3][0]) <= (1 if precision == 64 else 3)
+    assert rel(out[4][1], out[3][1]) < (1e-9 if precision == 64 else 5e-4)
+    sim = out[4][2]
     # not converged within maxit, and a zero right side
     x = torch.zeros_like(bt)
     rc, it, res = sim.poisson_solve(bt, x, 1e-30, 5, allow_not_converged=True)
