@@ -22,7 +22,8 @@
 // enters the march.  Only in-plane neighbours pass through shared memory
 // (one plane of p and one of r', each double-buffered by plane parity); the
 // planes of r_i and p_{i-1} (halo two) and of x (owned nodes) arrive through
-// rings that cp.async fills three planes ahead.  Per plane step, after one
+// rings that cp.async fills three planes ahead, in 16-byte chunks (and pairs
+// of nodes at the halo's x ends).  Per plane step, after one
 // block barrier:
 //   A  p(f) = r(f) + beta p_old(f) at every position
 //   B  q(f-1) = L_c p, r'(f-1) = r(f-1) - alpha q(f-1) within the halo of one
@@ -34,6 +35,7 @@
 // p_{i-1}, x) and written three times (p_i, r_{i+1}, x); the halo re-reads a
 // third of r_i and p_{i-1}, mostly from L2.
 #include <algorithm>
+#include <cstdint>
 #include <string>
 
 #include "les_gridsync.cuh"
@@ -43,7 +45,10 @@ namespace les {
 namespace {
 
 constexpr int WX = 64, WY = 16, WH = 2;
-constexpr int SX = WX + 2 * WH, SY = WY + 2 * WH, SN = SX * SY;  // a plane with its halo of two
+constexpr int SX = WX + 2 * WH, SY = WY + 2 * WH;  // a plane with its halo of two
+// staged planes in shared memory: rows of SP elements, the owned columns from
+// element 4 on (16-byte aligned rows, so whole 16-byte chunks are copied)
+constexpr int SP = WX + 8, SN = SP * SY;
 constexpr int NT = 256;                                          // threads per block
 // positions per thread: four owned nodes (x = lane + 32 (m & 1), y = warp +
 // 8 (m >> 1)) and two of the halo ring (336 positions: two rows below and
@@ -52,6 +57,18 @@ constexpr int NO = WX * WY / NT, NR = 2 * SX * WH + 2 * WH * WY, NS = NO + (NR +
 static_assert(NO == 4 && NR == 336 && NS == 6, "tile and thread count");
 constexpr int D = 4;   // r_i / p_{i-1} ring: planes f .. f+3
 constexpr int DX = 6;  // x ring: planes f-2 .. f+3
+
+// the staging copies of a plane: owned rows in 16-byte chunks; each halo row
+// in chunks with a pair of nodes at either end; a pair at either end of each
+// owned row
+template <typename T>
+struct Copies {
+  static constexpr int V = 16 / (int)sizeof(T);      // nodes per 16-byte chunk
+  static constexpr int OC = WX * WY / V / NT;         // owned chunks per thread
+  static constexpr int RC = WX / V + 2;               // copies per halo row
+  static constexpr int NH = 2 * WH * RC + 2 * WY;     // halo copies per plane
+  static_assert(OC * V * NT == WX * WY && NH <= NT, "copy plan");
+};
 
 template <typename T>
 size_t wave_smem() {
@@ -275,15 +292,17 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
       const int k0 = chunk * f.zrun, k1 = min(k0 + f.zrun, f.nz);
       // this thread's positions: index in a staged plane, in-plane global
       // offset; the halo slots' classes (valid, within the halo of one)
-      int es[NS], goff[NS];
+      // (owned slots: a base plus constants, x = lane + 32 (m & 1), y = warp +
+      // 8 (m >> 1))
+      int esr[NS - NO] = {};  // halo slots
       unsigned valid = (1u << NO) - 1u, in1 = (1u << NO) - 1u;
+      const int go0 = (y0 + (tid >> 5)) * f.nx + x0 + (tid & 31);  // global offset of owned slot 0
+      const int eo0 = ((tid >> 5) + WH) * SP + (tid & 31) + 4;      // staged index of owned slot 0
+      auto es = [&](int m) { return m < NO ? eo0 + 8 * (m >> 1) * SP + 32 * (m & 1) : esr[m - NO]; };
 #pragma unroll
-      for (int m = 0; m < NS; ++m) {
+      for (int m = NO; m < NS; ++m) {
         int ex, ey;
-        if (m < NO) {
-          ex = (tid & 31) + 32 * (m & 1);
-          ey = (tid >> 5) + 8 * (m >> 1);
-        } else {
+        {
           const int j = tid + (m - NO) * NT;
           if (j < 2 * SX * WH) {  // the two rows below and the two above
             const int top = j >= SX * WH;
@@ -301,8 +320,33 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
             if (ex >= -1 && ex <= WX && ey >= -1 && ey <= WY) in1 |= 1u << m;
           }
         }
-        es[m] = (ey + WH) * SX + (ex + WH);
-        goff[m] = wrapw(y0 + ey, f.ny) * f.nx + wrapw(x0 + ex, f.nx);
+        esr[m - NO] = (ey + WH) * SP + (ex + 4);
+      }
+      // this thread's staging copies (shared and in-plane global offsets)
+      using CP = Copies<T>;
+      int od[CP::OC], os[CP::OC];
+#pragma unroll
+      for (int j = 0; j < CP::OC; ++j) {
+        const int c = tid + j * NT, ey = c / (WX / CP::V), ex = (c % (WX / CP::V)) * CP::V;
+        od[j] = (ey + WH) * SP + ex + 4;
+        os[j] = (y0 + ey) * f.nx + x0 + ex;
+      }
+      int hd = 0, hs = 0, hk = 0;  // halo copy: kind 0 none, 1 a pair of nodes, 2 a chunk
+      if (tid < CP::NH) {
+        int ey, ex;
+        if (tid < 2 * WH * CP::RC) {
+          const int r = tid / CP::RC, j = tid % CP::RC;
+          ey = r < WH ? r - WH : WY + r - WH;
+          ex = j == 0 ? -WH : (j == CP::RC - 1 ? WX : (j - 1) * CP::V);
+          hk = (j == 0 || j == CP::RC - 1) ? 1 : 2;
+        } else {
+          const int c = tid - 2 * WH * CP::RC;
+          ey = c >> 1;
+          ex = (c & 1) ? WX : -WH;
+          hk = 1;
+        }
+        hd = (ey + WH) * SP + ex + 4;
+        hs = wrapw(y0 + ey, f.ny) * f.nx + wrapw(x0 + ex, f.nx);
       }
       // plane kk of r_i, p_{i-1} (every position) and of x (owned positions,
       // planes of the run) into their ring slots; one commit group per plane
@@ -311,14 +355,22 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
         T* rr_ = RINGR + ((kk + 2 * D) % D) * SN;
         T* pp_ = RINGP + ((kk + 2 * D) % D) * SN;
         T* xx_ = RINGX + ((kk + 2 * DX) % DX) * SN;
+        const T* rs = ri + base;
+        const T* ps = pold + base;
+        const T* xs = f.x + base;
         const bool xrun = kk >= k0 && kk < k1;
 #pragma unroll
-        for (int m = 0; m < NS; ++m) {
-          if (m >= NO && !(valid >> m & 1u)) continue;
-          const int e = es[m];
-          cp_async(rr_ + e, ri + base + goff[m]);
-          if (!first) cp_async(pp_ + e, pold + base + goff[m]);
-          if (m < NO && xrun) cp_async(xx_ + e, f.x + base + goff[m]);
+        for (int j = 0; j < CP::OC; ++j) {
+          cp_async_bytes<16>(rr_ + od[j], rs + os[j]);
+          if (!first) cp_async_bytes<16>(pp_ + od[j], ps + os[j]);
+          if (xrun) cp_async_bytes<16>(xx_ + od[j], xs + os[j]);
+        }
+        if (hk == 2) {
+          cp_async_bytes<16>(rr_ + hd, rs + hs);
+          if (!first) cp_async_bytes<16>(pp_ + hd, ps + hs);
+        } else if (hk == 1) {
+          cp_async_bytes<2 * sizeof(T)>(rr_ + hd, rs + hs);
+          if (!first) cp_async_bytes<2 * sizeof(T)>(pp_ + hd, ps + hs);
         }
         cp_commit();
       };
@@ -343,7 +395,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
 #pragma unroll
         for (int m = 0; m < NS; ++m) {
           if (m >= NO && !(valid >> m & 1u)) continue;
-          const int e = es[m];
+          const int e = es(m);
           const T rv = rr_[e];
           const T pv = first ? rv : rv + tb * pp_[e];
           pw2[m] = pv;
@@ -358,9 +410,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
 #pragma unroll
           for (int m = 0; m < NS; ++m) {
             if (m >= NO && !(in1 >> m & 1u)) continue;
-            const int e = es[m];
+            const int e = es(m);
             const T c2 = T(2) * pw1[m];
-            const T qv = (pc[e - 1] + pc[e + 1] - c2) * cx + (pc[e - SX] + pc[e + SX] - c2) * cy +
+            const T qv = (pc[e - 1] + pc[e + 1] - c2) * cx + (pc[e - SP] + pc[e + SP] - c2) * cy +
                          (pw0[m] + pw2[m] - c2) * cz;
             const T r1 = ra0[m] - ta * qv;
             rw2[m] = r1;
@@ -379,13 +431,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
           const size_t base = (size_t)k * plane;
 #pragma unroll
           for (int m = 0; m < NO; ++m) {
-            const int e = es[m];
+            const int e = es(m);
             const T c2 = T(2) * rw1[m];
-            const T w = (rc[e - 1] + rc[e + 1] - c2) * cx + (rc[e - SX] + rc[e + SX] - c2) * cy +
+            const T w = (rc[e - 1] + rc[e + 1] - c2) * cx + (rc[e - SP] + rc[e + SP] - c2) * cy +
                         (rw0[m] + rw2[m] - c2) * cz;
             s[0].add(rw1[m] * rw1[m]);
             s[1].add(rw1[m] * w);
-            const size_t g = base + goff[m];
+            const size_t g = base + go0 + (8 * (m >> 1)) * f.nx + 32 * (m & 1);
             __stcg(f.x + g, xx_[e] + ta * pw0[m]);
             __stcg(pw + g, pw0[m]);
             __stcg(ro + g, rw1[m]);
@@ -473,6 +525,12 @@ bool wave_cg_eligible(int nx, int ny, int nz) {
 template <typename T>
 int poisson_solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
                        int* iters, double* rel, std::string* err) {
+  // the staging copies move 16-byte chunks: every vector must start on a
+  // 16-byte boundary (a caller's view at an odd offset takes the one-pass
+  // kernel for any grid instead)
+  auto aligned = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+  if (!(aligned(b) && aligned(x) && aligned(a.r) && aligned(a.q) && aligned(a.p0) && aligned(a.p1)))
+    return poisson_solve_roll<T>(a, fc, b, x, tol, maxit, iters, rel, err);
   WaveArgs<T> f;
   f.nx = a.g.nx;
   f.ny = a.g.ny;
