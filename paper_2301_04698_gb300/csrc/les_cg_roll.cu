@@ -150,6 +150,16 @@ __global__ void __launch_bounds__(CX* CY, 3) k_cg_roll(RollArgs<T> f) {
     const T zp = __ldcg(v + (size_t)zmapc(k + 1, f.nz, f.walls) * plane + (size_t)j * f.nx + i);
     return (xm + xp - c2) * cx + (ym + yp - c2) * cy + (zm + zp - c2) * cz;
   };
+  // every node once, rows of x dealt to the blocks (one division per row, not
+  // three 64-bit ones per node)
+  auto each_node = [&](auto&& body) {
+    const long long nrow = (long long)f.ny * f.nz;
+    for (long long rw = blockIdx.x; rw < nrow; rw += gridDim.x) {
+      const int j = (int)(rw % f.ny), k = (int)(rw / f.ny);
+      const long long m0 = rw * f.nx;
+      for (int i = tid; i < f.nx; i += CX * CY) body(m0 + i, i, j, k);
+    }
+  };
 
   double rr = 0.0, bb = 0.0, rel = 0.0, pq = 0.0;  // meaningful in thread 0
   int status = 0;  // 0 running, 1 converged, 2 maxit, 3 breakdown, 4 zero rhs, 5 timeout
@@ -176,8 +186,7 @@ __global__ void __launch_bounds__(CX* CY, 3) k_cg_roll(RollArgs<T> f) {
   if (!status) {
     LongSum<T> s[2];
     int cnt = 0;
-    for (long long m = gtid; m < f.n; m += gstride) {
-      const int i = (int)(m % f.nx), j = (int)((m / f.nx) % f.ny), k = (int)(m / plane);
+    each_node([&](long long m, int i, int j, int k) {
       const T bm = __ldcg(f.b + m) - mean;
       const T rv = bm - lap_global(f.x, i, j, k);
       __stcg(f.r[0] + m, rv);
@@ -187,7 +196,7 @@ __global__ void __launch_bounds__(CX* CY, 3) k_cg_roll(RollArgs<T> f) {
         s[0].flush();
         s[1].flush();
       }
-    }
+    });
     double t[2];
     const bool ok = grid_long_t0<2>(s, gs, t);
     if (tid == 0) {
@@ -230,11 +239,10 @@ __global__ void __launch_bounds__(CX* CY, 3) k_cg_roll(RollArgs<T> f) {
   if (!status) {
     LongSum<T> s[1];
     int cnt = 0;
-    for (long long m = gtid; m < f.n; m += gstride) {
-      const int i = (int)(m % f.nx), j = (int)((m / f.nx) % f.ny), k = (int)(m / plane);
+    each_node([&](long long m, int i, int j, int k) {
       s[0].add(__ldcg(f.r[0] + m) * lap_global(f.r[0], i, j, k));
       if ((++cnt & 15) == 0) s[0].flush();
-    }
+    });
     double t[1];
     const bool ok = grid_long_t0<1>(s, gs, t);
     if (tid == 0) {
