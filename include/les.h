@@ -308,7 +308,7 @@ typedef struct les_tuning {
                                       standard CG iterates -- in shared
                                       memory when the grid fits there (see
                                       cg_resident), else variant 4 for
-                                      FP32 grids of whole 64 x 16 columns,
+                                      FP32 grids of whole columns,
                                       else variant 2 on tile-aligned grids,
                                       else variant 3;
                                       1 Chronopoulos-Gear (one barrier; its
@@ -317,10 +317,10 @@ typedef struct les_tuning {
                                       two-phase streaming CG (two barriers
                                       per iteration); 3 one pass over memory
                                       and one grid reduction per iteration,
-                                      any grid; 4 the same in 64 x 16
-                                      columns with the z neighbours in
-                                      registers (nx a multiple of 64, ny of
-                                      16, else as 3).  1 and 2 need nx a
+                                      any grid; 4 the same in 64 x 16 or
+                                      32 x 32 columns with the z neighbours
+                                      in registers (nx a multiple of 64 and
+                                      ny of 16, or both of 32; else as 3).  1 and 2 need nx a
                                       multiple of 128 (FP32) / 64 (FP64)
                                       and ny of cg_tile_rows, else the
                                       per-phase launches run               */

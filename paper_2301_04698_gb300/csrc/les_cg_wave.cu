@@ -1,7 +1,7 @@
 // les_cg_wave.cu -- conjugate-gradient Poisson solve in one persistent
 // cooperative launch with one pass over memory and one grid-wide sum per
-// iteration, for grids whose horizontal extents are multiples of 64 x 16
-// (Sec. 2.4: L_c psi = b, compact 7-point Laplacian, periodic in x, y,
+// iteration, for grids whose horizontal extents are multiples of 64 x 16 or
+// 32 x 32 (Sec. 2.4: L_c psi = b, compact 7-point Laplacian, periodic in x, y,
 // mirror or periodic in z; mean of b removed, psi returned with zero mean).
 //
 // The iterates are those of standard CG, formed as in the one-pass kernel of
@@ -13,10 +13,11 @@
 // beta_{i+1} = r'.r' / r_i.r_i (p_{i+1}.L_c p_{i+1} expanded with L_c
 // symmetric), every vector formed from its definition.
 //
-// A block of 256 threads owns a 64 x 16 column and marches a run of planes.
+// A block of 256 threads owns a 64 x 16 (or 32 x 32) column and marches a
+// run of planes.
 // Each thread holds fixed positions of the column's plane with its halo of
-// two (68 x 20 positions: four owned nodes and two of the halo ring per
-// thread) for the whole run, so the z neighbours of both stencils are
+// two (four owned nodes and two of the halo ring per thread) for the whole
+// run, so the z neighbours of both stencils are
 // registers: per position p on the planes
 // f-2 .. f, r' on f-3 .. f-1 and r_i on f-1 .. f, where f is the plane that
 // enters the march.  Only in-plane neighbours pass through shared memory
@@ -44,35 +45,44 @@
 namespace les {
 namespace {
 
-constexpr int WX = 64, WY = 16, WH = 2;
-constexpr int SX = WX + 2 * WH, SY = WY + 2 * WH;  // a plane with its halo of two
-// staged planes in shared memory: rows of SP elements, the owned columns from
-// element 4 on (16-byte aligned rows, so whole 16-byte chunks are copied)
-constexpr int SP = WX + 8, SN = SP * SY;
-constexpr int NT = 256;                                          // threads per block
-// positions per thread: four owned nodes (x = lane + 32 (m & 1), y = warp +
-// 8 (m >> 1)) and two of the halo ring (336 positions: two rows below and
-// above, two columns left and right)
-constexpr int NO = WX * WY / NT, NR = 2 * SX * WH + 2 * WH * WY, NS = NO + (NR + NT - 1) / NT;
-static_assert(NO == 4 && NR == 336 && NS == 6, "tile and thread count");
-constexpr int D = 4;   // r_i / p_{i-1} ring: planes f .. f+3
-constexpr int DX = 6;  // x ring: planes f-2 .. f+3
+constexpr int WH = 2;   // halo of the staged planes
+constexpr int NT = 256;  // threads per block
+constexpr int D = 4;     // r_i / p_{i-1} ring: planes f .. f+3
+constexpr int DX = 6;    // x ring: planes f-2 .. f+3
+
+// A column shape: WX x WY owned nodes (64 x 16 or 32 x 32).  Staged planes
+// keep rows of SP elements with the owned columns from element 4 on (16-byte
+// aligned rows, so whole 16-byte chunks are copied).  Positions per thread:
+// four owned nodes (x = lane + 32 (m mod NWX), y = warp + 8 (m / NWX)) and
+// two of the halo ring (two rows below and above, two columns left and
+// right).
+template <int WX_, int WY_>
+struct Col {
+  static constexpr int WX = WX_, WY = WY_;
+  static constexpr int SX = WX + 2 * WH, SY = WY + 2 * WH;
+  static constexpr int SP = WX + 8, SN = SP * SY;
+  static constexpr int NWX = WX / 32, NWARP = NT / 32;
+  static constexpr int NO = WX * WY / NT, NR = 2 * SX * WH + 2 * WH * WY, NS = NO + (NR + NT - 1) / NT;
+  static_assert(NO == 4 && NS == 6 && NWARP * (NO / NWX) == WY, "column shape and thread count");
+};
+using Col64 = Col<64, 16>;
+using Col32 = Col<32, 32>;
 
 // the staging copies of a plane: owned rows in 16-byte chunks; each halo row
 // in chunks with a pair of nodes at either end; a pair at either end of each
 // owned row
-template <typename T>
+template <typename T, typename C>
 struct Copies {
-  static constexpr int V = 16 / (int)sizeof(T);      // nodes per 16-byte chunk
-  static constexpr int OC = WX * WY / V / NT;         // owned chunks per thread
-  static constexpr int RC = WX / V + 2;               // copies per halo row
-  static constexpr int NH = 2 * WH * RC + 2 * WY;     // halo copies per plane
-  static_assert(OC * V * NT == WX * WY && NH <= NT, "copy plan");
+  static constexpr int V = 16 / (int)sizeof(T);        // nodes per 16-byte chunk
+  static constexpr int OC = C::WX * C::WY / V / NT;     // owned chunks per thread
+  static constexpr int RC = C::WX / V + 2;              // copies per halo row
+  static constexpr int NH = 2 * WH * RC + 2 * C::WY;    // halo copies per plane
+  static_assert(OC * V * NT == C::WX * C::WY && NH <= NT, "copy plan");
 };
 
-template <typename T>
+template <typename T, typename C>
 size_t wave_smem() {
-  return (size_t)((2 * D + DX + 4) * SN) * sizeof(T);
+  return (size_t)((2 * D + DX + 4) * C::SN) * sizeof(T);
 }
 
 template <typename T>
@@ -143,8 +153,10 @@ __device__ __forceinline__ bool wave_sum_t0(WaveSum<T> (&d)[NV], GridSync& gs, d
   return grid_sum_t0<NV, 2>(v, gs, tot);
 }
 
-template <typename T>
+template <typename T, typename C>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs<T> f) {
+  constexpr int WX = C::WX, WY = C::WY, SX = C::SX, SP = C::SP, SN = C::SN;
+  constexpr int NO = C::NO, NR = C::NR, NS = C::NS, NWX = C::NWX, NWARP = C::NWARP;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* RINGR = reinterpret_cast<T*>(smraw);  // [D][SN] r_i as copied
   T* RINGP = RINGR + D * SN;               // [D][SN] p_{i-1} as copied
@@ -300,13 +312,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
       const int k0 = chunk * f.zrun, k1 = min(k0 + f.zrun, f.nz);
       // this thread's positions: index in a staged plane, in-plane global
       // offset; the halo slots' classes (valid, within the halo of one)
-      // (owned slots: a base plus constants, x = lane + 32 (m & 1), y = warp +
-      // 8 (m >> 1))
+      // (owned slots: a base plus constants, x = lane + 32 (m mod NWX),
+      // y = warp + 8 (m / NWX))
       int esr[NS - NO] = {};  // halo slots
       unsigned valid = (1u << NO) - 1u, in1 = (1u << NO) - 1u;
       const int go0 = (y0 + (tid >> 5)) * f.nx + x0 + (tid & 31);  // global offset of owned slot 0
       const int eo0 = ((tid >> 5) + WH) * SP + (tid & 31) + 4;      // staged index of owned slot 0
-      auto es = [&](int m) { return m < NO ? eo0 + 8 * (m >> 1) * SP + 32 * (m & 1) : esr[m - NO]; };
+      auto es = [&](int m) { return m < NO ? eo0 + NWARP * (m / NWX) * SP + 32 * (m % NWX) : esr[m - NO]; };
 #pragma unroll
       for (int m = NO; m < NS; ++m) {
         int ex, ey;
@@ -331,7 +343,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
         esr[m - NO] = (ey + WH) * SP + (ex + 4);
       }
       // this thread's staging copies (shared and in-plane global offsets)
-      using CP = Copies<T>;
+      using CP = Copies<T, C>;
       int od[CP::OC], os[CP::OC];
 #pragma unroll
       for (int j = 0; j < CP::OC; ++j) {
@@ -445,7 +457,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
                         (rw0[m] + rw2[m] - c2) * cz;
             s[0].add(rw1[m] * rw1[m]);
             s[1].add(rw1[m] * w);
-            const size_t g = base + go0 + (8 * (m >> 1)) * f.nx + 32 * (m & 1);
+            const size_t g = base + go0 + (NWARP * (m / NWX)) * f.nx + 32 * (m % NWX);
             __stcg(f.x + g, xx_[e] + ta * pw0[m]);
             __stcg(pw + g, pw0[m]);
             __stcg(ro + g, rw1[m]);
@@ -526,19 +538,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
 
 }  // namespace
 
-bool wave_cg_eligible(int nx, int ny, int nz) {
-  return nx % WX == 0 && ny % WY == 0 && nz >= 2 && (long long)nx * ny < (1LL << 31);
-}
+namespace {
 
-template <typename T>
-int poisson_solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
-                       int* iters, double* rel, std::string* err) {
-  // the staging copies move 16-byte chunks: every vector must start on a
-  // 16-byte boundary (a caller's view at an odd offset takes the one-pass
-  // kernel for any grid instead)
-  auto aligned = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
-  if (!(aligned(b) && aligned(x) && aligned(a.r) && aligned(a.q) && aligned(a.p0) && aligned(a.p1)))
-    return poisson_solve_roll<T>(a, fc, b, x, tol, maxit, iters, rel, err);
+bool col_fits(int nx, int ny, int wx, int wy) { return nx % wx == 0 && ny % wy == 0; }
+
+template <typename T, typename C>
+int solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit, int* iters,
+               double* rel, std::string* err) {
   WaveArgs<T> f;
   f.nx = a.g.nx;
   f.ny = a.g.ny;
@@ -547,8 +553,8 @@ int poisson_solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T
   f.cx = a.g.idx * a.g.idx;
   f.cy = a.g.idy * a.g.idy;
   f.cz = a.g.idz * a.g.idz;
-  f.ntx = f.nx / WX;
-  f.nty = f.ny / WY;
+  f.ntx = f.nx / C::WX;
+  f.nty = f.ny / C::WY;
   f.n = (long long)f.nx * f.ny * f.nz;
   f.b = b;
   f.x = x;
@@ -565,12 +571,12 @@ int poisson_solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T
   f.guard = a.guard;
   int per_sm = 0, dev = 0, nsm = 0;
   cudaError_t e;
-  const void* kern = (const void*)k_cg_wave<T>;
+  const void* kern = (const void*)k_cg_wave<T, C>;
+  const size_t smem = wave_smem<T, C>();
   if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
       (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wave_smem<T>())) !=
-          cudaSuccess ||
-      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, wave_smem<T>())) != cudaSuccess) {
+      (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) != cudaSuccess) {
     if (err) *err = std::string("wave CG occupancy: ") + cudaGetErrorString(e);
     return LES_ERR_CUDA;
   }
@@ -596,7 +602,7 @@ int poisson_solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T
   void* args[] = {&f};
   {
     ProfScope ps(a.prof, KI_CG_WAVE, a.st);
-    e = cudaLaunchCooperativeKernel(kern, dim3((unsigned)G), dim3(NT), args, wave_smem<T>(), a.st);
+    e = cudaLaunchCooperativeKernel(kern, dim3((unsigned)G), dim3(NT), args, smem, a.st);
   }
   if (e != cudaSuccess) {
     if (err) *err = std::string("wave CG launch: ") + cudaGetErrorString(e);
@@ -628,6 +634,28 @@ int poisson_solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T
       if (err) *err = "poisson: wave solver returned no status";
       return LES_ERR_CUDA;
   }
+}
+
+}  // namespace
+
+bool wave_cg_eligible(int nx, int ny, int nz) {
+  return (col_fits(nx, ny, Col64::WX, Col64::WY) || col_fits(nx, ny, Col32::WX, Col32::WY)) && nz >= 2 &&
+         (long long)nx * ny < (1LL << 31);
+}
+
+template <typename T>
+int poisson_solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
+                       int* iters, double* rel, std::string* err) {
+  // the staging copies move 16-byte chunks: every vector must start on a
+  // 16-byte boundary (a caller's view at an odd offset takes the one-pass
+  // kernel for any grid instead)
+  auto aligned = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+  if (!wave_cg_eligible(a.g.nx, a.g.ny, a.g.nz) ||
+      !(aligned(b) && aligned(x) && aligned(a.r) && aligned(a.q) && aligned(a.p0) && aligned(a.p1)))
+    return poisson_solve_roll<T>(a, fc, b, x, tol, maxit, iters, rel, err);
+  if (col_fits(a.g.nx, a.g.ny, Col64::WX, Col64::WY))
+    return solve_wave<T, Col64>(a, fc, b, x, tol, maxit, iters, rel, err);
+  return solve_wave<T, Col32>(a, fc, b, x, tol, maxit, iters, rel, err);
 }
 
 template int poisson_solve_wave<float>(const SolverArgs<float>&, const FusedCfg&, const float*, float*, double, int,

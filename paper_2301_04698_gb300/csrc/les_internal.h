@@ -305,8 +305,8 @@ int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, 
 template <typename T>
 int poisson_solve_roll(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
                        int* iters, double* rel, std::string* err);
-// one pass and one grid sum per iteration, 64 x 16 columns with z windows in
-// registers (nx % 64 == 0, ny % 16 == 0)
+// one pass and one grid sum per iteration, 64 x 16 or 32 x 32 columns with z
+// windows in registers (nx % 64 == 0 and ny % 16 == 0, or both % 32 == 0)
 bool wave_cg_eligible(int nx, int ny, int nz);
 template <typename T>
 int poisson_solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,

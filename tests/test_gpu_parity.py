@@ -507,11 +507,15 @@ def test_rolling_cg_matches_oracle(les_mod, precision, walls, shape):
     (32, False, (64, 32, 3), 0),        # three planes, periodic
     (32, True, (192, 48, 40), 0),       # the tile-aligned grid of a larger run
     (64, True, (64, 16, 2), 0),         # two planes between the walls
-    (32, True, (128, 16, 24), 64)])     # several z-runs per column, blocks looping
+    (32, True, (128, 16, 24), 64),      # several z-runs per column, blocks looping
+    (32, True, (160, 32, 12), 0),       # 32 x 32 columns (nx not a multiple of 64)
+    (64, False, (96, 64, 9), 0),        # 32 x 32 columns, periodic
+    (32, True, (32, 32, 5), 0),         # one 32 x 32 column
+    (32, False, (160, 160, 20), 64)])   # 32 x 32 columns, blocks looping
 def test_wave_cg_matches_oracle(les_mod, precision, walls, shape, max_blocks):
-    """The one-pass CG with 64 x 16 columns and register windows (variant 4)
-    against the FP64 oracle and the one-pass kernel of variant 3 (same
-    iterates)."""
+    """The one-pass CG with 64 x 16 or 32 x 32 columns and register windows
+    (variant 4) against the FP64 oracle and the one-pass kernel of variant 3
+    (same iterates)."""
     from oracle import Oracle
     nx, ny, nz = shape
     case = inputs.Case(name="wave", nx=nx, ny=ny, nz=nz, dx=35.0, dy=30.0, dz=10.0, walls=walls,
