@@ -552,6 +552,35 @@ def test_wave_cg_matches_oracle(les_mod, precision, walls, shape, max_blocks):
     assert rc == 0 and it == 0 and float(x.abs().max()) == 0.0
 
 
+def test_wave_cg_alignment_and_variant_range(les_mod):
+    """Vectors that do not start on a 16-byte boundary take the one-pass
+    kernel for any grid instead of the column kernel (whose staging copies
+    move 16-byte chunks), with the same solution; cg_variant outside 0..4 is
+    refused."""
+    case = inputs.Case(name="wave_al", nx=64, ny=16, nz=8, dx=35.0, dy=30.0, dz=10.0, walls=True,
+                       precision=32, init="zero", physics=())
+    sim = les_mod.Simulation(case)
+    sim.set_tuning(cg_resident=1, cg_variant=4)
+    b = torch.from_numpy(inputs.uniform(35, 0, case.n, -1, 1).reshape(case.shape) + 0.25).float().cuda()
+    out = []
+    for off, kern in ((0, "cg_wave"), (1, "cg_roll")):
+        bbuf = torch.zeros(case.n + 4, device="cuda")
+        xbuf = torch.zeros(case.n + 4, device="cuda")
+        bv = bbuf[off:off + case.n].view(case.shape)
+        xv = xbuf[off:off + case.n].view(case.shape)
+        bv.copy_(b)
+        sim.profile_reset()
+        rc, it, res = sim.poisson_solve(bv, xv, 1e-6, 2000)
+        assert rc == 0 and res <= 1e-6
+        assert _fused_launches(sim, (kern,)) == 1, off
+        out.append((it, xv.cpu().double().numpy()))
+    assert abs(out[0][0] - out[1][0]) <= 3
+    assert rel(out[0][1], out[1][1]) < 5e-4
+    with pytest.raises(les_mod.LesError):
+        sim.set_tuning(cg_variant=5)
+    sim.close()
+
+
 def test_fused_steps_fp64(les_mod):
     case = _moist_case(nx=64, ny=16, nz=16, dt=1.0)
     sim, ref, _ = pair(les_mod, case)
