@@ -9,6 +9,7 @@
 // through a run of z-planes; all loads go through the read-only path so that
 // the stencil neighbours of a tile are served from L1 / L2.  Templated on the
 // field precision T (float or double); every sum that leaves a kernel is FP64.
+#include "les_gridsync.cuh"
 #include "les_internal.h"
 
 namespace les {
@@ -449,7 +450,13 @@ __global__ void __launch_bounds__(NTHREADS)
   }
 }
 
-// ---- a8: FP64 diagnostics -------------------------------------------------------
+// ---- a8: diagnostics with FP64 totals -------------------------------------------
+// sum rho0 theta_l dV, sum rho0 q_t dV, sum rho0 u_c dV (3), kinetic energy,
+// max Courant number, max |D(rho0 u)|, non-finite values, sum rho0 q_l dV.
+// FP64 fields accumulate in FP64.  FP32 fields form each thread's sums in
+// FP32 over runs of 16 nodes, folded into compensated FP32 pairs (FP64 on
+// this GPU costs tens of FP32 operations per node), with dV applied to the
+// FP64 totals; maxima and the count in FP32.
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
     k_diag(Grid<T> g, Phys<T> ph, const T* __restrict__ u, const T* __restrict__ v,
@@ -461,37 +468,102 @@ __global__ void __launch_bounds__(NTHREADS)
 #pragma unroll
   for (int q = 0; q < LES_NDIAG; ++q) acc[q] = 0.0;
   const double dV = (double)g.dx * (double)g.dy * (double)g.dz;
-  for (long long t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-    int i, j, k0, k1;
-    tile_origin(g, t, i, j, k0, k1);
-    if (i >= g.nx || j >= g.ny) continue;
-    for (int k = k0; k < k1; ++k) {
-      const size_t m = g.lin(i, j, k);
-      const double r0 = (double)ph.rho0[k];
-      acc[0] += r0 * (double)th[m] * dV;
-      acc[1] += r0 * (double)qt[m] * dV;
-      double ke = 0.0, cfl = 0.0, div = 0.0;
+  if constexpr (sizeof(T) == 4) {
+    constexpr int NS = 7;  // the sums: 0 theta, 1 q_t, 2-4 u, 5 2 x kinetic energy, 6 q_l
+    F2 sum[NS];
+    float run[NS];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int ci = c == 0, cj = c == 1, ck = c == 2;
-        const double uc = (double)vel[c][m];
-        acc[2 + c] += r0 * uc * dV;
-        ke += uc * uc;
-        cfl += fabs(uc) * (double)g.ih(c);
-        div += ((double)g.prof(ph.rho0, k + ck) * (double)g.at(vel[c], i + ci, j + cj, k + ck, vghost(c)) -
-                (double)g.prof(ph.rho0, k - ck) * (double)g.at(vel[c], i - ci, j - cj, k - ck, vghost(c))) *
-               (0.5 * (double)g.ih(c));
+    for (int q = 0; q < NS; ++q) {
+      sum[q] = F2{0.f, 0.f};
+      run[q] = 0.f;
+    }
+    float cmax = 0.f, dmax = 0.f, bad = 0.f;
+    int cnt = 0;
+    for (long long t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+      int i, j, k0, k1;
+      tile_origin(g, t, i, j, k0, k1);
+      if (i >= g.nx || j >= g.ny) continue;
+      for (int k = k0; k < k1; ++k) {
+        const size_t m = g.lin(i, j, k);
+        const float r0 = ph.rho0[k];
+        const float uc[3] = {u[m], v[m], w[m]};
+        run[0] += r0 * th[m];
+        run[1] += r0 * qt[m];
+        float ke = 0.f, cfl = 0.f, div = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int ci = c == 0, cj = c == 1, ck = c == 2;
+          run[2 + c] += r0 * uc[c];
+          ke += uc[c] * uc[c];
+          cfl += fabsf(uc[c]) * g.ih(c);
+          div += (g.prof(ph.rho0, k + ck) * g.at(vel[c], i + ci, j + cj, k + ck, vghost(c)) -
+                  g.prof(ph.rho0, k - ck) * g.at(vel[c], i - ci, j - cj, k - ck, vghost(c))) *
+                 (0.5f * g.ih(c));
+        }
+        run[5] += r0 * ke;
+        run[6] += r0 * ql[m];
+        cmax = fmaxf(cmax, cfl * ph.dt);
+        dmax = fmaxf(dmax, fabsf(div));
+        const float vals[6] = {uc[0], uc[1], uc[2], p[m], th[m], qt[m]};
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+          if (!isfinite(vals[q])) bad += 1.f;
+        if ((++cnt & 15) == 0)
+#pragma unroll
+          for (int q = 0; q < NS; ++q) {
+            f2_acc(sum[q], run[q]);
+            run[q] = 0.f;
+          }
       }
-      acc[5] += 0.5 * r0 * ke * dV;
-      acc[6] = fmax(acc[6], cfl * (double)ph.dt);
-      acc[7] = fmax(acc[7], fabs(div));
-      const double vals[6] = {(double)u[m], (double)v[m], (double)w[m], (double)p[m], (double)th[m], (double)qt[m]};
+    }
 #pragma unroll
-      for (int q = 0; q < 6; ++q)
-        if (!isfinite(vals[q])) acc[8] += 1.0;
-      acc[9] += r0 * (double)ql[m] * dV;
+    for (int q = 0; q < NS; ++q) f2_acc(sum[q], run[q]);
+    acc[0] = f2_value(sum[0]);
+    acc[1] = f2_value(sum[1]);
+    acc[2] = f2_value(sum[2]);
+    acc[3] = f2_value(sum[3]);
+    acc[4] = f2_value(sum[4]);
+    acc[5] = 0.5 * f2_value(sum[5]);
+    acc[6] = cmax;
+    acc[7] = dmax;
+    acc[8] = bad;
+    acc[9] = f2_value(sum[6]);
+  } else {
+    for (long long t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+      int i, j, k0, k1;
+      tile_origin(g, t, i, j, k0, k1);
+      if (i >= g.nx || j >= g.ny) continue;
+      for (int k = k0; k < k1; ++k) {
+        const size_t m = g.lin(i, j, k);
+        const double r0 = (double)ph.rho0[k];
+        acc[0] += r0 * (double)th[m];
+        acc[1] += r0 * (double)qt[m];
+        double ke = 0.0, cfl = 0.0, div = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int ci = c == 0, cj = c == 1, ck = c == 2;
+          const double uc = (double)vel[c][m];
+          acc[2 + c] += r0 * uc;
+          ke += uc * uc;
+          cfl += fabs(uc) * (double)g.ih(c);
+          div += ((double)g.prof(ph.rho0, k + ck) * (double)g.at(vel[c], i + ci, j + cj, k + ck, vghost(c)) -
+                  (double)g.prof(ph.rho0, k - ck) * (double)g.at(vel[c], i - ci, j - cj, k - ck, vghost(c))) *
+                 (0.5 * (double)g.ih(c));
+        }
+        acc[5] += 0.5 * r0 * ke;
+        acc[6] = fmax(acc[6], cfl * (double)ph.dt);
+        acc[7] = fmax(acc[7], fabs(div));
+        const double vals[6] = {(double)u[m], (double)v[m], (double)w[m], (double)p[m], (double)th[m], (double)qt[m]};
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+          if (!isfinite(vals[q])) acc[8] += 1.0;
+        acc[9] += r0 * (double)ql[m];
+      }
     }
   }
+  // the cell volume, applied once per thread
+#pragma unroll
+  for (int q : {0, 1, 2, 3, 4, 5, 9}) acc[q] *= dV;
   double res[LES_NDIAG];
   if (grid_reduce<LES_NDIAG>(acc, (1u << 6) | (1u << 7), partials, &ctl->tickets[TK_DIAG], res)) {
 #pragma unroll

@@ -307,6 +307,21 @@ def test_deterministic(les_mod):
         assert np.array_equal(outs[0][f], outs[1][f]), f
 
 
+def test_fp32_diagnostics_match_oracle(les_mod):
+    """FP32 fields: the diagnostics (compensated FP32 sums into FP64 totals,
+    FP32 maxima) against the FP64 oracle's on the same state: sums to the
+    FP32 rounding of the stored values, maxima to a few FP32 ulps."""
+    case = inputs.cbl(40, 36, 48, precision=32, dt=0.5)
+    sim, ref, _ = pair(les_mod, case)
+    d, dr = sim.diagnostics(), ref.diagnostics()
+    for k in ("sum_rho_theta", "sum_rho_qt", "kinetic_energy"):
+        assert abs(d[k] - dr[k]) <= 1e-6 * abs(dr[k]), (k, d[k], dr[k])
+    for k in ("sum_rho_u", "sum_rho_v"):
+        assert abs(d[k] - dr[k]) <= 1e-6 * abs(dr[k]) + 1e-9, (k, d[k], dr[k])
+    assert abs(d["max_cfl"] - dr["max_cfl"]) <= 1e-5 * dr["max_cfl"]
+    assert d["nonfinite"] == 0.0 and dr["nonfinite"] == 0.0
+
+
 def test_nonfinite_is_reported(les_mod):
     case = inputs.tgv(8)
     st = inputs.initial_state(case)
