@@ -444,8 +444,7 @@ def main():
     barrier(world)
     t0 = time.perf_counter()
     for s in range(args.steps):
-        for k in names:
-            sim.set_from_host(k, host[k])
+        sim.set_many_from_host(host)
         sim.step(1, allow_not_converged=True)
         sim.diagnostics()
     torch.cuda.synchronize()

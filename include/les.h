@@ -198,6 +198,15 @@ int les_set_stream(les_handle *h, void *stream);
 int les_set_state(les_handle *h, int32_t field, const void *src, int32_t on_device);
 int les_get_state(les_handle *h, int32_t field, void *dst, int32_t on_device);
 
+/* les_set_state for count fields (fields[q] from srcs[q], all on the device
+ * or all on the host): every copy is enqueued before the one synchronisation
+ * that host sources need, so the uploads of a whole state follow each other
+ * on the copy engine.  LES_ERR_INVALID_ARG (and nothing copied) for a bad
+ * id, a NULL pointer or count < 0.  The paper has no counterpart: a
+ * convenience for callers that hold the state on the host. */
+int les_set_states(les_handle *h, int32_t count, const int32_t *fields, const void *const *srcs,
+                   int32_t on_device);
+
 /* Byte offset of a field's current buffer inside the workspace (buffers of
  * the scalars and u^n rotate between steps and sub-iterations). */
 int les_field_offset(les_handle *h, int32_t field, size_t *offset);

@@ -652,6 +652,20 @@ int les_set_state(les_handle* h, int32_t field, const void* src, int32_t on_devi
   return e == cudaSuccess ? LES_OK : h->cuda_fail(e, "set_state");
 }
 
+int les_set_states(les_handle* h, int32_t count, const int32_t* fields, const void* const* srcs,
+                   int32_t on_device) {
+  if (!h) return LES_ERR_INVALID_ARG;
+  if (count < 0 || (count > 0 && (!fields || !srcs))) return h->fail(LES_ERR_INVALID_ARG, "bad field list");
+  for (int q = 0; q < count; ++q)
+    if (!h->field_ptr(fields[q]) || !srcs[q]) return h->fail(LES_ERR_INVALID_ARG, "bad field id or NULL source");
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < count && e == cudaSuccess; ++q)
+    e = cudaMemcpyAsync(h->field_ptr(fields[q]), srcs[q], h->n * h->es,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->st);
+  return e == cudaSuccess ? LES_OK : h->cuda_fail(e, "set_states");
+}
+
 int les_get_state(les_handle* h, int32_t field, void* dst, int32_t on_device) {
   if (!h) return LES_ERR_INVALID_ARG;
   void* src = h->field_ptr(field);

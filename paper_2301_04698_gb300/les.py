@@ -44,7 +44,7 @@ EXPORTED = ("les_config_default", "les_workspace_bytes", "les_init", "les_destro
             "les_unet_destroy", "les_unet_set_stream", "les_unet_set_weights", "les_unet_get_weights",
             "les_unet_forward", "les_unet_loss_grad", "les_unet_train_step", "les_unet_last_error",
             "les_set_warm_model", "les_unet_set_output_scale", "les_unet_get_output_scale",
-            "les_ensemble_step")
+            "les_ensemble_step", "les_set_states")
 
 
 class LesConfig(C.Structure):
@@ -121,6 +121,8 @@ def load_library(path: str = LIB_PATH):
     lib.les_set_stream.argtypes = [vp, vp]
     lib.les_set_state.restype = C.c_int
     lib.les_set_state.argtypes = [vp, i32, vp, i32]
+    lib.les_set_states.restype = C.c_int
+    lib.les_set_states.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(vp), i32]
     lib.les_get_state.restype = C.c_int
     lib.les_get_state.argtypes = [vp, i32, vp, i32]
     lib.les_field_offset.restype = C.c_int
@@ -297,6 +299,15 @@ class Simulation:
         """Host-buffer transfer through the ABI (host pointer, synchronous)."""
         rc = self.lib.les_set_state(self.h, FIELDS[name], C.c_void_p(host.data_ptr()), 0)
         _check(self.lib, self.h, rc, f"set {name} (host)")
+
+    def set_many_from_host(self, hosts: dict) -> None:
+        """Host-buffer transfer of several fields through one ABI call (all
+        copies enqueued, one synchronisation)."""
+        names = list(hosts)
+        ids = (C.c_int32 * len(names))(*[FIELDS[k] for k in names])
+        ptrs = (C.c_void_p * len(names))(*[C.c_void_p(hosts[k].data_ptr()) for k in names])
+        rc = self.lib.les_set_states(self.h, len(names), ids, ptrs, 0)
+        _check(self.lib, self.h, rc, "set states (host)")
 
     def get_to_host(self, name: str, host) -> None:
         rc = self.lib.les_get_state(self.h, FIELDS[name], C.c_void_p(host.data_ptr()), 0)

@@ -322,6 +322,26 @@ def test_fp32_diagnostics_match_oracle(les_mod):
     assert d["nonfinite"] == 0.0 and dr["nonfinite"] == 0.0
 
 
+def test_set_states_matches_set_state(les_mod):
+    """les_set_states uploads the same values as one les_set_state per field
+    and refuses a bad field id without copying."""
+    import ctypes as C
+    case = inputs.cbl(40, 36, 24, precision=32, dt=0.5)
+    st = inputs.initial_state(case)
+    host = {k: torch.from_numpy(st[k]).float().pin_memory() for k in ("u", "v", "w", "p", "theta_l", "q_t")}
+    a, b = les_mod.Simulation(case), les_mod.Simulation(case)
+    a.set_many_from_host(host)
+    for k, h in host.items():
+        b.set_from_host(k, h)
+    for k in host:
+        assert np.array_equal(a.get(k), b.get(k)), k
+    ids = (C.c_int32 * 2)(0, 999)
+    ptrs = (C.c_void_p * 2)(C.c_void_p(host["u"].data_ptr()), C.c_void_p(host["v"].data_ptr()))
+    assert a.lib.les_set_states(a.h, 2, ids, ptrs, 0) == les_mod.LES_ERR_INVALID_ARG
+    a.close()
+    b.close()
+
+
 def test_nonfinite_is_reported(les_mod):
     case = inputs.tgv(8)
     st = inputs.initial_state(case)
