@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", default="auto", help="oracle sample: auto | full | NXxNY")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain Poisson leg")
+    ap.add_argument("--long-run", type=int, default=-1,
+                    help="steps of the untimed-in-value long-run leg from the seeded state (cbl128: 1000 by "
+                         "default, the configuration's run length; 0 skips it)")
     ap.add_argument("--warm", default="zero", choices=("zero", "prev"),
                     help="first guess of every Poisson solve of the timed workload")
     ap.add_argument("--advection", default="quick", choices=("quick", "weno3"),
@@ -470,6 +473,36 @@ def main():
                    **ev}
         del B, P, model
 
+    # ---- the configuration's full run: every step from the seeded state --------
+    # The timed steps above start from the seeded state, where the Poisson
+    # solves need about half the CG iterations of the developed flow; this leg
+    # runs the configuration's whole run length and reports its mean rate.
+    long_run = None
+    nlong = args.long_run if args.long_run >= 0 else (1000 if args.workload == "cbl128" else 0)
+    if rank == 0 and world == 1 and nlong > 0:
+        lsim = les.Simulation(case)
+        lsim.set_state(inputs.initial_state(case))
+        chunk = 50
+        done, iters_l, nc_l, ms_l = 0, 0, 0, 0.0
+        while done < nlong:
+            n = min(chunk, nlong - done)
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(lsim.stream)
+            st = lsim.step(n, allow_not_converged=True)
+            eb.record(lsim.stream)
+            eb.synchronize()
+            ms_l += ea.elapsed_time(eb)
+            iters_l += st["iters_total"]
+            nc_l += st["not_converged"]
+            done += n
+        d = lsim.diagnostics()
+        lsim.close()
+        long_run = {"steps": nlong, "value": case.n * nlong / (ms_l / 1e3), "unit": UNIT,
+                    "ms_per_step": ms_l / nlong, "iters_per_step": iters_l / nlong, "not_converged": nc_l,
+                    "nonfinite": d["nonfinite"], "max_cfl_end": d["max_cfl"],
+                    "note": "every step from the seeded state, CUDA events around chunks of 50 steps, "
+                            "no L2 flush"}
+
     # ---- CPU oracle baseline ---------------------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -498,6 +531,7 @@ def main():
                         "not_converged": nc, "warm_start": case.warm, "tol": case.tol,
                         "learned_vs_plain": learned},
             "stage_ms_per_step": stage_ms,
+            "long_run": long_run,
             "kernels": kernels,
             "wall_s_timed": wall,
         }
