@@ -448,9 +448,10 @@ def test_fused_cg_matches_oracle(les_mod, precision, walls, shape):
         assert rel(xn, x1.cpu().double().numpy()) < (1e-9 if precision == 64 else 5e-4)
 
 
-@pytest.mark.parametrize("variant,stream,kern", [(0, 0, "cg_resident"), (3, 1, "cg_roll"), (2, 1, "cg_fused")])
-def test_fused_cg_barrier_timeout_is_reported(les_mod, variant, stream, kern):
-    case = inputs.Case(name="fused", nx=128, ny=8, nz=4, dx=1.0, dy=1.0, dz=1.0, precision=32,
+@pytest.mark.parametrize("variant,stream,kern,ny", [(0, 0, "cg_resident", 8), (3, 1, "cg_roll", 8),
+                                                    (2, 1, "cg_fused", 8), (4, 1, "cg_wave", 16)])
+def test_fused_cg_barrier_timeout_is_reported(les_mod, variant, stream, kern, ny):
+    case = inputs.Case(name="fused", nx=128, ny=ny, nz=4, dx=1.0, dy=1.0, dz=1.0, precision=32,
                        init="zero", physics=())
     sim = les_mod.Simulation(case)
     sim.set_tuning(cg_resident=stream, cg_variant=variant)
