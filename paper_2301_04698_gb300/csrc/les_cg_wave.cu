@@ -35,8 +35,12 @@
 // between passes.  Per iteration each node is read three times (r_i,
 // p_{i-1}, x) and written three times (p_i, r_{i+1}, x); the halo re-reads a
 // third of r_i and p_{i-1}, mostly from L2.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 #include <string>
 
 #include "les_gridsync.cuh"
@@ -82,11 +86,16 @@ struct Copies {
 
 template <typename T, typename C>
 size_t wave_smem() {
-  return (size_t)((2 * D + DX + 4) * C::SN) * sizeof(T);
+  return ((size_t)(2 * D + 4) * C::SN + (size_t)DX * C::WX * C::WY) * sizeof(T);
 }
 
 template <typename T>
 struct WaveArgs {
+  // TMA descriptors of r[0], r[1], p[0], p[1] (boxes of a staged plane, SP x
+  // SY x 1) and x (boxes of the owned nodes, WX x WY x 1); use_tma = 0 when
+  // they could not be encoded
+  CUtensorMap tm_r[2], tm_p[2], tm_x;
+  int use_tma;
   int nx, ny, nz, walls;
   T cx, cy, cz;  // 1/dx^2, 1/dy^2, 1/dz^2
   int ntx, nty, zrun, nchunk;
@@ -153,16 +162,50 @@ __device__ __forceinline__ bool wave_sum_t0(WaveSum<T> (&d)[NV], GridSync& gs, d
   return grid_sum_t0<NV, 2>(v, gs, tot);
 }
 
+// mbarrier and TMA (cp.async.bulk.tensor) helpers
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
 template <typename T, typename C>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs<T> f) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(const __grid_constant__ WaveArgs<T> f) {
   constexpr int WX = C::WX, WY = C::WY, SX = C::SX, SP = C::SP, SN = C::SN;
   constexpr int NO = C::NO, NR = C::NR, NS = C::NS, NWX = C::NWX, NWARP = C::NWARP;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   T* RINGR = reinterpret_cast<T*>(smraw);  // [D][SN] r_i as copied
   T* RINGP = RINGR + D * SN;               // [D][SN] p_{i-1} as copied
-  T* RINGX = RINGP + D * SN;               // [DX][SN] x at the owned positions
-  T* PP = RINGX + DX * SN;                 // [2][SN] p of a plane, by plane parity
+  T* PP = RINGP + D * SN;                  // [2][SN] p of a plane, by plane parity
   T* RP = PP + 2 * SN;                     // [2][SN] r' of a plane, by plane parity
+  T* RINGX = RP + 2 * SN;                  // [DX][WY][WX] x of the owned nodes
+  // one barrier per ring slot: the TMA copies of a plane (r_i, p_{i-1}, x)
+  // complete on it; bit s of phase is the parity this thread waits for next
+  __shared__ __align__(8) uint64_t bars[D];
+  unsigned phase = 0;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < D; ++q) mbar_init(&bars[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
   __shared__ struct {
     T ta, tb, mean;
     int status, restart;
@@ -342,13 +385,16 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
         }
         esr[m - NO] = (ey + WH) * SP + (ex + 4);
       }
+      // interior columns take TMA boxes (the periodic wrap of an edge column
+      // is not a box); the others take per-thread copies
+      const bool tma = f.use_tma && x0 >= 4 && x0 + WX + 4 <= f.nx && y0 >= WH && y0 + WY + WH <= f.ny;
       // this thread's staging copies (shared and in-plane global offsets)
       using CP = Copies<T, C>;
       int od[CP::OC], os[CP::OC];
 #pragma unroll
       for (int j = 0; j < CP::OC; ++j) {
         const int c = tid + j * NT, ey = c / (WX / CP::V), ex = (c % (WX / CP::V)) * CP::V;
-        od[j] = (ey + WH) * SP + ex + 4;
+        od[j] = (ey + WH) * SP + ex + 4;  // in a staged plane; x rows are dense: ey WX + ex
         os[j] = (y0 + ey) * f.nx + x0 + ex;
       }
       int hd = 0, hs = 0, hk = 0;  // halo copy: kind 0 none, 1 a pair of nodes, 2 a chunk
@@ -371,19 +417,32 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
       // plane kk of r_i, p_{i-1} (every position) and of x (owned positions,
       // planes of the run) into their ring slots; one commit group per plane
       auto fetch = [&](int kk) {
-        const size_t base = (size_t)zmapw(kk, f.nz, f.walls) * plane;
-        T* rr_ = RINGR + ((kk + 2 * D) % D) * SN;
-        T* pp_ = RINGP + ((kk + 2 * D) % D) * SN;
-        T* xx_ = RINGX + ((kk + 2 * DX) % DX) * SN;
+        const int zs = zmapw(kk, f.nz, f.walls);
+        const size_t base = (size_t)zs * plane;
+        const int slot = (kk + 2 * D) % D;
+        T* rr_ = RINGR + slot * SN;
+        T* pp_ = RINGP + slot * SN;
+        T* xx_ = RINGX + ((kk + 2 * DX) % DX) * (WX * WY);
+        const bool xrun = kk >= k0 && kk < k1;
+        if (tma) {
+          if (tid == 0) {
+            const unsigned bytes = (unsigned)((first ? 1 : 2) * SN * sizeof(T) + (xrun ? WX * WY * sizeof(T) : 0));
+            mbar_expect_tx(&bars[slot], bytes);
+            tma_load_3d(rr_, &f.tm_r[iter & 1], x0 - 4, y0 - WH, zs, &bars[slot]);
+            if (!first) tma_load_3d(pp_, &f.tm_p[(iter + 1) & 1], x0 - 4, y0 - WH, zs, &bars[slot]);
+            if (xrun) tma_load_3d(xx_, &f.tm_x, x0, y0, kk, &bars[slot]);
+          }
+          return;
+        }
         const T* rs = ri + base;
         const T* ps = pold + base;
         const T* xs = f.x + base;
-        const bool xrun = kk >= k0 && kk < k1;
 #pragma unroll
         for (int j = 0; j < CP::OC; ++j) {
+          const int c = tid + j * NT;
           cp_async_bytes<16>(rr_ + od[j], rs + os[j]);
           if (!first) cp_async_bytes<16>(pp_ + od[j], ps + os[j]);
-          if (xrun) cp_async_bytes<16>(xx_ + od[j], xs + os[j]);
+          if (xrun) cp_async_bytes<16>(xx_ + (c / (WX / CP::V)) * WX + (c % (WX / CP::V)) * CP::V, xs + os[j]);
         }
         if (hk == 2) {
           cp_async_bytes<16>(rr_ + hd, rs + hs);
@@ -402,9 +461,24 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
       __syncthreads();  // the previous column's readers are done with every buffer
       for (int kk = k0 - 2; kk < k0 - 2 + D - 1; ++kk) fetch(kk);
       int cnt = 0;
+      // wait (bounded) for the TMA copies of plane kk; a wait that runs out
+      // raises the grid's fail flag, so every grid sum of the launch fails
+      auto wait_plane = [&](int kk) {
+        const int slot = (kk + 2 * D) % D;
+        const long long t0 = clock64();
+        unsigned spins = 0;
+        while (!mbar_try_wait(&bars[slot], (phase >> slot) & 1u)) {
+          if ((++spins & 63u) == 0u && (ld_volatile(&f.bar->fail.v) != 0u || clock64() - t0 > f.spin_cycles)) {
+            atomicExch(&f.bar->fail.v, 1u);
+            break;
+          }
+        }
+        phase ^= 1u << slot;
+      };
       for (int fp = k0 - 2; fp <= k1 + 1; ++fp) {
-        // plane fp has landed: the D - 2 later copy groups may still fly
-        cp_wait<D - 2>();
+        // plane fp has landed: the later copies may still fly
+        if (tma) wait_plane(fp);
+        else cp_wait<D - 2>();
         __syncthreads();
         // the slot of plane fp - 1 is free (its r_i is held in registers)
         fetch(fp + D - 1);
@@ -447,7 +521,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
         if (fp >= k0 + 2) {
           const int k = fp - 2;
           const T* rc = RP + (k & 1) * SN;
-          const T* xx_ = RINGX + ((k + 2 * DX) % DX) * SN;
+          const T* xx_ = RINGX + ((k + 2 * DX) % DX) * (WX * WY);
           const size_t base = (size_t)k * plane;
 #pragma unroll
           for (int m = 0; m < NO; ++m) {
@@ -458,7 +532,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
             s[0].add(rw1[m] * rw1[m]);
             s[1].add(rw1[m] * w);
             const size_t g = base + go0 + (NWARP * (m / NWX)) * f.nx + 32 * (m % NWX);
-            __stcg(f.x + g, xx_[e] + ta * pw0[m]);
+            __stcg(f.x + g, xx_[((tid >> 5) + NWARP * (m / NWX)) * WX + (tid & 31) + 32 * (m % NWX)] + ta * pw0[m]);
             __stcg(pw + g, pw0[m]);
             __stcg(ro + g, rw1[m]);
           }
@@ -476,6 +550,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(WaveArgs
           ra0[m] = ra1[m];
         }
       }
+      // the copies issued beyond the run (planes k1 + 2 .. k1 + D) land
+      // before the buffers are used again
+      if (tma)
+        for (int kk = k1 + 2; kk <= k1 + D; ++kk) wait_plane(kk);
       cp_wait<0>();
     }
     double t[4];
@@ -542,6 +620,40 @@ namespace {
 
 bool col_fits(int nx, int ny, int wx, int wy) { return nx % wx == 0 && ny % wy == 0; }
 
+// cuTensorMapEncodeTiled from the driver, looked up once
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::mutex mu;
+  static bool tried = false;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// a 3-D map of an nx x ny x nz vector with bx x by x 1 boxes (no swizzle,
+// no interleave; out-of-range elements are never requested)
+template <typename T>
+bool encode_map(CUtensorMap* m, const void* base, int nx, int ny, int nz, int bx, int by) {
+  const auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(T), (cuuint64_t)nx * ny * sizeof(T)};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  return enc(m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+             const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename T, typename C>
 int solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit, int* iters,
                double* rel, std::string* err) {
@@ -569,6 +681,13 @@ int solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, dou
   f.maxit = maxit;
   f.spin_cycles = fc.spin_cycles;
   f.guard = a.guard;
+  // TMA boxes for the interior columns: a staged plane of r and p_{i-1}
+  // (SP x SY, from x0 - 4), the owned nodes of x (WX x WY)
+  f.use_tma = encode_map<T>(&f.tm_r[0], a.r, f.nx, f.ny, f.nz, C::SP, C::SY) &&
+              encode_map<T>(&f.tm_r[1], a.q, f.nx, f.ny, f.nz, C::SP, C::SY) &&
+              encode_map<T>(&f.tm_p[0], a.p0, f.nx, f.ny, f.nz, C::SP, C::SY) &&
+              encode_map<T>(&f.tm_p[1], a.p1, f.nx, f.ny, f.nz, C::SP, C::SY) &&
+              encode_map<T>(&f.tm_x, x, f.nx, f.ny, f.nz, C::WX, C::WY);
   int per_sm = 0, dev = 0, nsm = 0;
   cudaError_t e;
   const void* kern = (const void*)k_cg_wave<T, C>;

@@ -575,11 +575,15 @@ def test_rolling_cg_matches_oracle(les_mod, precision, walls, shape):
     (32, True, (160, 32, 12), 0),       # 32 x 32 columns (nx not a multiple of 64)
     (64, False, (96, 64, 9), 0),        # 32 x 32 columns, periodic
     (32, True, (32, 32, 5), 0),         # one 32 x 32 column
-    (32, False, (160, 160, 20), 64)])   # 32 x 32 columns, blocks looping
+    (32, False, (160, 160, 20), 64),    # 32 x 32 columns, blocks looping
+    (32, True, (320, 64, 12), 0),       # six interior 64 x 16 columns: TMA-staged planes
+    (64, False, (160, 96, 10), 0),      # interior 32 x 32 columns, FP64 boxes
+    (32, False, (384, 64, 16), 64)])    # TMA and per-thread columns mixed in each block
 def test_wave_cg_matches_oracle(les_mod, precision, walls, shape, max_blocks):
     """The one-pass CG with 64 x 16 or 32 x 32 columns and register windows
-    (variant 4) against the FP64 oracle and the one-pass kernel of variant 3
-    (same iterates)."""
+    (variant 4; interior columns staged by TMA boxes, edge columns by
+    per-thread copies) against the FP64 oracle and the one-pass kernel of
+    variant 3 (same iterates)."""
     from oracle import Oracle
     nx, ny, nz = shape
     case = inputs.Case(name="wave", nx=nx, ny=ny, nz=nz, dx=35.0, dy=30.0, dz=10.0, walls=walls,
