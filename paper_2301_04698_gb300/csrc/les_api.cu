@@ -623,10 +623,10 @@ int les_init(const les_config* cfg, const double* rho0_z, void* workspace, size_
       else ((float*)host.data())[q * cfg->nz + k] = (float)v[q];
     }
   }
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(h->ws, 0, L.total, h->st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(h->profiles, host.data(), host.size(), cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(h->st)) != cudaSuccess) {
+  // no handle survives a failure here, so only the status reports it
+  if (cudaMemsetAsync(h->ws, 0, L.total, h->st) != cudaSuccess ||
+      cudaMemcpyAsync(h->profiles, host.data(), host.size(), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+      cudaStreamSynchronize(h->st) != cudaSuccess) {
     delete h;
     return LES_ERR_CUDA;
   }

@@ -14,18 +14,18 @@
 // symmetric), every vector formed from its definition.
 //
 // A block of 256 threads owns a 64 x 16 (or 32 x 32) column and marches a
-// run of planes.
-// Each thread holds fixed positions of the column's plane with its halo of
-// two (four owned nodes and two of the halo ring per thread) for the whole
-// run, so the z neighbours of both stencils are
-// registers: per position p on the planes
-// f-2 .. f, r' on f-3 .. f-1 and r_i on f-1 .. f, where f is the plane that
-// enters the march.  Only in-plane neighbours pass through shared memory
-// (one plane of p and one of r', each double-buffered by plane parity); the
-// planes of r_i and p_{i-1} (halo two) and of x (owned nodes) arrive through
-// rings that cp.async fills three planes ahead, in 16-byte chunks (and pairs
-// of nodes at the halo's x ends).  Per plane step, after one
-// block barrier:
+// run of planes.  Each thread holds fixed positions of the column's plane
+// with its halo of two (four owned nodes and two of the halo ring per
+// thread) for the whole run, so the z neighbours of both stencils are
+// registers: per position p on the planes f-2 .. f, r' on f-3 .. f-1 and r_i
+// on f-1 .. f, where f is the plane that enters the march.  Only in-plane
+// neighbours pass through shared memory (one plane of p and one of r', each
+// double-buffered by plane parity).  The planes of r_i and p_{i-1} (halo
+// two) and of x (owned nodes) arrive through rings filled three planes
+// ahead: for an interior column as TMA boxes completing on one mbarrier per
+// ring slot, for a column at a periodic edge (whose wrap is not a box) as
+// per-thread cp.async copies of 16-byte chunks and node pairs.  Per plane
+// step, after one block barrier:
 //   A  p(f) = r(f) + beta p_old(f) at every position
 //   B  q(f-1) = L_c p, r'(f-1) = r(f-1) - alpha q(f-1) within the halo of one
 //   C  w(f-2) = L_c r' at the owned positions
