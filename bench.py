@@ -445,15 +445,28 @@ def main():
     h2d = sum(h.numel() * h.element_size() for h in host.values())
     torch.cuda.synchronize()
     barrier(world)
+    # each call returns after its own synchronisation, so host clocks around
+    # the three calls split the step's wall time without adding a sync
+    parts = [0.0, 0.0, 0.0]  # upload, step, diagnostics read-back
     t0 = time.perf_counter()
     for s in range(args.steps):
+        ta = time.perf_counter()
         sim.set_many_from_host(host)
+        tb = time.perf_counter()
         sim.step(1, allow_not_converged=True)
+        tc = time.perf_counter()
         sim.diagnostics()
+        td = time.perf_counter()
+        parts[0] += tb - ta
+        parts[1] += tc - tb
+        parts[2] += td - tc
     torch.cuda.synchronize()
     e2e_s = allmax(world, time.perf_counter() - t0)
     e2e = {"value": world * case.n * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": les.NDIAG * 8}
+           "d2h_bytes_per_step": les.NDIAG * 8,
+           "ms_per_step": {"upload": 1e3 * parts[0] / args.steps, "step": 1e3 * parts[1] / args.steps,
+                           "diagnostics": 1e3 * parts[2] / args.steps},
+           "h2d_gbs": h2d * args.steps / max(parts[0], 1e-12) / 1e9}
 
     # ---- Poisson ms/step at a fixed residual: learned vs plain first guesses ----
     learned = None
