@@ -127,22 +127,34 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """nvidia-smi clock / throttle sampling during the timed region.  The
+    sampler is started, and its first sample awaited, before the region;
+    mark() brackets the region and stop() keeps the samples stamped inside
+    it (or the one nearest to it when the region is shorter than the
+    sampling interval)."""
 
     def __init__(self, gpu_index: int):
         self.proc = None
+        self.t = [None, None]
         self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
                                  f".clocks_{os.getpid()}.csv")
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t_end = time.time() + 5.0
+        while time.time() < t_end and os.path.getsize(self.path) == 0 and self.proc.poll() is None:
+            time.sleep(0.02)
+
+    def mark(self, which: int) -> None:
+        self.t[which] = time.time()
 
     def stop(self):
         if self.proc is None:
@@ -153,13 +165,15 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.fh.close()
+        import datetime
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
         try:
@@ -168,11 +182,18 @@ class Clocks:
             pass
         if not rows:
             return None
-        sm = [r[0] for r in rows]
-        mx = max(r[1] for r in rows)
+        t0, t1 = self.t
+        inside = [r for r in rows if t0 is not None and t1 is not None and t0 <= r[0] <= t1]
+        if not inside and t0 is not None and t1 is not None:
+            mid = 0.5 * (t0 + t1)
+            inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+        use = inside or rows
+        sm = [r[1] for r in use]
+        mx = max(r[2] for r in use)
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({names[i] for r in use for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(use),
+                "samples_in_region": len([r for r in use if t0 is not None and t1 is not None and t0 <= r[0] <= t1])}
 
 
 def src_hash() -> str:
@@ -287,6 +308,7 @@ def bench_ensemble(args, rank, world, local):
     total_s = 0.0
     iters = 0
     barrier(world)
+    clocks.mark(0)
     for s in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
@@ -295,6 +317,7 @@ def bench_ensemble(args, rank, world, local):
         torch.cuda.synchronize()
         total_s += time.perf_counter() - t0
         iters += sum(x["iters_total"] for x in st)
+    clocks.mark(1)
     barrier(world)
     clk = clocks.stop()
     total_s = allmax(world, total_s)
@@ -376,6 +399,7 @@ def main():
     nc = 0
     barrier(world)
     torch.cuda.synchronize()
+    clocks.mark(0)
     wall0 = time.perf_counter()
     with torch.cuda.stream(stream):
         for s in range(args.steps):
@@ -387,6 +411,7 @@ def main():
             nc += r["not_converged"]
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    clocks.mark(1)
     barrier(world)
     clk = clocks.stop()
     dev_ms = sum(a.elapsed_time(b) for a, b in ev)
