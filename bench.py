@@ -4,23 +4,30 @@
 A step is one full time step of the iterative predictor-corrector scheme:
 thermodynamics, K = 3 sub-iterations of (scalar predictor, momentum predictor
 and Poisson right side, Poisson solve, correction).  Default workload: the
-moist capped boundary layer on 128 x 128 x 96 nodes, dx = 35 m, dz = 10 m,
-FP32 fields with FP64 reductions, CG to 1e-6 relative residual.
+largest single-GPU configuration, the dry Taylor-Green box tiled to
+1536 x 1536 x 256 nodes (604 M cells), FP32 fields with FP64 reductions, CG to
+1e-6 relative residual.
 
 Legs of one run:
   value    device time of exactly --steps steps (CUDA events on the library's
            stream; L2 flushed by a 256 MiB write before every timed step,
-           outside the events), inputs resident in HBM;
-  e2e      the same steps through the C ABI with host buffers: every step
-           uploads the state from pinned host memory and reads the FP64
-           diagnostics back;
+           outside the events; the large workload's fields are each larger
+           than L2 anyway), inputs resident in HBM;
+  e2e      steps through the C ABI with host buffers: every step uploads the
+           state from pinned host memory and reads the FP64 diagnostics back;
   roofline the kernel with the largest share of device time in a profiled
            pass of the same steps (event pair around every launch):
-           algorithmic bytes per launch / mean launch time vs measured HBM peak;
+           algorithmic bytes per launch / mean launch time vs measured HBM
+           peak; every kernel's fraction is in `kernels`;
+  second_record  the moist capped boundary layer 128 x 128 x 96 (its rate over
+           --steps steps and over its whole 1000-step run from the seeded
+           state);
   cpu_baseline (rank 0, N = 1) the FP64 oracle on a bounded sample.
 --impl reference times the oracle alone (the reference arm of this build).
-Under torchrun each rank runs an independent replica (different seed): weak
-scaling with no collective on the data path; timing is max over ranks.
+--poisson-only times single Poisson solves on a chosen grid (for profiling a
+CG kernel).  Under torchrun each rank runs an independent replica (different
+seed): weak scaling with no collective on the data path; timing is max over
+ranks.
 """
 from __future__ import annotations
 
@@ -31,6 +38,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -70,7 +78,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", default="cbl128", choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--workload", default="tgv_large", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", default="auto", help="oracle sample: auto | full | NXxNY")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain Poisson leg")
@@ -84,6 +92,21 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="ensemble workload: keep the default tuning")
     ap.add_argument("--learned-seeds", type=int, default=20, help="training runs for the learned leg")
     ap.add_argument("--learned-train-steps", type=int, default=1500)
+    ap.add_argument("--no-second-record", action="store_true",
+                    help="skip the 128x128x96 capped-boundary-layer record")
+    ap.add_argument("--aux-steps", type=int, default=-1,
+                    help="steps of the stage-breakdown, profiled and end-to-end legs (default: --steps, at most 3 / "
+                         "3 / 5 on grids above 100 M cells)")
+    # single Poisson solves (profiling a CG kernel)
+    ap.add_argument("--poisson-only", action="store_true",
+                    help="time single Poisson solves of a seeded right side instead of steps")
+    ap.add_argument("--grid", default="512x512x64", help="--poisson-only grid NXxNYxNZ (walls in z)")
+    ap.add_argument("--variant", type=int, default=0, help="--poisson-only: les_tuning.cg_variant")
+    ap.add_argument("--resident", type=int, default=1,
+                    help="--poisson-only: les_tuning.cg_resident (0: on chip when the grid fits)")
+    ap.add_argument("--iters", type=int, default=20, help="--poisson-only: CG iterations (tolerance unreachable)")
+    ap.add_argument("--repeat", type=int, default=2, help="--poisson-only: solves")
+    ap.add_argument("--fp64", action="store_true", help="--poisson-only: FP64 fields")
     return ap.parse_args()
 
 
@@ -136,8 +159,8 @@ class Clocks:
     def __init__(self, gpu_index: int):
         self.proc = None
         self.t = [None, None]
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                                 f".clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="les_clocks_", suffix=".csv")
+        os.close(fd)
         q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -221,23 +244,26 @@ def traffic_for(kernel: str, workload_name: str):
 
 
 # ---------------------------------------------------------------------------
-def oracle_sample(case, args, budget=2.0e6):
+def oracle_sample(case, args, budget=2.0e6, side=None):
     """A bounded sample of the workload for the FP64 oracle: the same physics
     on the full column height over a horizontal sub-domain of at most
-    `budget` cells."""
+    `budget` cells (or `side` x `side` columns).  Sides are halved from the
+    full grid, so a Taylor-Green tiling keeps whole periods."""
     if args.cpu_sample == "full":
         return case, "full domain"
     if args.cpu_sample not in ("auto",):
         sx, sy = (int(v) for v in args.cpu_sample.lower().split("x"))
+    elif side is not None:
+        sx, sy = min(side, case.nx), min(side, case.ny)
     else:
-        sx = sy = case.nx
+        sx, sy = case.nx, case.ny
         while sx * sy * case.nz > budget and sx > 16:
             sx //= 2
             sy //= 2
     if sx == case.nx and sy == case.ny:
         return case, "full domain"
     sub = case.replace(nx=sx, ny=sy, name=case.name + f"_sub{sx}x{sy}")
-    return sub, f"{sx}x{sy}x{case.nz} horizontal sub-domain of the same workload"
+    return sub, f"{sx}x{sy}x{case.nz} horizontal sub-domain (full columns) of the same workload"
 
 
 def time_oracle(case, steps: int, warm: int):
@@ -265,8 +291,13 @@ def reference_arm(args, rank, world):
         case = case.replace(warm=args.warm)
     if args.advection != case.advection:
         case = case.replace(advection=args.advection)
-    # each of the W + K oracle steps is a ~0.4 M-cell sample so the arm ends in minutes
-    sample, desc = oracle_sample(case, args, budget=4.0e5)
+    # each of the W + K oracle steps is a bounded sample so the arm ends in
+    # minutes: 64 x 64 full columns of the large box (1 M cells), ~0.4 M cells
+    # of the others
+    if case.n > 1e8:
+        sample, desc = oracle_sample(case, args, side=64)
+    else:
+        sample, desc = oracle_sample(case, args, budget=4.0e5)
     val, secs = time_oracle(sample, args.steps, args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
@@ -278,6 +309,39 @@ def reference_arm(args, rank, world):
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def poisson_only(args):
+    """Single Poisson solves of a seeded uniform right side through the public
+    API (Sec. 2.4: L_c psi = b, CG), one JSON line per solve: iterations, the
+    relative residual reached and the CUDA-event time.  Walls in z; the
+    tolerance is unreachable so every solve runs --iters iterations."""
+    import torch
+
+    from paper_2301_04698_gb300 import build as B
+    from paper_2301_04698_gb300 import inputs, les
+    B.build()
+    les.load_library()
+    nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
+    prec = 64 if args.fp64 else 32
+    case = inputs.Case(name="poisson", nx=nx, ny=ny, nz=nz, dx=35.0, dy=35.0, dz=10.0, walls=True,
+                       precision=prec, init="zero", physics=())
+    sim = les.Simulation(case)
+    sim.set_tuning(cg_variant=args.variant, cg_resident=args.resident)
+    dt = torch.float64 if prec == 64 else torch.float32
+    b = torch.from_numpy(inputs.uniform(1, 0, case.n, -1, 1).reshape(case.shape)).to("cuda", dt)
+    for _ in range(args.repeat):
+        x = torch.zeros_like(b)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        rc, it, rel = sim.poisson_solve(b, x, 1e-30, args.iters, allow_not_converged=True)
+        t1.record()
+        t1.synchronize()
+        print(json.dumps({"grid": [nx, ny, nz], "precision": prec, "variant": args.variant,
+                          "resident": args.resident, "iters": it, "rel": rel, "ms": t0.elapsed_time(t1)}),
+              flush=True)
+    sim.close()
     return 0
 
 
@@ -351,15 +415,98 @@ def bench_ensemble(args, rank, world, local):
     return 0
 
 
+def timed_steps(sim, case, steps, flush, stream, world, local):
+    """Exactly `steps` steps bracketed by CUDA events on the library's stream,
+    L2 flushed before each (outside the events); clocks sampled meanwhile."""
+    import torch
+    launches0 = sim.launch_count()
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    iters = nc = 0
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.mark(0)
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for s in range(steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            r = sim.step(1, allow_not_converged=True)
+            ev[s][1].record(stream)
+            iters += r["iters_total"]
+            nc += r["not_converged"]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks.mark(1)
+    barrier(world)
+    clk = clocks.stop()
+    dev_ms = allmax(world, sum(a.elapsed_time(b) for a, b in ev))
+    return {"dev_ms": dev_ms, "iters": iters, "not_converged": nc, "wall": wall, "clocks": clk,
+            "launches": sim.launch_count() - launches0}
+
+
+def long_run(case, nlong, chunk=50):
+    """The configuration's whole run from the seeded state, CUDA events around
+    chunks of steps (no L2 flush): mean cell-steps/s and CG iterations."""
+    import torch
+
+    from paper_2301_04698_gb300 import inputs, les
+    lsim = les.Simulation(case)
+    lsim.set_state(inputs.initial_state(case))
+    done, iters_l, nc_l, ms_l = 0, 0, 0, 0.0
+    while done < nlong:
+        n = min(chunk, nlong - done)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(lsim.stream)
+        st = lsim.step(n, allow_not_converged=True)
+        eb.record(lsim.stream)
+        eb.synchronize()
+        ms_l += ea.elapsed_time(eb)
+        iters_l += st["iters_total"]
+        nc_l += st["not_converged"]
+        done += n
+    d = lsim.diagnostics()
+    lsim.close()
+    return {"steps": nlong, "value": case.n * nlong / (ms_l / 1e3), "unit": UNIT, "ms_per_step": ms_l / nlong,
+            "iters_per_step": iters_l / nlong, "not_converged": nc_l, "nonfinite": d["nonfinite"],
+            "max_cfl_end": d["max_cfl"],
+            "note": f"every step from the seeded state, CUDA events around chunks of {chunk} steps, no L2 flush"}
+
+
+def second_record(args, rank, world, local, flush):
+    """The moist capped boundary layer (128 x 128 x 96, FP32): its rate over
+    the timed steps after the warm-up, and over its whole 1000-step run."""
+    import torch
+
+    from paper_2301_04698_gb300 import inputs, les
+    case = workload("cbl128", seed=1 + rank)
+    sim = les.Simulation(case)
+    sim.set_state(inputs.initial_state(case))
+    with torch.cuda.stream(sim.stream):
+        for _ in range(args.warmup):
+            sim.step(1, allow_not_converged=True)
+    torch.cuda.synchronize()
+    steps = max(args.steps, 10)
+    t = timed_steps(sim, case, steps, flush, sim.stream, world, local)
+    sim.close()
+    rec = {"workload": WORKLOAD_DESC["cbl128"], "steps": steps, "warmup": args.warmup,
+           "value": world * case.n * steps / (t["dev_ms"] / 1e3), "unit": UNIT,
+           "ms_per_step": t["dev_ms"] / steps, "iters_per_step": t["iters"] / steps}
+    if world == 1 and args.long_run != 0:
+        rec["long_run"] = long_run(case, args.long_run if args.long_run > 0 else 1000)
+    return rec
+
+
 def main():
     args = parse()
+    if args.poisson_only:
+        return poisson_only(args)
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         rc = reference_arm(args, rank, world)
         barrier(world)
         return rc
 
-    import numpy as np
     import torch
 
     from paper_2301_04698_gb300 import build as B
@@ -377,9 +524,14 @@ def main():
         case = case.replace(warm=args.warm)
     if args.advection != case.advection:
         case = case.replace(advection=args.advection)
+    big = case.n > 1e8
+    aux = args.aux_steps if args.aux_steps > 0 else None
+    aux_prof = aux or (min(args.steps, 3) if big else args.steps)
+    aux_e2e = aux or (min(args.steps, 5) if big else args.steps)
     st0 = inputs.initial_state(case)
     sim = les.Simulation(case)
     sim.set_state(st0)
+    del st0
     stream = sim.stream
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
 
@@ -392,31 +544,8 @@ def main():
     snap = {k: sim.view(k).clone() for k in names}
 
     # ---- timed region: exactly --steps steps ------------------------------
-    launches0 = sim.launch_count()
-    clocks = Clocks(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    iters = 0
-    nc = 0
-    barrier(world)
-    torch.cuda.synchronize()
-    clocks.mark(0)
-    wall0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for s in range(args.steps):
-            flush.zero_()
-            ev[s][0].record(stream)
-            r = sim.step(1, allow_not_converged=True)
-            ev[s][1].record(stream)
-            iters += r["iters_total"]
-            nc += r["not_converged"]
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    clocks.mark(1)
-    barrier(world)
-    clk = clocks.stop()
-    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
-    dev_ms = allmax(world, dev_ms)
-    launches = sim.launch_count() - launches0
+    t = timed_steps(sim, case, args.steps, flush, stream, world, local)
+    dev_ms = t["dev_ms"]
     value = world * case.n * args.steps / (dev_ms / 1e3)
 
     # ---- stage breakdown (Poisson ms / step) -------------------------------
@@ -425,7 +554,7 @@ def main():
     stage_ms = {"begin": 0.0, "scalar": 0.0, "momentum": 0.0, "solve": 0.0, "correct": 0.0}
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
-        for s in range(args.steps):
+        for s in range(aux_prof):
             flush.zero_()
             for stg in ["begin"] + ["scalar", "momentum", "solve", "correct"] * case.K + ["end"]:
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -435,7 +564,7 @@ def main():
                 b.synchronize()
                 if stg in stage_ms:
                     stage_ms[stg] += a.elapsed_time(b)
-    stage_ms = {k: v / args.steps for k, v in stage_ms.items()}
+    stage_ms = {k: v / aux_prof for k, v in stage_ms.items()}
 
     # ---- per-kernel profile of the same steps -------------------------------
     for k in names:
@@ -444,7 +573,7 @@ def main():
     sim.profile(True)
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
-        for s in range(args.steps):
+        for s in range(aux_prof):
             flush.zero_()
             sim.step(1, allow_not_converged=True)
     kstats = sim.profile_read()
@@ -459,14 +588,19 @@ def main():
                 "share": top["total_ms"] / total_k, "mean_launch_us": mean_ms * 1e3,
                 "bytes_per_launch": top["bytes_per_launch"], "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "frac_of_8tbs": achieved / 8000.0}
-    kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 4),
-                           "share": round(k["total_ms"] / total_k, 4),
-                           "gbs": round(k["bytes_per_launch"] / (k["total_ms"] / max(k["timed"], 1) / 1e3) / 1e9, 1)
-                           if k["total_ms"] > 0 else None} for k in kstats}
+                "frac_of_8tbs": achieved / 8000.0, "profiled_steps": aux_prof}
+    kernels = {}
+    for k in kstats:
+        mean = k["total_ms"] / max(k["timed"], 1)
+        gbs = k["bytes_per_launch"] / (mean / 1e3) / 1e9 if k["total_ms"] > 0 else None
+        kernels[k["name"]] = {"launches": k["launches"], "ms": round(k["total_ms"], 4),
+                              "share": round(k["total_ms"] / total_k, 4), "mean_us": round(mean * 1e3, 2),
+                              "gbs": round(gbs, 1) if gbs else None,
+                              "frac": round(gbs / hbm, 4) if gbs else None}
 
     # ---- end to end through the C ABI with host buffers ----------------------
     host = {k: snap[k].cpu().pin_memory() for k in names}
+    del snap
     h2d = sum(h.numel() * h.element_size() for h in host.values())
     torch.cuda.synchronize()
     barrier(world)
@@ -474,10 +608,10 @@ def main():
     # the three calls split the step's wall time without adding a sync
     parts = [0.0, 0.0, 0.0]  # upload, step, diagnostics read-back
     e2e_iters = 0
-    eva = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    evb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    eva = [torch.cuda.Event(enable_timing=True) for _ in range(aux_e2e)]
+    evb = [torch.cuda.Event(enable_timing=True) for _ in range(aux_e2e)]
     t0 = time.perf_counter()
-    for s in range(args.steps):
+    for s in range(aux_e2e):
         ta = time.perf_counter()
         sim.set_many_from_host(host)
         tb = time.perf_counter()
@@ -493,66 +627,54 @@ def main():
         parts[2] += td - tc
     torch.cuda.synchronize()
     e2e_s = allmax(world, time.perf_counter() - t0)
-    e2e = {"value": world * case.n * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": les.NDIAG * 8,
-           "ms_per_step": {"upload": 1e3 * parts[0] / args.steps, "step": 1e3 * parts[1] / args.steps,
-                           "diagnostics": 1e3 * parts[2] / args.steps,
-                           "step_on_device": sum(x.elapsed_time(y) for x, y in zip(eva, evb)) / args.steps},
-           "h2d_gbs": h2d * args.steps / max(parts[0], 1e-12) / 1e9,
-           "iters_per_step": e2e_iters / args.steps}
+    e2e = {"value": world * case.n * aux_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": les.NDIAG * 8, "steps": aux_e2e,
+           "ms_per_step": {"upload": 1e3 * parts[0] / aux_e2e, "step": 1e3 * parts[1] / aux_e2e,
+                           "diagnostics": 1e3 * parts[2] / aux_e2e,
+                           "step_on_device": sum(x.elapsed_time(y) for x, y in zip(eva, evb)) / aux_e2e},
+           "h2d_gbs": h2d * aux_e2e / max(parts[0], 1e-12) / 1e9,
+           "iters_per_step": e2e_iters / aux_e2e}
+    del host
+    sim.close()
+    del flush
+    torch.cuda.empty_cache()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
     # ---- Poisson ms/step at a fixed residual: learned vs plain first guesses ----
     learned = None
     if rank == 0 and not args.no_learned:
         from paper_2301_04698_gb300 import learned as L
         t0 = time.perf_counter()
-        B, P = L.generate_pairs(list(range(100, 100 + args.learned_seeds)), 50, n=32)
+        Bp, Pp = L.generate_pairs(list(range(100, 100 + args.learned_seeds)), 50, n=32)
         nval = 16
         model = les.UNet(32, max_batch=16)
         model.set_weights(L.init_weights(0))
-        model.out_scale = L.output_scale(B[nval:], P[nval:])
-        hist, t_train = L.train(model, B[nval:], P[nval:], steps=args.learned_train_steps, batch=16)
+        model.out_scale = L.output_scale(Bp[nval:], Pp[nval:])
+        hist, t_train = L.train(model, Bp[nval:], Pp[nval:], steps=args.learned_train_steps, batch=16)
         ev = L.evaluate(model, [1, 2], steps=10, n=32, tol=1e-6)
         learned = {"workload": "Taylor-Green 32^3, FP64, K=3, CG to 1e-6 relative residual, held-out seeds 1-2",
-                   "pairs": int(B.shape[0]), "train_steps": args.learned_train_steps, "train_s": t_train,
-                   "leg_s": time.perf_counter() - t0, "val_rel_err": L.relative_error(model, B[:nval], P[:nval]),
+                   "pairs": int(Bp.shape[0]), "train_steps": args.learned_train_steps, "train_s": t_train,
+                   "leg_s": time.perf_counter() - t0, "val_rel_err": L.relative_error(model, Bp[:nval], Pp[:nval]),
                    **ev}
-        del B, P, model
+        del Bp, Pp, model
 
-    # ---- the configuration's full run: every step from the seeded state --------
-    # The timed steps above start from the seeded state, where the Poisson
-    # solves need about half the CG iterations of the developed flow; this leg
-    # runs the configuration's whole run length and reports its mean rate.
-    long_run = None
+    # ---- the configuration's full run from the seeded state (on request) ------
+    long_main = None
     nlong = args.long_run if args.long_run >= 0 else (1000 if args.workload == "cbl128" else 0)
     if rank == 0 and world == 1 and nlong > 0:
-        lsim = les.Simulation(case)
-        lsim.set_state(inputs.initial_state(case))
-        chunk = 50
-        done, iters_l, nc_l, ms_l = 0, 0, 0, 0.0
-        while done < nlong:
-            n = min(chunk, nlong - done)
-            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ea.record(lsim.stream)
-            st = lsim.step(n, allow_not_converged=True)
-            eb.record(lsim.stream)
-            eb.synchronize()
-            ms_l += ea.elapsed_time(eb)
-            iters_l += st["iters_total"]
-            nc_l += st["not_converged"]
-            done += n
-        d = lsim.diagnostics()
-        lsim.close()
-        long_run = {"steps": nlong, "value": case.n * nlong / (ms_l / 1e3), "unit": UNIT,
-                    "ms_per_step": ms_l / nlong, "iters_per_step": iters_l / nlong, "not_converged": nc_l,
-                    "nonfinite": d["nonfinite"], "max_cfl_end": d["max_cfl"],
-                    "note": "every step from the seeded state, CUDA events around chunks of 50 steps, "
-                            "no L2 flush"}
+        long_main = long_run(case, nlong)
+
+    # ---- second record: the moist capped boundary layer ------------------------
+    second = None
+    if args.workload != "cbl128" and not args.no_second_record:
+        second = second_record(args, rank, world, local, flush)
 
     # ---- CPU oracle baseline ---------------------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample, desc = oracle_sample(case, args)
+        # the large box: a 256 x 256 x 256 sub-box of full columns (8 x 8 x 8
+        # Taylor-Green periods, 16.8 M cells); others: at most 2 M cells
+        sample, desc = oracle_sample(case, args, side=256) if big else oracle_sample(case, args)
         val, secs = time_oracle(sample, 1, 0)
         cpu = {"value": val, "unit": UNIT, "cores": cores(), "kind": "oracle",
                "sample": f"1 step of the {desc} (FP64, {secs:.1f} s)"}
@@ -566,24 +688,25 @@ def main():
             "config": {"workload": WORKLOAD_DESC[args.workload], "grid": [case.nx, case.ny, case.nz],
                        "cells": case.n, "K": case.K, "solver": case.solver, "tol": case.tol,
                        "warm_start": case.warm, "advection": case.advection,
-                       "l2": "flushed (256 MiB write) before every timed step",
+                       "l2": "flushed (256 MiB write) before every timed step"
+                             + ("; every field (2.4 GB) is also larger than L2" if big else ""),
                        "replicas": world, "seed": 1},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": launches,
-            "clocks": clk,
-            "poisson": {"ms_per_step": stage_ms["solve"], "iters_per_step": iters / args.steps,
-                        "not_converged": nc, "warm_start": case.warm, "tol": case.tol,
+            "gpu_launches": t["launches"],
+            "clocks": t["clocks"],
+            "poisson": {"ms_per_step": stage_ms["solve"], "iters_per_step": t["iters"] / args.steps,
+                        "not_converged": t["not_converged"], "warm_start": case.warm, "tol": case.tol,
                         "learned_vs_plain": learned},
             "stage_ms_per_step": stage_ms,
-            "long_run": long_run,
+            "long_run": long_main,
             "kernels": kernels,
-            "wall_s_timed": wall,
+            "second_record": second,
+            "wall_s_timed": t["wall"],
         }
         print(json.dumps(line), flush=True)
     barrier(world)
-    sim.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -193,8 +193,13 @@ void les_destroy(les_handle *h);
 int les_set_stream(les_handle *h, void *stream);
 
 /* Copy nx*ny*nz values of the handle's precision into / out of a field.
- * on_device != 0: src / dst is a device pointer (stream-ordered copy);
- * otherwise a host pointer (the call synchronises the stream). */
+ * The fields are the prognostic and diagnostic variables of Sec. 2.1
+ * (u, v, w, p', theta_l, q_t; T, q_l and b of Sec. 2.1-2.2) and the
+ * intermediate arrays of the scheme of Sec. 2.4 (u^n, phi^{n+1/2}, the
+ * predicted velocity, the Poisson right side and psi = alpha0 dp), in the
+ * layout above.  on_device != 0: src / dst is a device pointer
+ * (stream-ordered copy); otherwise a host pointer (the call synchronises the
+ * stream).  LES_ERR_INVALID_ARG for a bad id or a NULL pointer. */
 int les_set_state(les_handle *h, int32_t field, const void *src, int32_t on_device);
 int les_get_state(les_handle *h, int32_t field, void *dst, int32_t on_device);
 
@@ -221,8 +226,11 @@ int les_step(les_handle *h, int32_t nsteps, les_step_stats *stats);
 int les_stage(les_handle *h, int32_t stage, les_step_stats *stats);
 
 /* Solve A x = b with the handle's operator, boundary conditions and solver:
- * A = L_c (LES_OP_COMPACT) or D(rho0 G .) (LES_OP_WIDE).  b's mean is
- * removed first and x is returned with zero mean.  d_rhs, d_x: device arrays
+ * the pressure-correction equation of Sec. 2.4 (Eq. pressure_correction,
+ * with the compact Laplacian of Appendix A: A = L_c, LES_OP_COMPACT) or the
+ * consistent operator A = D(rho0 G .) (LES_OP_WIDE); the solver is CG or the
+ * weighted Jacobi iteration the paper uses (Sec. 2.4).  b's mean is removed
+ * first and x is returned with zero mean.  d_rhs, d_x: device arrays
  * of nx*ny*nz values, distinct from the handle's fields; x holds the initial
  * guess on entry.  rtol > 0, maxit >= 0.  iters / rel_res may be NULL.
  * Synchronises the stream.  LES_ERR_NOT_CONVERGED if maxit was reached. */
@@ -253,7 +261,9 @@ int les_diagnostics(les_handle *h, double *out);
  * cudaFree or allocating library routine is called.
  * The first call on a device looks up the array's device address with that
  * device current (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture.  Every call on a device shares the one array,
+ * before any stream capture.  The cached address belongs to the device's
+ * current context: after cudaDeviceReset() on that device, further calls in
+ * the same process are invalid.  Every call on a device shares the one array,
  * which keeps the previous call's contents (the call clears the control
  * block it needs zeroed): calls that overlap on the GPU race, so issue them
  * on one stream or serialise them.

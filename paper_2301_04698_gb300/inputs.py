@@ -46,17 +46,27 @@ STREAM_ENSEMBLE = 17
 def uniform01(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
     """n uniform doubles in [0, 1) from counter indices offset .. offset+n-1."""
     with np.errstate(over="ignore"):
-        idx = np.arange(offset, offset + n, dtype=np.uint64)
-        x = np.uint64(seed) * _GOLD + (np.uint64(stream) << np.uint64(40)) + idx
-        z = x + _GOLD
-        z = (z ^ (z >> np.uint64(30))) * _M1
-        z = (z ^ (z >> np.uint64(27))) * _M2
-        z = z ^ (z >> np.uint64(31))
-    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+        # (seed * golden + (stream << 40) + index) + golden, wrapping mod 2^64
+        base = np.uint64(seed) * _GOLD + (np.uint64(stream) << np.uint64(40)) + _GOLD
+        z = np.arange(offset, offset + n, dtype=np.uint64)
+        z += base
+        t = np.empty_like(z)
+        np.right_shift(z, np.uint64(30), out=t)
+        z ^= t
+        z *= _M1
+        np.right_shift(z, np.uint64(27), out=t)
+        z ^= t
+        z *= _M2
+        np.right_shift(z, np.uint64(31), out=t)
+        z ^= t
+        z >>= np.uint64(11)
+    out = z.astype(np.float64)
+    out *= 1.0 / 9007199254740992.0
+    return out
 
 
-def uniform(seed: int, stream: int, n: int, lo: float, hi: float) -> np.ndarray:
-    return lo + (hi - lo) * uniform01(seed, stream, n)
+def uniform(seed: int, stream: int, n: int, lo: float, hi: float, offset: int = 0) -> np.ndarray:
+    return lo + (hi - lo) * uniform01(seed, stream, n, offset)
 
 
 @dataclass
@@ -228,15 +238,27 @@ def initial_state(case: Case) -> dict:
         x = (np.arange(nx) + 0.5) * case.dx
         y = (np.arange(ny) + 0.5) * case.dy
         z = (np.arange(nz) + 0.5) * case.dz
-        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
         tp = 2.0 * np.pi
         amp, eps = a.get("amp", 1.0), a.get("noise", 1e-3)
-        u = amp * np.sin(tp * X) * np.cos(tp * Y) * np.cos(tp * Z)
-        v = -amp * np.cos(tp * X) * np.sin(tp * Y) * np.cos(tp * Z)
-        w = np.zeros_like(u)
-        out["u"] = u + uniform(case.seed, STREAM_U, n, -eps, eps).reshape(case.shape)
-        out["v"] = v + uniform(case.seed, STREAM_V, n, -eps, eps).reshape(case.shape)
-        out["w"] = w + uniform(case.seed, STREAM_W, n, -eps, eps).reshape(case.shape)
+        sx, cx = np.sin(tp * x)[None, None, :], np.cos(tp * x)[None, None, :]
+        sy, cy = np.sin(tp * y)[None, :, None], np.cos(tp * y)[None, :, None]
+        cz = np.cos(tp * z)[:, None, None]
+        for k in ("u", "v", "w"):
+            out[k] = np.empty(case.shape)
+        # plane chunks keep the temporaries small on large grids; the values
+        # are those of the whole-array expressions
+        plane = nx * ny
+        step = max(1, (1 << 24) // plane)
+        for k0 in range(0, nz, step):
+            k1 = min(nz, k0 + step)
+            m = (k1 - k0) * plane
+            zs = slice(k0, k1)
+            out["u"][zs] = amp * sx * cy * cz[zs] + \
+                uniform(case.seed, STREAM_U, m, -eps, eps, offset=k0 * plane).reshape(k1 - k0, ny, nx)
+            out["v"][zs] = -amp * cx * sy * cz[zs] + \
+                uniform(case.seed, STREAM_V, m, -eps, eps, offset=k0 * plane).reshape(k1 - k0, ny, nx)
+            out["w"][zs] = 0.0 + \
+                uniform(case.seed, STREAM_W, m, -eps, eps, offset=k0 * plane).reshape(k1 - k0, ny, nx)
         out["theta_l"] = np.full(case.shape, a.get("theta", 300.0))
         out["q_t"] = np.zeros(case.shape)
     elif case.init == "cbl":

@@ -34,19 +34,36 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def _static_solve(les_mod, lib, case, b, tol, maxit, rho0=None, x=None):
+    cfg = les_mod.config_from_case(case)
+    err = C.create_string_buffer(256)
+    if x is None:
+        x = torch.zeros_like(b)
+    it = C.c_int32(0)
+    rel = C.c_double(0.0)
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.les_poisson_solve_static(C.byref(cfg), C.c_void_p(rho0.data_ptr()) if rho0 is not None else None,
+                                      C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), tol, maxit,
+                                      C.c_void_p(stream), C.byref(it), C.byref(rel), err, len(err))
+    torch.cuda.synchronize()
+    return rc, x, it.value, rel.value, err.value
+
+
+def _case(nx, ny, nz, precision, walls, op="compact", solver="cg"):
+    return inputs.Case(name="static", nx=nx, ny=ny, nz=nz, dx=35.0, dy=35.0, dz=10.0, walls=walls,
+                       precision=precision, init="zero", physics=(), op=op, solver=solver,
+                       rho0_const=None if walls else 1.0)
+
+
 @pytest.mark.parametrize("precision,walls,op", [(64, True, "compact"), (32, True, "compact"),
                                                 (64, False, "wide")])
 def test_static_solve_matches_handle_solve(les_mod, precision, walls, op):
-    case = inputs.Case(name="static", nx=40, ny=36, nz=20, dx=35.0, dy=35.0, dz=10.0, walls=walls,
-                       precision=precision, init="zero", physics=(), op=op,
-                       rho0_const=None if walls else 1.0)
+    case = _case(40, 36, 20, precision, walls, op)
     tol = 1e-10 if precision == 64 else 1e-6
     dt = torch.float64 if precision == 64 else torch.float32
     sim = les_mod.Simulation(case)
-    cfg = les_mod.config_from_case(case)
     rho0 = torch.ones(case.nz, dtype=dt, device="cuda")
     lib = sim.lib
-    err = C.create_string_buffer(256)
     for call, seed in enumerate((11, 12)):
         # a right side in the operator's range (D(rho0 G) has more than the
         # constant in its null space on an even periodic grid)
@@ -54,19 +71,60 @@ def test_static_solve_matches_handle_solve(les_mod, precision, walls, op):
         b = sim.apply_poisson(xt, op)
         x_ref = torch.zeros_like(b)
         rc_ref, it_ref, res_ref = sim.poisson_solve(b, x_ref, tol, 5000)
-        x = torch.zeros_like(b)
-        it = C.c_int32(0)
-        rel = C.c_double(0.0)
-        stream = torch.cuda.current_stream().cuda_stream
-        rc = lib.les_poisson_solve_static(C.byref(cfg), C.c_void_p(rho0.data_ptr()), C.c_void_p(b.data_ptr()),
-                                          C.c_void_p(x.data_ptr()), tol, 5000, C.c_void_p(stream),
-                                          C.byref(it), C.byref(rel), err, len(err))
-        torch.cuda.synchronize()
-        assert rc == les_mod.LES_OK, err.value
+        rc, x, it, rel, msg = _static_solve(les_mod, lib, case, b, tol, 5000, rho0)
+        assert rc == les_mod.LES_OK, msg
         # the handle's solver may be a different (persistent) CG kernel whose
         # sums round in another order: the same iterates to within rounding
-        assert rel.value <= tol and abs(it.value - it_ref) <= (1 if precision == 64 else 3)
+        assert rel <= tol and abs(it - it_ref) <= (1 if precision == 64 else 3)
         assert _rel(x.cpu().double().numpy(), x_ref.cpu().double().numpy()) < (1e-9 if precision == 64 else 1e-5), call
+    sim.close()
+
+
+def test_static_weighted_jacobi_matches_handle_solve(les_mod):
+    """The Jacobi branch keeps its second iterate in the array and reports the
+    buffer holding the answer through the control block: the same answer
+    and iteration count as the handle's weighted Jacobi, twice in a row."""
+    case = _case(16, 12, 8, 64, True, solver="jacobi")
+    sim = les_mod.Simulation(case)
+    for seed in (21, 22):
+        xt = torch.from_numpy(inputs.uniform(seed, 0, case.n, -1, 1).reshape(case.shape)).to("cuda", torch.float64)
+        b = sim.apply_poisson(xt, "compact")
+        x_ref = torch.zeros_like(b)
+        rc_ref, it_ref, res_ref = sim.poisson_solve(b, x_ref, 1e-4, 20000)
+        rc, x, it, rel, msg = _static_solve(les_mod, sim.lib, case, b, 1e-4, 20000)
+        assert rc == les_mod.LES_OK, msg
+        assert it == it_ref and rel <= 1e-4
+        assert _rel(x.cpu().numpy(), x_ref.cpu().numpy()) < 1e-12
+    sim.close()
+
+
+def test_static_solve_allocates_nothing_and_keeps_no_state(les_mod):
+    """A call leaves the device's free memory unchanged once the library's
+    module is loaded on the device (the first call of a process may load it,
+    so each grid gets one call first); and a solve on a large grid followed by
+    one on a smaller grid (whose vectors then start inside the large grid's
+    leftovers) still matches the handle's solve."""
+    lib = les_mod.load_library()
+    results = []
+    for dims in ((96, 80, 32), (40, 36, 20)):
+        case = _case(*dims, 32, True)
+        sim = les_mod.Simulation(case)
+        xt = torch.from_numpy(inputs.uniform(31, 0, case.n, -1, 1).reshape(case.shape)).to("cuda", torch.float32)
+        b = sim.apply_poisson(xt, "compact")
+        x_ref = torch.zeros_like(b)
+        sim.poisson_solve(b, x_ref, 1e-6, 5000)
+        rc, _, _, _, msg = _static_solve(les_mod, lib, case, b, 1e-6, 5000)
+        assert rc == les_mod.LES_OK, msg
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        rc, x, it, rel, msg = _static_solve(les_mod, lib, case, b, 1e-6, 5000, x=x)
+        free1 = torch.cuda.mem_get_info()[0]
+        assert rc == les_mod.LES_OK, msg
+        assert free1 == free0
+        results.append(_rel(x.cpu().double().numpy(), x_ref.cpu().double().numpy()))
+        sim.close()
+    assert max(results) < 1e-5
 
 
 def test_static_solve_rejects_oversized_grids(les_mod):
