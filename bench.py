@@ -672,9 +672,9 @@ def main():
     # ---- CPU oracle baseline ---------------------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # the large box: a 256 x 256 x 256 sub-box of full columns (8 x 8 x 8
-        # Taylor-Green periods, 16.8 M cells); others: at most 2 M cells
-        sample, desc = oracle_sample(case, args, side=256) if big else oracle_sample(case, args)
+        # the large box: 128 x 128 full columns (4 x 4 x 8 Taylor-Green
+        # periods, 4.2 M cells, ~15 s on 16 cores); others: at most 2 M cells
+        sample, desc = oracle_sample(case, args, side=128) if big else oracle_sample(case, args)
         val, secs = time_oracle(sample, 1, 0)
         cpu = {"value": val, "unit": UNIT, "cores": cores(), "kind": "oracle",
                "sample": f"1 step of the {desc} (FP64, {secs:.1f} s)"}

@@ -303,10 +303,12 @@ int les_ensemble_step(les_handle *const *hs, int32_t m, int32_t nsteps, les_step
  * device stays usable.  fault_missing_arrivals is a failure-detection test
  * hook: the barrier then waits for that many blocks that never arrive, so
  * every wait runs out; it must be 0 otherwise.  stencil_path selects the
- * predictor kernels (same results to rounding): 0 (default) both
- * predictors as rolling z-marches through shared-memory plane rings; 1
- * direct-load kernels with nu_t stored between kernels; 2 both predictors in
- * shared-memory 3-D tiles.  Paths 0 and 2 compute nu_t in place.  With
+ * stencil kernels (same results to rounding): 0 (default) column marches
+ * over 16-byte lanes where the grid allows them (nx a multiple of 128 floats
+ * / 64 doubles, ny a multiple of 8), else as 3; 1 direct-load kernels with
+ * nu_t stored between kernels; 2 both predictors in shared-memory 3-D tiles;
+ * 3 rolling z-marches through shared-memory plane rings.  Paths 0, 2 and 3
+ * compute nu_t in place.  With
  * cg_resident = 0 the standard CG solve first tries a decomposition of the
  * grid into one brick per thread block (x extent 32, 64 or 128 dividing nx,
  * y and z extents dividing ny and nz, at most one block per SM, x, r and p
@@ -322,7 +324,8 @@ typedef struct les_tuning {
   int32_t  cg_max_blocks;          /* >= 1                                  */
   double   barrier_timeout_ms;     /* > 0                                   */
   int32_t  fault_missing_arrivals; /* 0 in production                      */
-  int32_t  stencil_path;           /* 0 rolling (default), 1 direct, 2 tiled */
+  int32_t  stencil_path;           /* 0 columns (default), 1 direct, 2 tiled,
+                                      3 rolling                            */
   int32_t  cg_variant;             /* persistent CG: 0 (default) the
                                       standard CG iterates -- in shared
                                       memory when the grid fits there (see

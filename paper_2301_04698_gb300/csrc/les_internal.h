@@ -101,7 +101,8 @@ struct FusedCfg {
   long long spin_cycles = 4000000000LL; // barrier wait limit (~2 s at 2 GHz)
   double timeout_ms = 2000.0;
   int missing = 0;                      // test hook: arrivals that never come
-  int stencil_path = 0;                 // 0 rolling z-march, 1 direct-load, 2 tiled
+  int stencil_path = 0;                 // 0 column marches where eligible (else 3), 1 direct-load, 2 tiled,
+                                        // 3 rolling z-march
   int variant = 0;                      // 0 standard iterates (resident, else two-phase streaming when
                                         // tile-aligned, else one-pass), 1 Chronopoulos-Gear,
                                         // 2 two-phase streaming, 3 one-pass one-reduction
@@ -252,6 +253,16 @@ cudaError_t launch_momentum_roll(const StageArgs<T>& a, int max_blocks, const T*
 template <typename T>
 cudaError_t launch_rhs(const StageArgs<T>& a, int op, const T* ou, const T* ov, const T* ow,
                        const T* psi, T* rhs);
+// column marches over 16-byte lanes (les_stencil_col.cu): nx a multiple of
+// 32 lanes x (16 bytes / element size), ny a multiple of 8
+template <typename T>
+bool col_eligible(const Grid<T>& g);
+template <typename T>
+cudaError_t launch_correct_col(const StageArgs<T>& a, int max_blocks, const T* ou, const T* ov, const T* ow,
+                               const T* psi, T* u, T* v, T* w, T* p);
+template <typename T>
+cudaError_t launch_rhs_col(const StageArgs<T>& a, int max_blocks, int op, const T* ou, const T* ov, const T* ow,
+                           const T* psi, T* rhs);
 template <typename T>
 cudaError_t launch_correct(const StageArgs<T>& a, const T* ou, const T* ov, const T* ow,
                            const T* psi, T* u, T* v, T* w, T* p);
