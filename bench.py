@@ -49,14 +49,14 @@ METRIC = "LES cell-steps/s on 1 GB300; Poisson ms/step at fixed residual, learne
 UNIT = "cell-steps/s"
 
 
-def workload(name: str, seed: int):
+def workload(name: str, seed: int, grid=None):
     from paper_2301_04698_gb300 import inputs
     if name == "cbl128":
         return inputs.cbl(128, 128, 96, seed=seed, precision=32)
     if name == "tgv32":
         return inputs.tgv(32, seed=seed)
     if name == "tgv_large":
-        return inputs.tgv(32, nxyz=(1536, 1536, 256), seed=seed, precision=32, steps_tol=1e-6)
+        return inputs.tgv(32, nxyz=grid or (1536, 1536, 256), seed=seed, precision=32, steps_tol=1e-6)
     if name == "ensemble16":
         return inputs.ensemble(16, seed=seed)
     raise SystemExit(f"unknown workload {name}")
@@ -100,7 +100,9 @@ def parse():
     # single Poisson solves (profiling a CG kernel)
     ap.add_argument("--poisson-only", action="store_true",
                     help="time single Poisson solves of a seeded right side instead of steps")
-    ap.add_argument("--grid", default="512x512x64", help="--poisson-only grid NXxNYxNZ (walls in z)")
+    ap.add_argument("--grid", default=None,
+                    help="NXxNYxNZ: the --poisson-only grid (walls in z, default 512x512x64), or another grid for "
+                         "--workload tgv_large (profiling a smaller tiling of the same box)")
     ap.add_argument("--variant", type=int, default=0, help="--poisson-only: les_tuning.cg_variant")
     ap.add_argument("--resident", type=int, default=1,
                     help="--poisson-only: les_tuning.cg_resident (0: on chip when the grid fits)")
@@ -323,7 +325,7 @@ def poisson_only(args):
     from paper_2301_04698_gb300 import inputs, les
     B.build()
     les.load_library()
-    nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
+    nx, ny, nz = (int(v) for v in (args.grid or "512x512x64").lower().split("x"))
     prec = 64 if args.fp64 else 32
     case = inputs.Case(name="poisson", nx=nx, ny=ny, nz=nz, dx=35.0, dy=35.0, dz=10.0, walls=True,
                        precision=prec, init="zero", physics=())
@@ -519,7 +521,10 @@ def main():
     if args.workload == "ensemble16":
         return bench_ensemble(args, rank, world, local)
 
-    case = workload(args.workload, seed=1 + rank)
+    grid = tuple(int(v) for v in args.grid.lower().split("x")) if args.grid else None
+    if grid is not None and args.workload != "tgv_large":
+        raise SystemExit("--grid applies to --workload tgv_large (or --poisson-only)")
+    case = workload(args.workload, seed=1 + rank, grid=grid)
     if args.warm != case.warm:
         case = case.replace(warm=args.warm)
     if args.advection != case.advection:
@@ -685,7 +690,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if case.precision == 32 else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC[args.workload], "grid": [case.nx, case.ny, case.nz],
+            "config": {"workload": WORKLOAD_DESC[args.workload] if grid is None else
+                       f"dry triply periodic Taylor-Green {case.nx}x{case.ny}x{case.nz}, FP32 (FP64 reductions), K=3, "
+                       "CG to 1e-6", "grid": [case.nx, case.ny, case.nz],
                        "cells": case.n, "K": case.K, "solver": case.solver, "tol": case.tol,
                        "warm_start": case.warm, "advection": case.advection,
                        "l2": "flushed (256 MiB write) before every timed step"

@@ -335,7 +335,11 @@ int stage_scalar(les_handle* h) {
   T* const* F = (T* const*)h->fixed;
   const int ti = h->cur ? B_THB : B_THA, qi = h->cur ? B_QTB : B_QTA;
   const int to = h->cur ? B_THA : B_THB, qo = h->cur ? B_QTA : B_QTB;
-  if (h->fused.stencil_path == 0 || h->fused.stencil_path == 3) {
+  if ((h->fused.stencil_path == 0 || h->fused.stencil_path == 4) && pcol_eligible<T>(a.g)) {
+    if ((e = launch_scalar_col<T>(a, h->L.max_blocks / 8, F[B_U], F[B_V], F[B_W], F[B_B], F[ti], F[qi], F[B_THH],
+                                  F[B_QTH], F[B_SRAD], F[to], F[qo])) != cudaSuccess)
+      return h->cuda_fail(e, "scalar predictor");
+  } else if (h->fused.stencil_path == 0 || h->fused.stencil_path == 3 || h->fused.stencil_path == 4) {
     if ((e = launch_scalar_roll<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_B], F[ti], F[qi], F[B_THH],
                                    F[B_QTH], F[B_SRAD], F[to], F[qo])) != cudaSuccess)
       return h->cuda_fail(e, "scalar predictor");
@@ -360,7 +364,11 @@ int stage_momentum(les_handle* h) {
   auto a = stage_args<T>(h);
   cudaError_t e;
   T* const* F = (T* const*)h->fixed;
-  if (h->fused.stencil_path == 0 || h->fused.stencil_path == 3) {
+  if (h->fused.stencil_path == 4 && pcol_eligible<T>(a.g)) {
+    if ((e = launch_momentum_col<T>(a, h->L.max_blocks / 8, F[B_U], F[B_V], F[B_W], F[B_UN], F[B_VN], F[B_WN],
+                                    F[B_P], F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess)
+      return h->cuda_fail(e, "momentum predictor");
+  } else if (h->fused.stencil_path == 0 || h->fused.stencil_path == 3 || h->fused.stencil_path == 4) {
     if ((e = launch_momentum_roll<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_UN], F[B_VN], F[B_WN],
                                      F[B_P], F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess)
       return h->cuda_fail(e, "momentum predictor");
@@ -376,10 +384,10 @@ int stage_momentum(les_handle* h) {
                                 F[B_P], F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess)
       return h->cuda_fail(e, "momentum predictor");
   }
-  if (h->fused.stencil_path == 0 && col_eligible<T>(a.g))
+  if ((h->fused.stencil_path == 0 || h->fused.stencil_path == 4) && col_eligible<T>(a.g))
     e = launch_rhs_col<T>(a, h->L.max_blocks, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI],
                           F[B_RHS]);
-  else if (h->fused.stencil_path == 0 || h->fused.stencil_path == 3)
+  else if (h->fused.stencil_path == 0 || h->fused.stencil_path == 3 || h->fused.stencil_path == 4)
     e = launch_rhs_roll<T>(a, h->L.max_blocks, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI],
                            F[B_RHS]);
   else
@@ -438,7 +446,7 @@ int stage_correct(les_handle* h) {
   auto a = stage_args<T>(h);
   T* const* F = (T* const*)h->fixed;
   cudaError_t e =
-      h->fused.stencil_path == 0 && col_eligible<T>(a.g)
+      (h->fused.stencil_path == 0 || h->fused.stencil_path == 4) && col_eligible<T>(a.g)
           ? launch_correct_col<T>(a, h->L.max_blocks, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI], F[B_U], F[B_V],
                                   F[B_W], F[B_P])
           : launch_correct<T>(a, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI], F[B_U], F[B_V], F[B_W], F[B_P]);
@@ -839,8 +847,8 @@ int les_set_tuning(les_handle* h, const les_tuning* in) {
     h->fused.spin_cycles = (long long)(in->barrier_timeout_ms * (double)khz);
   }
   h->fused.missing = in->fault_missing_arrivals;
-  if (in->stencil_path < 0 || in->stencil_path > 3)
-    return h->fail(LES_ERR_INVALID_ARG, "stencil_path must be 0, 1, 2 or 3");
+  if (in->stencil_path < 0 || in->stencil_path > 4)
+    return h->fail(LES_ERR_INVALID_ARG, "stencil_path must be 0 .. 4");
   h->fused.stencil_path = in->stencil_path;
   if (in->cg_variant < 0 || in->cg_variant > 4)
     return h->fail(LES_ERR_INVALID_ARG, "cg_variant must be 0, 1, 2, 3 or 4");

@@ -101,8 +101,8 @@ struct FusedCfg {
   long long spin_cycles = 4000000000LL; // barrier wait limit (~2 s at 2 GHz)
   double timeout_ms = 2000.0;
   int missing = 0;                      // test hook: arrivals that never come
-  int stencil_path = 0;                 // 0 column marches where eligible (else 3), 1 direct-load, 2 tiled,
-                                        // 3 rolling z-march
+  int stencil_path = 0;                 // 0 column marches where eligible (momentum as 3), 1 direct-load,
+                                        // 2 tiled, 3 rolling z-march, 4 as 0 with a column momentum march
   int variant = 0;                      // 0 standard iterates (resident, else two-phase streaming when
                                         // tile-aligned, else one-pass), 1 Chronopoulos-Gear,
                                         // 2 two-phase streaming, 3 one-pass one-reduction
@@ -263,6 +263,18 @@ cudaError_t launch_correct_col(const StageArgs<T>& a, int max_blocks, const T* o
 template <typename T>
 cudaError_t launch_rhs_col(const StageArgs<T>& a, int max_blocks, int op, const T* ou, const T* ov, const T* ow,
                            const T* psi, T* rhs);
+// predictors as column marches with staged shared-memory planes
+// (les_predict_col.cu): nx a multiple of 32 lanes x (16 bytes / element
+// size), ny a multiple of 8
+template <typename T>
+bool pcol_eligible(const Grid<T>& g);
+template <typename T>
+cudaError_t launch_scalar_col(const StageArgs<T>& a, int nsm, const T* u, const T* v, const T* w, const T* b,
+                              const T* thk, const T* qtk, const T* thh, const T* qth, const T* srad, T* th_out,
+                              T* qt_out);
+template <typename T>
+cudaError_t launch_momentum_col(const StageArgs<T>& a, int nsm, const T* uk, const T* vk, const T* wk, const T* un,
+                                const T* vn, const T* wn, const T* p, const T* b, T* ou, T* ov, T* ow);
 template <typename T>
 cudaError_t launch_correct(const StageArgs<T>& a, const T* ou, const T* ov, const T* ow,
                            const T* psi, T* u, T* v, T* w, T* p);

@@ -56,10 +56,14 @@ def _moist(nx, ny, nz, walls, advection="quick", precision=64):
     return c
 
 
+@pytest.mark.parametrize("path", [0, 4])
 @pytest.mark.parametrize("shape,walls,advection", [
     ((64, 16, 12), True, "quick"), ((128, 8, 10), False, "quick"), ((64, 8, 2), True, "quick"),
     ((64, 24, 9), False, "weno3"), ((192, 8, 6), True, "weno3")])
-def test_column_stages_fp64(les_mod, shape, walls, advection):
+def test_column_stages_fp64(les_mod, shape, walls, advection, path):
+    """Stage-by-stage FP64 parity; path 0 (default: column correction, right
+    side and scalar predictor) and path 4 (the momentum predictor as a column
+    march too)."""
     from oracle import Oracle
     case = _moist(*shape, walls, advection)
     st = _state(case)
@@ -67,6 +71,7 @@ def test_column_stages_fp64(les_mod, shape, walls, advection):
     sim.set_state(st)
     ref = Oracle(case, st)
     assert sim.tuning()["stencil_path"] == 0
+    sim.set_tuning(stencil_path=path)
     sim.stage("begin")
     ref.begin_step()
     for k in range(case.K):
@@ -110,14 +115,15 @@ def test_column_rhs_and_correct_fp64_exact_inputs(les_mod, op):
     assert np.max(np.abs(sim.get("rhs") - ref.get("rhs"))) <= 1e-11 * np.max(np.abs(ref.get("rhs")))
 
 
+@pytest.mark.parametrize("path", [0, 4])
 @pytest.mark.parametrize("shape,walls", [((128, 16, 24), True), ((256, 8, 10), False), ((128, 8, 2), True)])
-def test_column_fp32_matches_rolling(les_mod, shape, walls):
+def test_column_fp32_matches_rolling(les_mod, shape, walls, path):
     """FP32: the column kernels and the rolling kernels (stencil_path 3) on the
     same inputs agree to float rounding, stage by stage, for three steps."""
     case = _moist(*shape, walls, precision=32).replace(dt=0.5)
     st = _state(case)
     sims = []
-    for path in (0, 3):
+    for path in (path, 3):
         s = les_mod.Simulation(case)
         s.set_state(st)
         s.set_tuning(stencil_path=path)
