@@ -277,6 +277,61 @@ int les_poisson_solve_static(const les_config *cfg, const void *d_rho0, const vo
                              double rtol, int32_t maxit, void *stream, int32_t *iters,
                              double *rel_res, char *err, size_t err_len);
 
+/* ---- domain decomposition of the Poisson solve --------------------------------
+ * The paper runs its LES on many TPU cores by cutting the domain into
+ * partitions, exchanging halos before every stencil pass and reducing the
+ * iterative solver's sums over all partitions (Sec. 2.5; the partitionings of
+ * Sec. 4.2).  These calls do that for the pressure-correction solve (Sec. 2.4,
+ * compact operator of Appendix A), the part of the step that dominates its
+ * time: the global nx x ny x nz grid of *cfg (periodic in x and y) is cut into
+ * px x py sub-domains of (nx / px) x (ny / py) x nz nodes (the z columns stay
+ * whole, as in every partitioning the paper reports), one per rank; rank
+ * (rx, ry) owns the nodes x in [rx nx/px, (rx+1) nx/px), y likewise.
+ * The solve is the standard CG to ||b - A x|| <= tol ||b|| with b's global mean
+ * removed and x returned with zero global mean, the same iterates as
+ * les_poisson_solve up to the order of the sums.  Per iteration it calls
+ * ops->exchange once (the halo of the search direction) and ops->allreduce
+ * once (four FP64 sums).  The caller implements both: NCCL send / receive and
+ * all-reduce between GPUs, peer copies, or in-process copies between
+ * sub-domains on one device. */
+typedef struct les_dd les_dd;
+typedef struct les_dd_ops {
+  void *ctx;  /* passed back to both functions */
+  /* Send the four face strips send[f] (device buffers of bytes[f] bytes;
+   * f = 0 west: the nodes x = x0, 1 east: x = x0 + nx/px - 1, 2 south:
+   * y = y0, 3 north: y = y0 + ny/py - 1; each strip ordered with the
+   * in-face index fastest, then z) to the neighbour on that side, and receive
+   * the neighbours' opposite strips into recv[f] (recv[0] from the west
+   * neighbour's east strip, and so on; periodic neighbours wrap).  Called
+   * with the work enqueued on `stream`; on return recv must hold the data
+   * for work later enqueued on that stream.  Return 0 on success. */
+  int (*exchange)(void *ctx, void *const *send, void *const *recv, const size_t *bytes, void *stream);
+  /* Replace each of the n host doubles by its sum over all ranks; return 0
+   * on success. */
+  int (*allreduce)(void *ctx, double *values, int32_t n);
+} les_dd_ops;
+/* Device workspace of one sub-domain (its vectors with a one-node halo, the
+ * face strips and the partial sums).  LES_ERR_INVALID_ARG unless px divides
+ * nx, py divides ny, nz >= 2 and the precision is 32 or 64. */
+int les_dd_workspace_bytes(const les_config *cfg, int32_t px, int32_t py, size_t *bytes);
+/* Sub-domain (rx, ry) of a px x py partition of *cfg's grid; the workspace
+ * (>= 256-B aligned) is borrowed until les_dd_destroy; work runs on stream.
+ * Only the compact operator (LES_OP_COMPACT) is decomposed. */
+int les_dd_create(const les_config *cfg, int32_t px, int32_t py, int32_t rx, int32_t ry, void *workspace,
+                  size_t workspace_bytes, void *stream, les_dd **out);
+void les_dd_destroy(les_dd *d);
+/* The local interior size and its global offset (any pointer may be NULL). */
+int les_dd_local_shape(const les_dd *d, int32_t *nx, int32_t *ny, int32_t *nz, int32_t *x0, int32_t *y0);
+/* Solve on this rank's part: d_rhs, d_x device arrays of the local interior
+ * ((nx/px) x (ny/py) x nz, x fastest), d_x holds the rank's part of the
+ * initial guess.  Every rank of the partition must call it with the same
+ * rtol and maxit.  Synchronises the stream.  Returns LES_OK,
+ * LES_ERR_NOT_CONVERGED, LES_ERR_NONFINITE (CG breakdown), LES_ERR_CUDA (a
+ * CUDA call or a callback failed) or LES_ERR_INVALID_ARG. */
+int les_dd_poisson_solve(les_dd *d, const les_dd_ops *ops, const void *d_rhs, void *d_x, double rtol,
+                         int32_t maxit, int32_t *iters, double *rel_res);
+const char *les_dd_last_error(const les_dd *d);
+
 /* ---- ensembles -----------------------------------------------------------------
  * Independent members -- different grids, seeds and forcings, as in ensembles
  * of LES runs that produce parameterisation training data -- stepped
@@ -304,11 +359,13 @@ int les_ensemble_step(les_handle *const *hs, int32_t m, int32_t nsteps, les_step
  * hook: the barrier then waits for that many blocks that never arrive, so
  * every wait runs out; it must be 0 otherwise.  stencil_path selects the
  * stencil kernels (same results to rounding): 0 (default) column marches
- * over 16-byte lanes where the grid allows them (nx a multiple of 128 floats
- * / 64 doubles, ny a multiple of 8), else as 3; 1 direct-load kernels with
- * nu_t stored between kernels; 2 both predictors in shared-memory 3-D tiles;
- * 3 rolling z-marches through shared-memory plane rings.  Paths 0, 2 and 3
- * compute nu_t in place.  With
+ * over 16-byte lanes for the correction, the Poisson right side and the
+ * scalar predictor where the grid allows them (nx a multiple of 128 floats /
+ * 64 doubles, ny a multiple of 8), the momentum predictor as in 3; 1
+ * direct-load kernels with nu_t stored between kernels; 2 both predictors in
+ * shared-memory 3-D tiles; 3 rolling z-marches through shared-memory plane
+ * rings; 4 as 0 with the momentum predictor as a column march too.  Paths 0,
+ * 2, 3 and 4 compute nu_t in place.  With
  * cg_resident = 0 the standard CG solve first tries a decomposition of the
  * grid into one brick per thread block (x extent 32, 64 or 128 dividing nx,
  * y and z extents dividing ny and nz, at most one block per SM, x, r and p
@@ -325,7 +382,7 @@ typedef struct les_tuning {
   double   barrier_timeout_ms;     /* > 0                                   */
   int32_t  fault_missing_arrivals; /* 0 in production                      */
   int32_t  stencil_path;           /* 0 columns (default), 1 direct, 2 tiled,
-                                      3 rolling                            */
+                                      3 rolling, 4 columns incl. momentum  */
   int32_t  cg_variant;             /* persistent CG: 0 (default) the
                                       standard CG iterates -- in shared
                                       memory when the grid fits there (see
@@ -391,6 +448,18 @@ int les_unet_forward(les_unet *u, int32_t precision, const void *d_b, int32_t ba
  * the host (may be NULL; synchronises the stream when given) */
 int les_unet_loss_grad(les_unet *u, int32_t precision, const void *d_b, const void *d_psi, int32_t batch,
                        double *loss, float *d_grad);
+/* Training loss of les_unet_loss_grad / les_unet_train_step (default MSE):
+ * LES_UNET_LOSS_MSE     mean of d^2,
+ * LES_UNET_LOSS_ENERGY  sum of d (-Delta d) / count, -Delta the 7-point negative
+ *                       Laplacian with unit spacing on the periodic grid: the
+ *                       energy norm of the error, which weights each Fourier
+ *                       mode by the operator's eigenvalue as a CG solve from
+ *                       the guess does, and ignores the constant,
+ * with d = y - psi / (s out_scale) per sample.  LES_ERR_INVALID_ARG for another
+ * kind.  Not in the paper (the learned warm start is this library's). */
+#define LES_UNET_LOSS_MSE     0
+#define LES_UNET_LOSS_ENERGY  1
+int les_unet_set_loss(les_unet *u, int32_t kind);
 /* loss_grad followed by one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) */
 int les_unet_train_step(les_unet *u, int32_t precision, const void *d_b, const void *d_psi, int32_t batch,
                         float lr, double *loss);

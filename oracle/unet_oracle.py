@@ -182,6 +182,20 @@ def mse_loss(y, t):
     return float((d * d).mean()), 2.0 * d / d.size
 
 
+def energy_loss(y, t):
+    """Energy norm of the error on the periodic grid, unit spacing:
+    L = sum_v d_v (-Delta d)_v / size with d = y - t and -Delta the 7-point
+    negative Laplacian (6 d - the six neighbours), and its gradient
+    2 (-Delta d) / size (the form is symmetric).  It weights each Fourier mode
+    of the error by the operator's eigenvalue -- what a CG solve started from
+    y pays for -- and ignores the constant."""
+    d = y - t
+    ld = 6.0 * d
+    for ax in (-1, -2, -3):
+        ld -= np.roll(d, 1, axis=ax) + np.roll(d, -1, axis=ax)
+    return float((d * ld).sum() / d.size), 2.0 * ld / d.size
+
+
 def warm_start(params, b):
     """psi_0 = s (y - mean y), s = rms(b), y = net(b / s); b: (N, N, N)."""
     s = float(np.sqrt(np.mean(b * b)))

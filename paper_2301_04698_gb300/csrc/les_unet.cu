@@ -390,6 +390,38 @@ __global__ void k_loss(const float* y, const float* t, long long total, bf16* gy
   const double r = block_reduce<false>(acc, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
+// Energy norm of the error on the periodic n^3 grid (unit spacing) over
+// batch samples: loss = sum d (6 d - sum of the six neighbours) / count,
+// d = y - t; gy = 2 (6 d - sum of the six neighbours) / count in channel 0.
+__global__ void k_loss_energy(const float* y, const float* t, int n, long long total, bf16* gy, double* part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  const float inv = 2.f / (float)total;
+  const long long n3 = (long long)n * n * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long s0 = (i / n3) * n3;
+    const int v = (int)(i - s0);
+    const int x = v % n, yy = (v / n) % n, z = v / (n * n);
+    auto d = [&](int xx, int yv, int zz) {
+      const long long q = s0 + ((long long)zz * n + yv) * n + xx;
+      return y[(size_t)q * 8] - t[q];
+    };
+    const float d0 = d(x, yy, z);
+    const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
+    const int ym = yy == 0 ? n - 1 : yy - 1, yp = yy == n - 1 ? 0 : yy + 1;
+    const int zm = z == 0 ? n - 1 : z - 1, zp = z == n - 1 ? 0 : z + 1;
+    const float ld = 6.f * d0 - (d(xm, yy, z) + d(xp, yy, z)) - (d(x, ym, z) + d(x, yp, z)) -
+                     (d(x, yy, zm) + d(x, yy, zp));
+    acc += (double)d0 * ld;
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(gy + (size_t)i * 16);
+    o[0] = __floats2bfloat162_rn(ld * inv, 0.f);
+    const __nv_bfloat162 zr = __floats2bfloat162_rn(0.f, 0.f);
+#pragma unroll
+    for (int q = 1; q < 8; ++q) o[q] = zr;
+  }
+  const double r = block_reduce<false>(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
 __global__ void k_sum_part(const double* part, int n, double* out) {
   __shared__ double sh[32];
   double acc = 0.0;
@@ -475,6 +507,7 @@ struct les_unet {
   size_t wpart_floats = 0;
   double *scale, *ymean, *dpart, *loss;
   int step = 0;
+  int loss_kind = 0;       // 0 mean squared error, 1 energy norm of the error
   double out_scale = 1.0;  // psi_0 = s * out_scale * (y - mean y)
   std::string err;
   Profiler* prof = nullptr;
@@ -728,7 +761,8 @@ int run_loss_grad(les_unet* u, const T* b, const T* psi, int batch, double* loss
   if ((e = forward(u, batch)) != cudaSuccess) return unet_fail(u, e, "forward");
   const long long total = (long long)batch * u->n * u->n * u->n;
   const int nb = (int)std::min<long long>((total + 255) / 256, 4096);
-  k_loss<<<nb, 256, 0, u->st>>>(u->y, u->tgt, total, u->G0, u->dpart);
+  if (u->loss_kind == 1) k_loss_energy<<<nb, 256, 0, u->st>>>(u->y, u->tgt, u->n, total, u->G0, u->dpart);
+  else k_loss<<<nb, 256, 0, u->st>>>(u->y, u->tgt, total, u->G0, u->dpart);
   k_sum_part<<<1, 256, 0, u->st>>>(u->dpart, nb, u->loss);
   if ((e = backward(u, batch)) != cudaSuccess) return unet_fail(u, e, "backward");
   if (loss) {
@@ -862,6 +896,12 @@ int les_unet_train_step(les_unet* u, int32_t precision, const void* d_b, const v
   }
   cudaError_t e = refresh_weights(u);
   return e == cudaSuccess ? LES_OK : unet_fail(u, e, "adam");
+}
+
+int les_unet_set_loss(les_unet* u, int32_t kind) {
+  if (!u || (kind != LES_UNET_LOSS_MSE && kind != LES_UNET_LOSS_ENERGY)) return LES_ERR_INVALID_ARG;
+  u->loss_kind = kind;
+  return LES_OK;
 }
 
 int les_unet_set_output_scale(les_unet* u, double scale) {

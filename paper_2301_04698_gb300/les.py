@@ -43,8 +43,9 @@ EXPORTED = ("les_config_default", "les_workspace_bytes", "les_init", "les_destro
             "les_set_tuning", "les_unet_param_count", "les_unet_workspace_bytes", "les_unet_create",
             "les_unet_destroy", "les_unet_set_stream", "les_unet_set_weights", "les_unet_get_weights",
             "les_unet_forward", "les_unet_loss_grad", "les_unet_train_step", "les_unet_last_error",
-            "les_set_warm_model", "les_unet_set_output_scale", "les_unet_get_output_scale",
-            "les_ensemble_step", "les_set_states")
+            "les_set_warm_model", "les_unet_set_output_scale", "les_unet_get_output_scale", "les_unet_set_loss",
+            "les_ensemble_step", "les_set_states", "les_dd_workspace_bytes", "les_dd_create", "les_dd_destroy",
+            "les_dd_local_shape", "les_dd_poisson_solve", "les_dd_last_error")
 
 
 class LesConfig(C.Structure):
@@ -185,6 +186,20 @@ def load_library(path: str = LIB_PATH):
     lib.les_unet_set_output_scale.argtypes = [vp, dbl]
     lib.les_unet_get_output_scale.restype = dbl
     lib.les_unet_get_output_scale.argtypes = [vp]
+    lib.les_unet_set_loss.restype = C.c_int
+    lib.les_unet_set_loss.argtypes = [vp, C.c_int32]
+    lib.les_dd_workspace_bytes.restype = C.c_int
+    lib.les_dd_workspace_bytes.argtypes = [cfgp, i32, i32, C.POINTER(sz)]
+    lib.les_dd_create.restype = C.c_int
+    lib.les_dd_create.argtypes = [cfgp, i32, i32, i32, i32, vp, sz, vp, C.POINTER(vp)]
+    lib.les_dd_destroy.restype = None
+    lib.les_dd_destroy.argtypes = [vp]
+    lib.les_dd_local_shape.restype = C.c_int
+    lib.les_dd_local_shape.argtypes = [vp] + [C.POINTER(i32)] * 5
+    lib.les_dd_poisson_solve.restype = C.c_int
+    lib.les_dd_poisson_solve.argtypes = [vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl)]
+    lib.les_dd_last_error.restype = C.c_char_p
+    lib.les_dd_last_error.argtypes = [vp]
     lib.les_set_warm_model.restype = C.c_int
     lib.les_set_warm_model.argtypes = [vp, vp]
     lib.les_poisson_solve_static.restype = C.c_int
@@ -457,6 +472,10 @@ class UNet:
     @out_scale.setter
     def out_scale(self, v: float) -> None:
         self._ck(self.lib.les_unet_set_output_scale(self.h, float(v)), "set_output_scale")
+
+    def set_loss(self, kind: str) -> None:
+        """Training loss: "mse" or "energy" (energy norm of the error)."""
+        self._ck(self.lib.les_unet_set_loss(self.h, {"mse": 0, "energy": 1}[kind]), "set_loss")
 
     def get_weights(self) -> np.ndarray:
         out = np.empty(self.nparams, dtype=np.float32)

@@ -51,7 +51,9 @@ def test_adjoint_identities():
     assert np.isclose((U.conv(x, W, np.zeros(4)) * g).sum(), (x * gx).sum())
 
 
-def test_network_gradients_by_finite_differences():
+@pytest.mark.parametrize("loss_fn", ["mse_loss", "energy_loss"])
+def test_network_gradients_by_finite_differences(loss_fn):
+    lossf = getattr(U, loss_fn)
     n = 8
     rng = np.random.default_rng(3)
     w = U.init_weights(5) + 0.01 * rng.standard_normal(U.n_params())
@@ -60,10 +62,10 @@ def test_network_gradients_by_finite_differences():
 
     def loss(wv, xv):
         y, _ = U.forward(wv, xv)
-        return U.mse_loss(y, t)[0]
+        return lossf(y, t)[0]
 
     y, cache = U.forward(w, x0)
-    L, gy = U.mse_loss(y, t)
+    L, gy = lossf(y, t)
     gw, gx = U.backward(w, cache, gy)
     h = 1e-6
     # a spread of weights in every layer, and a few input values
@@ -94,3 +96,19 @@ def test_warm_start_is_scale_equivariant_and_mean_free():
     assert np.allclose(p2, 3.5 * p1, rtol=1e-12, atol=1e-12)
     assert abs(p1.mean()) < 1e-12
     assert U.n_params() == sum(co * ci * k ** 3 + co for _, ci, co, k in U.LAYERS)
+
+
+def test_energy_loss_of_a_fourier_mode():
+    """For an error d = cos(2 pi (m . x) / n) the energy loss is the 7-point
+    symbol sum_d 4 sin^2(pi m_d / n) times mean(d^2), and constants cost
+    nothing."""
+    n = 12
+    i = np.arange(n)
+    for m in ((1, 0, 0), (2, 3, 1), (6, 6, 6)):
+        ph = 2 * np.pi * (m[0] * i[None, None, :] + m[1] * i[None, :, None] + m[2] * i[:, None, None]) / n
+        d = np.cos(ph)[None]
+        lam = sum(4 * np.sin(np.pi * q / n) ** 2 for q in m)
+        L, _ = U.energy_loss(d + 0.3, np.zeros_like(d) + 0.3)
+        assert abs(L - lam * np.mean(d * d)) < 1e-12 * max(1.0, lam)
+        L2, g = U.energy_loss(d + 5.0, np.zeros_like(d))
+        assert abs(L2 - L) < 1e-12 * max(1.0, lam)
