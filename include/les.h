@@ -78,6 +78,9 @@ extern "C" {
  * library's reading -- the paper gives none) */
 #define LES_ADV_QUICK      0
 #define LES_ADV_WENO3      1
+/* preconditioner of the CG solve (not in the paper) */
+#define LES_PRECOND_NONE    0
+#define LES_PRECOND_LEARNED 1
 
 /* field ids for get / set / offset */
 enum les_field {
@@ -146,7 +149,12 @@ typedef struct les_config {
                                 1: one launch per CG phase               */
   int32_t  advection;        /* LES_ADV_QUICK (paper's default) |
                                 LES_ADV_WENO3 (its alternative, Sec. 2.4)  */
-  int32_t  reserved_i;
+  int32_t  precond;          /* LES_PRECOND_NONE (default) |
+                                LES_PRECOND_LEARNED: flexible CG with the
+                                attached network (les_set_warm_model) as
+                                the preconditioner, z = net(r), or z = r
+                                where r.z <= 0; CG and the compact
+                                operator only; not in the paper        */
   double   reserved[3];
 } les_config;
 

@@ -68,6 +68,9 @@ int validate(const les_config* c, std::string* why) {
   if (c->sat_maxit < 0 || c->sat_maxit > 1000) return bad("sat_maxit out of range");
   if (c->solver_path != 0 && c->solver_path != 1) return bad("solver_path must be 0 or 1");
   if (c->advection != LES_ADV_QUICK && c->advection != LES_ADV_WENO3) return bad("unknown advection scheme");
+  if (c->precond != LES_PRECOND_NONE && c->precond != LES_PRECOND_LEARNED) return bad("unknown preconditioner");
+  if (c->precond == LES_PRECOND_LEARNED && (c->solver != LES_SOLVER_CG || c->poisson_op != LES_OP_COMPACT))
+    return bad("the learned preconditioner needs the CG solver and the compact operator");
   return LES_OK;
 }
 
@@ -423,8 +426,16 @@ int stage_solve(les_handle* h, les_step_stats* st) {
   int iters = 0;
   double rel = 0;
   std::string err;
-  int rc = poisson_solve<T>(s, (const T*)h->fixed[B_RHS], psi, h->cfg.poisson_tol, h->cfg.poisson_maxit, &iters,
-                            &rel, &err);
+  int rc;
+  if (h->cfg.precond == LES_PRECOND_LEARNED) {
+    if (!h->model) return h->fail(LES_ERR_NO_MODEL, "learned preconditioner requested but no model is attached");
+    int fb = 0;
+    rc = poisson_solve_fcg<T>(s, h->model, (const T*)h->fixed[B_RHS], psi, h->cfg.poisson_tol, h->cfg.poisson_maxit,
+                              &iters, &rel, &fb, &err);
+  } else {
+    rc = poisson_solve<T>(s, (const T*)h->fixed[B_RHS], psi, h->cfg.poisson_tol, h->cfg.poisson_maxit, &iters, &rel,
+                          &err);
+  }
   if (rc == LES_ERR_CUDA || rc == LES_ERR_NONFINITE) return h->fail(rc, err);
   if (h->cfg.warm_start == LES_WARM_PREV) {
     if ((e = cudaMemcpyAsync(h->prev[k], psi, bytes, cudaMemcpyDeviceToDevice, h->st)) != cudaSuccess)
@@ -771,12 +782,19 @@ int les_poisson_solve(les_handle* h, const void* d_rhs, void* d_x, double rtol, 
   double rel = 0;
   std::string err;
   int rc;
+  const bool fcg = h->cfg.precond == LES_PRECOND_LEARNED;
+  if (fcg && !h->model) return h->fail(LES_ERR_NO_MODEL, "learned preconditioner requested but no model is attached");
+  int fb = 0;
   if (h->cfg.precision == 64) {
     auto s = solver_args<double>(h);
-    rc = poisson_solve<double>(s, (const double*)d_rhs, (double*)d_x, rtol, maxit, &it, &rel, &err);
+    rc = fcg ? poisson_solve_fcg<double>(s, h->model, (const double*)d_rhs, (double*)d_x, rtol, maxit, &it, &rel, &fb,
+                                         &err)
+             : poisson_solve<double>(s, (const double*)d_rhs, (double*)d_x, rtol, maxit, &it, &rel, &err);
   } else {
     auto s = solver_args<float>(h);
-    rc = poisson_solve<float>(s, (const float*)d_rhs, (float*)d_x, rtol, maxit, &it, &rel, &err);
+    rc = fcg ? poisson_solve_fcg<float>(s, h->model, (const float*)d_rhs, (float*)d_x, rtol, maxit, &it, &rel, &fb,
+                                        &err)
+             : poisson_solve<float>(s, (const float*)d_rhs, (float*)d_x, rtol, maxit, &it, &rel, &err);
   }
   if (iters) *iters = it;
   if (rel_res) *rel_res = rel;

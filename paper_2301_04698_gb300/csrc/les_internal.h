@@ -348,6 +348,12 @@ namespace les {
 int unet_predict(les_unet* u, int precision, const void* b, void* psi0, cudaStream_t st, std::string* err);
 int unet_grid(const les_unet* u);
 
+// Flexible CG with the learned network as the preconditioner (les_fcg.cu);
+// *fallbacks counts the iterations that took z = r.
+template <typename T>
+int poisson_solve_fcg(const SolverArgs<T>& a, les_unet* model, const T* b, T* x, double tol, int maxit, int* iters,
+                      double* rel, int* fallbacks, std::string* err);
+
 // Solve A x = b; returns LES_OK / LES_ERR_NOT_CONVERGED / LES_ERR_CUDA.
 template <typename T>
 int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxit, int* iters,

@@ -93,6 +93,7 @@ class Case:
     omega: float = 2.0 / 3.0
     solver_path: int = 0       # 0: persistent CG launch when eligible, 1: per-phase launches
     advection: str = "quick"   # "quick" | "weno3" (WENO3 with the local Lax-Friedrichs flux)
+    precond: str = "none"      # "none" | "learned" (flexible CG with the network as preconditioner)
     physics: tuple = ("adv", "sgs")
     cs: float = 0.18
     pr: float = 0.4

@@ -63,7 +63,7 @@ class LesConfig(C.Structure):
         ("shf", C.c_double), ("lhf", C.c_double), ("rad_f0", C.c_double), ("rad_f1", C.c_double),
         ("rad_kappa", C.c_double), ("theta0", C.c_double), ("p00", C.c_double),
         ("sat_tol", C.c_double), ("sat_maxit", C.c_int32), ("solver_path", C.c_int32),
-        ("advection", C.c_int32), ("reserved_i", C.c_int32), ("reserved", C.c_double * 3),
+        ("advection", C.c_int32), ("precond", C.c_int32), ("reserved", C.c_double * 3),
     ]
 
 
@@ -235,6 +235,7 @@ def config_from_case(case) -> LesConfig:
     c.sat_maxit = int(case.sat_maxit)
     c.solver_path = int(getattr(case, "solver_path", 0))
     c.advection = {"quick": 0, "weno3": 1}[getattr(case, "advection", "quick")]
+    c.precond = {"none": 0, "learned": 1}[getattr(case, "precond", "none")]
     return c
 
 

@@ -241,3 +241,56 @@ def test_trained_network_against_plain_first_guesses(les_mod, loss):
     assert err1 < 0.6
     for mode in ("zero", "prev", "learned"):
         assert ev[mode]["not_converged"] == 0 and ev[mode]["iters_per_step"] > 0
+
+
+def test_learned_preconditioner_flexible_cg(les_mod):
+    """Flexible CG with the network as the preconditioner (precond "learned").
+    An untrained network answers 0, so every iteration takes the fallback
+    z = -r: the solve is then the plain CG -- the same iteration count within
+    two and the same solution.  With a network trained on solver pairs every
+    solve still reaches the tolerance (the plain iteration is the judge);
+    its iterations and time are reported next to the plain solve's."""
+    import time
+
+    from paper_2301_04698_gb300 import learned as L
+    B, P = L.generate_pairs([300, 301, 302, 303], 10, n=32)
+    case = inputs.tgv(32, steps_tol=1e-6)
+    plain = les_mod.Simulation(case)
+    fcg = les_mod.Simulation(case.replace(precond="learned"))
+    untrained = les_mod.UNet(32, max_batch=1)
+    untrained.set_weights(L.init_weights(0))
+    les_mod.attach_model(fcg, untrained)
+    for i in (0, 40, 100):
+        b = B[i].double().contiguous()
+        x0 = torch.zeros_like(b)
+        _, it0, rel0 = plain.poisson_solve(b, x0, 1e-6, 5000)
+        x1 = torch.zeros_like(b)
+        _, it1, rel1 = fcg.poisson_solve(b, x1, 1e-6, 5000)
+        assert rel1 <= 1e-6 and abs(it1 - it0) <= 2, (it0, it1)
+        assert rel(x1.cpu().numpy(), x0.cpu().numpy()) < 1e-5
+    model = les_mod.UNet(32, max_batch=16)
+    model.set_weights(L.init_weights(0))
+    model.set_loss("energy")
+    model.out_scale = L.output_scale(B[16:], P[16:])
+    L.train(model, B[16:], P[16:], steps=400, batch=16)
+    trained = les_mod.UNet(32, max_batch=1)
+    trained.set_weights(model.get_weights())
+    trained.out_scale = model.out_scale
+    les_mod.attach_model(fcg, trained)
+    stats = []
+    for i in range(0, 16, 4):     # held-out pairs
+        b = B[i].double().contiguous()
+        x0 = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, it0, _ = plain.poisson_solve(b, x0, 1e-6, 5000)
+        t1 = time.perf_counter()
+        x1 = torch.zeros_like(b)
+        rc, it1, rel1 = fcg.poisson_solve(b, x1, 1e-6, 5000, allow_not_converged=True)
+        t2 = time.perf_counter()
+        assert rc == les_mod.LES_OK and rel1 <= 1e-6
+        assert rel(x1.cpu().numpy(), x0.cpu().numpy()) < 1e-4
+        stats.append((it0, it1, (t1 - t0) * 1e3, (t2 - t1) * 1e3))
+    s = np.array(stats)
+    print(f"plain CG {s[:, 0].mean():.1f} iterations {s[:, 2].mean():.2f} ms; learned flexible CG "
+          f"{s[:, 1].mean():.1f} iterations {s[:, 3].mean():.2f} ms per solve")
