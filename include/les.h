@@ -346,8 +346,13 @@ const char *les_dd_last_error(const les_dd *d);
  * together.  les_ensemble_step runs les_step(hs[i], nsteps, &stats[i]) for
  * the m distinct handles concurrently, one host thread per handle, each on its
  * own device and stream (give every handle its own stream, les_set_stream,
- * for the members' kernels to overlap).  The members' persistent CG solves
- * run one at a time; their stencil kernels overlap.  stats: optional array
+ * for the members' kernels to overlap).  The members' stencil kernels
+ * overlap freely.  Their persistent CG solves share the device's SMs: a
+ * member whose les_tuning.cg_max_blocks caps its solve at B blocks (B at
+ * most the SM count) holds B SMs while the solve runs, an uncapped member
+ * all of them; so members capped at a share of the SMs solve together, and
+ * uncapped ones one at a time (the blocks of a persistent solve must all be
+ * resident at once).  stats: optional array
  * of m; failed: optional, the index of the first member whose status is
  * returned (-1 if none).  Returns LES_OK, LES_ERR_NOT_CONVERGED (state valid)
  * or the first other error; LES_ERR_INVALID_ARG for m <= 0, m > 1024, a null

@@ -229,6 +229,7 @@ SolverArgs<T> solver_args(les_handle* h) {
   SolverArgs<T> s;
   s.g = make_grid<T>(h->cfg, 8);
   s.lc = tile_launch(s.g, h->L.max_blocks);
+  s.nsm = h->L.max_blocks / 8;
   s.st = h->st;
   s.op = h->cfg.poisson_op;
   s.solver = h->cfg.solver;

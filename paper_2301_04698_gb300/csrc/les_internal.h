@@ -305,6 +305,7 @@ struct SolverArgs {
   T* q;
   Profiler* prof;
   FusedBar* bar = nullptr;          // persistent-solver barrier (workspace)
+  int nsm = 0;                      // SMs of the device (the persistent solves' budget)
   int guard = 0;                    // restart from x = 0 if ||b - A x0|| > ||b|| (learned guesses)
   T* e0 = nullptr;                  // extra vectors for the one-barrier variant
   T* e1 = nullptr;

@@ -10,8 +10,10 @@
 // are launched back to back and the host only polls the control block between
 // batches.  Weighted Jacobi (the paper's solver) uses one kernel per sweep.
 #include <algorithm>
+#include <memory>
 #include <string>
 
+#include <condition_variable>
 #include <mutex>
 
 #include "les_internal.h"
@@ -301,10 +303,44 @@ cudaError_t launch_apply(const SolverArgs<T>& a, int op, const T* x, T* y) {
   return cudaGetLastError();
 }
 
-std::mutex& persistent_solve_lock() {
-  static std::mutex m;
-  return m;
+// Persistent CG launches spin on their own grid barrier, so every block of
+// a launch must be resident at once.  Solves of different handles (ensemble
+// members stepped from several host threads) share the device's SMs through
+// a budget: a launch capped at B <= nsm blocks (les_tuning.cg_max_blocks)
+// holds B units, an uncapped one all nsm, until it returns.  Launches whose
+// caps sum to at most the SM count are then resident together (each block
+// fits on an SM, and the non-persistent kernels beside them finish), and
+// uncapped solves run one at a time.
+struct SmBudget {
+  std::mutex m;
+  std::condition_variable cv;
+  int used = 0;
+};
+SmBudget& sm_budget(int dev) {
+  static SmBudget b[64];
+  return b[(dev >= 0 && dev < 64) ? dev : 0];
 }
+class SmHold {
+ public:
+  SmHold(int dev, int units, int total) : b_(sm_budget(dev)), units_(std::max(1, std::min(units, total))) {
+    std::unique_lock<std::mutex> lk(b_.m);
+    b_.cv.wait(lk, [&] { return b_.used + units_ <= total; });
+    b_.used += units_;
+  }
+  ~SmHold() {
+    {
+      std::lock_guard<std::mutex> lk(b_.m);
+      b_.used -= units_;
+    }
+    b_.cv.notify_all();
+  }
+  SmHold(const SmHold&) = delete;
+  SmHold& operator=(const SmHold&) = delete;
+
+ private:
+  SmBudget& b_;
+  int units_;
+};
 
 template <typename T>
 int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxit, int* iters, double* rel,
@@ -313,13 +349,18 @@ int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxi
   // one-pass kernel with 64 x 16 columns (variant 4, and variant 0 for FP32
   // grids of whole columns), the two-phase streaming kernel on tile-aligned
   // grids (variant 0 or 2) or the one-pass kernel (variant 0 on other grids,
-  // or variant 3); variant 1 is Chronopoulos-Gear.  Persistent solves of different handles (ensemble
-  // members stepped from several host threads) run one at a time: each
-  // grid spins on its own barrier and is sized to fill the GPU, so two of
-  // them must never wait for each other's SMs.
+  // or variant 3); variant 1 is Chronopoulos-Gear.  Persistent solves of
+  // different handles (ensemble members stepped from several host threads)
+  // share the SMs through the budget above: capped ones run together, an
+  // uncapped one alone.
   const bool cg_c = a.op == LES_OP_COMPACT && a.solver == LES_SOLVER_CG;
-  std::unique_lock<std::mutex> one_at_a_time(persistent_solve_lock(), std::defer_lock);
-  if (a.bar && a.fused) one_at_a_time.lock();
+  std::unique_ptr<SmHold> hold;
+  if (a.bar && a.fused) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int nsm = std::max(1, a.nsm);
+    hold.reset(new SmHold(dev, a.fused->max_blocks < nsm ? a.fused->max_blocks : nsm, nsm));
+  }
   const int var = a.fused ? a.fused->variant : -1;
   const bool tiled = a.fused && fused_cg_eligible(a.g, a.op, a.solver, a.fused->ty);
   if (a.bar && cg_c && var == 0 && a.fused->resident == 0) {

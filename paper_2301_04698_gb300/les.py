@@ -522,12 +522,21 @@ class Ensemble:
     """Independent members (each its own Simulation and stream) stepped
     together through les_ensemble_step."""
 
-    def __init__(self, cases, device=None):
+    def __init__(self, cases, device=None, share: int = 1):
+        """share > 1 caps every member's persistent CG solve at 1/share of the
+        SMs (les_tuning.cg_max_blocks), so that up to `share` members solve
+        at once; 1 leaves the solves uncapped (one at a time)."""
         import torch
         self.torch = torch
         self.members = [Simulation(c, device=device, stream=torch.cuda.Stream(device=device)) for c in cases]
         self.lib = self.members[0].lib
         self.cells = sum(m.n for m in self.members)
+        self.share = share
+        if share > 1:
+            nsm = torch.cuda.get_device_properties(device if device is not None else
+                                                   torch.cuda.current_device()).multi_processor_count
+            for m in self.members:
+                m.set_tuning(cg_max_blocks=max(1, nsm // share))
 
     def set_states(self, states) -> None:
         for m, st in zip(self.members, states):

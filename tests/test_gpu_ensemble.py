@@ -44,6 +44,28 @@ def test_ensemble_matches_solo_runs(les_mod):
     ens.close()
 
 
+@pytest.mark.parametrize("share", [2, 4])
+def test_ensemble_shared_sms_matches_solo_runs(les_mod, share):
+    """Members capped at 1/share of the SMs solve concurrently; each member
+    still ends bit-identical to the same member run alone with the same
+    tuning (its grid, hence its order of sums, is the same)."""
+    cases = _members()
+    ens = les_mod.Ensemble(cases, share=share)
+    ens.set_states([inputs.initial_state(c) for c in cases])
+    stats = ens.step(2)
+    assert all(s["not_converged"] == 0 for s in stats)
+    torch.cuda.synchronize()
+    for c, m in zip(cases, ens.members):
+        solo = les_mod.Simulation(c)
+        solo.set_state(inputs.initial_state(c))
+        solo.set_tuning(cg_max_blocks=m.tuning()["cg_max_blocks"])
+        solo.step(2)
+        for f in ("u", "v", "w", "p", "theta_l", "q_t"):
+            assert np.array_equal(m.get(f), solo.get(f)), (c.name, f)
+        solo.close()
+    ens.close()
+
+
 def test_ensemble_member_against_oracle(les_mod):
     from oracle import Oracle
     c = _members()[1]
