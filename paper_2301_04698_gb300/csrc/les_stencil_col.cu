@@ -221,13 +221,27 @@ __global__ void __launch_bounds__(CW* CR) k_rhs_col(ColArgs<T> a) {
 #pragma unroll
       for (int c = 0; c < V; ++c) wz[q].v[c] *= sg;
     }
+    // the next plane's own-row inputs are loaded one step ahead, so that
+    // their latency overlaps a step of arithmetic
+    T sw;
+    Lane<T> wn = ldv(a.ow + (size_t)zplane(g, k0 + 1, G_ODD, sw) * plane + row + i);
+    Lane<T> pn = compact ? ldv(a.psi + (size_t)zplane(g, k0 + 2, G_EVEN, sg) * plane + row + i) : Lane<T>{};
+    Lane<T> un = ldv(a.ou + (size_t)k0 * plane + row + i);
+    T swn = sw;
     for (int k = k0; k < k1; ++k) {
       const size_t pk = (size_t)k * plane;
-      wz[2] = ldv(a.ow + (size_t)zplane(g, k + 1, G_ODD, sg) * plane + row + i);
+      wz[2] = wn;
 #pragma unroll
-      for (int c = 0; c < V; ++c) wz[2].v[c] *= sg;
+      for (int c = 0; c < V; ++c) wz[2].v[c] *= swn;
+      if (compact) ps[4] = pn;
       // u^ with one node beyond each lane end; v^ on the rows j -+ 1
-      const Lane<T> uc = ldv(a.ou + pk + row + i);
+      const Lane<T> uc = un;
+      if (k + 1 < k1) {
+        wn = ldv(a.ow + (size_t)zplane(g, k + 2, G_ODD, sw) * plane + row + i);
+        swn = sw;
+        if (compact) pn = ldv(a.psi + (size_t)zplane(g, k + 3, G_EVEN, sg) * plane + row + i);
+        un = ldv(a.ou + pk + plane + row + i);
+      }
       T ue_lo[1] = {edge ? __ldg(a.ou + pk + row + xb) : T(0)};
       T ue_hi[1] = {edge ? __ldg(a.ou + pk + row + xa) : T(0)};
       const Lane<T> vm = ldv(a.ov + pk + rm1 + i), vp = ldv(a.ov + pk + rp1 + i);
@@ -235,7 +249,6 @@ __global__ void __launch_bounds__(CW* CR) k_rhs_col(ColArgs<T> a) {
       const T r0 = g.prof(ph.rho0, k), rzm = g.prof(ph.rho0, k - 1), rzp = g.prof(ph.rho0, k + 1);
       Lane<T> out;
       if (compact) {
-        ps[4] = ldv(a.psi + (size_t)zplane(g, k + 2, G_EVEN, sg) * plane + row + i);
         T pe_lo[2] = {edge ? __ldg(a.psi + pk + row + xb) : T(0), edge ? __ldg(a.psi + pk + row + xa) : T(0)};
         const Lane<T> qm1 = ldv(a.psi + pk + rm1 + i), qp1 = ldv(a.psi + pk + rp1 + i);
         const Lane<T> qm2 = ldv(a.psi + pk + rm2 + i), qp2 = ldv(a.psi + pk + rp2 + i);
