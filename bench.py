@@ -90,6 +90,9 @@ def parse():
     ap.add_argument("--advection", default="quick", choices=("quick", "weno3"),
                     help="advection scheme of the timed workload")
     ap.add_argument("--no-autotune", action="store_true", help="ensemble workload: keep the default tuning")
+    ap.add_argument("--ensemble-share", type=int, default=1,
+                    help="ensemble workload: cap each member's persistent CG at 1/share of the SMs so that up to "
+                         "share members solve at once (1: one at a time)")
     ap.add_argument("--learned-seeds", type=int, default=20, help="training runs for the learned leg")
     ap.add_argument("--learned-train-steps", type=int, default=1500)
     ap.add_argument("--no-second-record", action="store_true",
@@ -221,28 +224,39 @@ class Clocks:
                 "samples_in_region": len([r for r in use if t0 is not None and t1 is not None and t0 <= r[0] <= t1])}
 
 
-def src_hash() -> str:
+# the source files whose change invalidates a kernel's DRAM-traffic record
+TRAFFIC_SOURCES = {
+    "cg_wave": ("les_cg_wave.cu", "les_gridsync.cuh", "les_common.cuh"),
+    "scalar": ("les_predict_col.cu", "les_common.cuh"),
+    "rhs": ("les_stencil_col.cu",),
+    "correct": ("les_stencil_col.cu",),
+}
+
+
+def src_hash(files) -> str:
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2301_04698_gb300", "csrc")
-    for f in sorted(os.listdir(cs)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(cs, f), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "les.h"), "rb").read())
+    for f in files:
+        h.update(open(os.path.join(cs, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str, workload_name: str):
+def traffic_for(kernel: str, units: float):
+    """DRAM bytes of one launch of `kernel` processing `units` (cells, or
+    cell-iterations for a CG solve), from the per-unit figure of an ncu
+    capture in profiles/traffic.json -- None when there is no record or the
+    kernel's source has changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
+        ent = d.get(kernel)
+        if not ent or ent.get("src") != src_hash(ent["files"]):
+            return None
+        return float(ent["dram_bytes_per_unit"]) * float(units)
     except Exception:
         return None
-    ent = d.get(f"{workload_name}:{kernel}")
-    if not ent or ent.get("src") != src_hash():
-        return None
-    return ent.get("dram_bytes_per_launch")
 
 
 # ---------------------------------------------------------------------------
@@ -357,7 +371,7 @@ def bench_ensemble(args, rank, world, local):
 
     from paper_2301_04698_gb300 import inputs, les
     cases = workload(args.workload, seed=1 + rank)
-    ens = les.Ensemble(cases)
+    ens = les.Ensemble(cases, share=args.ensemble_share)
     ens.set_states([inputs.initial_state(c) for c in cases])
     tuned = []
     for m in ens.members:
@@ -365,6 +379,9 @@ def bench_ensemble(args, rank, world, local):
             tuned.append(None)
         else:
             tuned.append(les.autotune(m)["tuning"])
+        if args.ensemble_share > 1:   # the share's cap wins over a tuned one
+            nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            m.set_tuning(cg_max_blocks=max(1, nsm // args.ensemble_share))
     for _ in range(args.warmup):
         ens.step(1, allow_not_converged=True)
     torch.cuda.synchronize()
@@ -407,7 +424,8 @@ def bench_ensemble(args, rank, world, local):
             "config": {"workload": WORKLOAD_DESC[args.workload], "members": [c.name for c in cases],
                        "cells": ens.cells, "K": cases[0].K, "tol": cases[0].tol,
                        "timing": "wall clock between device synchronisations (members on their own streams)",
-                       "l2": "flushed (256 MiB write) before every timed step", "autotuned": tuned},
+                       "l2": "flushed (256 MiB write) before every timed step", "autotuned": tuned,
+                       "share": args.ensemble_share},
             "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk,
             "poisson": {"iters_per_step": iters / args.steps},
             "one_after_another_ms_per_step": 1e3 * seq_s / args.steps,
@@ -577,10 +595,11 @@ def main():
     sim.profile_reset()
     sim.profile(True)
     torch.cuda.synchronize()
+    prof_iters = 0
     with torch.cuda.stream(stream):
         for s in range(aux_prof):
             flush.zero_()
-            sim.step(1, allow_not_converged=True)
+            prof_iters += sim.step(1, allow_not_converged=True)["iters_total"]
     kstats = sim.profile_read()
     sim.profile(False)
     total_k = sum(k["total_ms"] for k in kstats) or 1.0
@@ -588,20 +607,29 @@ def main():
     hbm, peak_kind = peaks()
     mean_ms = top["total_ms"] / max(top["timed"], 1)
     achieved = top["bytes_per_launch"] / (mean_ms / 1e3) / 1e9
+    # units of one launch of the top kernel for its traffic record: cells, or
+    # cell-iterations for a CG solve (the profiled steps' mean per solve)
+    top_units = case.n * (prof_iters / max(top["launches"], 1) if top["name"].startswith("cg") else 1.0)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic_for(top["name"], args.workload), "kernel": top["name"],
+                "traffic": traffic_for(top["name"], top_units), "kernel": top["name"],
                 "share": top["total_ms"] / total_k, "mean_launch_us": mean_ms * 1e3,
                 "bytes_per_launch": top["bytes_per_launch"], "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "frac_of_8tbs": achieved / 8000.0, "profiled_steps": aux_prof}
+                "frac_of_8tbs": achieved / 8000.0, "profiled_steps": aux_prof,
+                "traffic_source": "profiles/traffic.json: DRAM bytes per unit of an ncu capture on 512x512x64, "
+                                  "scaled to this launch's units"}
     kernels = {}
     for k in kstats:
         mean = k["total_ms"] / max(k["timed"], 1)
         gbs = k["bytes_per_launch"] / (mean / 1e3) / 1e9 if k["total_ms"] > 0 else None
+        units = case.n * (prof_iters / max(k["launches"], 1) if k["name"].startswith("cg") else 1.0)
+        tr = traffic_for(k["name"], units)
         kernels[k["name"]] = {"launches": k["launches"], "ms": round(k["total_ms"], 4),
                               "share": round(k["total_ms"] / total_k, 4), "mean_us": round(mean * 1e3, 2),
                               "gbs": round(gbs, 1) if gbs else None,
-                              "frac": round(gbs / hbm, 4) if gbs else None}
+                              "frac": round(gbs / hbm, 4) if gbs else None,
+                              "bytes_per_launch": k["bytes_per_launch"],
+                              "traffic_per_launch": round(tr) if tr else None}
 
     # ---- end to end through the C ABI with host buffers ----------------------
     host = {k: snap[k].cpu().pin_memory() for k in names}

@@ -79,17 +79,18 @@ def test_clocks_without_nvidia_smi(tmp_path, monkeypatch):
 def test_traffic_record_follows_the_source(tmp_path, monkeypatch):
     root = tmp_path
     (root / "profiles").mkdir()
-    (root / "include").mkdir()
     cs = root / "paper_2301_04698_gb300" / "csrc"
     cs.mkdir(parents=True)
     (cs / "k.cu").write_text("// kernel\n")
-    (root / "include" / "les.h").write_text("// abi\n")
+    (cs / "other.cu").write_text("// another kernel\n")
     monkeypatch.setattr(bench, "ROOT", str(root))
-    h = bench.src_hash()
-    rec = {"cbl128:cg_resident": {"src": h, "dram_bytes_per_launch": 1234}}
+    h = bench.src_hash(["k.cu"])
+    rec = {"cg_wave": {"files": ["k.cu"], "src": h, "per": "cell-iteration", "dram_bytes_per_unit": 25.0}}
     (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
-    assert bench.traffic_for("cg_resident", "cbl128") == 1234
-    assert bench.traffic_for("cg_resident", "tgv_large") is None
+    assert bench.traffic_for("cg_wave", 1000) == 25000.0
+    assert bench.traffic_for("scalar", 1000) is None
+    (cs / "other.cu").write_text("// another kernel, changed\n")   # not this kernel's source
+    assert bench.traffic_for("cg_wave", 1000) == 25000.0
     (cs / "k.cu").write_text("// kernel, changed\n")
-    assert bench.src_hash() != h
-    assert bench.traffic_for("cg_resident", "cbl128") is None
+    assert bench.src_hash(["k.cu"]) != h
+    assert bench.traffic_for("cg_wave", 1000) is None
