@@ -152,8 +152,8 @@ typedef struct les_config {
   int32_t  precond;          /* LES_PRECOND_NONE (default) |
                                 LES_PRECOND_LEARNED: flexible CG with the
                                 attached network (les_set_warm_model) as
-                                the preconditioner, z = net(r), or z = r
-                                where r.z <= 0; CG and the compact
+                                the preconditioner, z = net(r), or z = -r
+                                where r.net(r) >= 0; CG and the compact
                                 operator only; not in the paper        */
   double   reserved[3];
 } les_config;
@@ -310,9 +310,13 @@ typedef struct les_dd_ops {
    * y = y0, 3 north: y = y0 + ny/py - 1; each strip ordered with the
    * in-face index fastest, then z) to the neighbour on that side, and receive
    * the neighbours' opposite strips into recv[f] (recv[0] from the west
-   * neighbour's east strip, and so on; periodic neighbours wrap).  Called
-   * with the work enqueued on `stream`; on return recv must hold the data
-   * for work later enqueued on that stream.  Return 0 on success. */
+   * neighbour's east strip, and so on; periodic neighbours wrap).  A strip
+   * of 0 bytes is neither sent nor received (les_dd_halo_exchange moves the
+   * x strips and the y strips in two calls; its strips are LES_DD_HALO nodes
+   * deep and hold several fields, packed as the library unpacks them; every
+   * rank passes the same sizes).  Called with the work enqueued on `stream`;
+   * on return recv must hold the data for work later enqueued on that
+   * stream.  Return 0 on success. */
   int (*exchange)(void *ctx, void *const *send, void *const *recv, const size_t *bytes, void *stream);
   /* Replace each of the n host doubles by its sum over all ranks; return 0
    * on success. */
@@ -339,6 +343,56 @@ int les_dd_local_shape(const les_dd *d, int32_t *nx, int32_t *ny, int32_t *nz, i
 int les_dd_poisson_solve(les_dd *d, const les_dd_ops *ops, const void *d_rhs, void *d_x, double rtol,
                          int32_t maxit, int32_t *iters, double *rel_res);
 const char *les_dd_last_error(const les_dd *d);
+
+/* ---- the decomposed step ---------------------------------------------------
+ * The whole step (Sec. 2.4: thermodynamics, the scalar and momentum
+ * predictors, the Poisson solve and the correction) on one sub-domain of the
+ * partition above, the paper's parallel LES (Sec. 2.5), with halo exchanges
+ * before the stencil passes and the solver's sums reduced over all ranks.
+ * The sub-domain's fields live in an ordinary handle (les_init with the
+ * configuration from les_dd_step_config) whose grid is the sub-domain widened
+ * by LES_DD_HALO = 2 nodes on each side in x and y, (nx/px + 4) x (ny/py + 4)
+ * x nz: its node (i, j, k) is global node (x0 + i - 2, y0 + j - 2, k),
+ * wrapped periodically.  The handle's stencil stages run on that grid as on a
+ * periodic domain.  No stencil of the step reaches further than two nodes
+ * along x or y (the upwind-biased QUICK face value, the Smagorinsky stress
+ * with nu_t at the neighbouring nodes, the App. A term of the right side), so
+ * with fresh halos the owned nodes get the values of the undivided domain,
+ * bit for bit, and the halo nodes' values are discarded.  One step is
+ *     exchange u v w p theta_l q_t;  BEGIN;
+ *     for each sub-iteration k:  (k > 0: exchange u v w theta_l q_t);
+ *         SCALAR;  MOMENTUM;  exchange u^ v^;  les_dd_stage_solve;
+ *         exchange psi;  CORRECT;
+ *     END
+ * with BEGIN ... CORRECT, END by les_stage (the driver is
+ * paper_2301_04698_gb300.decomp.decomposed_step).  The time step must be fixed
+ * (cfg.dt > 0, or les_set_dt) and the same on every rank.  Diagnostics of
+ * the widened handle (les_diagnostics) include its halo nodes. */
+#define LES_DD_HALO 2
+#define LES_DD_MAX_FIELDS 8
+/* *out = the global configuration of d with nx, ny of the widened sub-domain. */
+int les_dd_step_config(const les_dd *d, les_config *out);
+/* Fill the LES_DD_HALO-deep x and y halos of nfields (1 .. LES_DD_MAX_FIELDS)
+ * fields of the widened handle h (ids as les_get_state: LES_U, LES_THETA_L
+ * (the current buffer), LES_UHAT, LES_PSI, ...) from the neighbours' owned
+ * nodes: ops->exchange is called twice, first with the west and east strips
+ * (the owned rows), then with the south and north strips over the whole
+ * widened width, which carries the corner nodes.  Runs on h's stream.
+ * LES_ERR_INVALID_ARG if h's grid is not d's widened sub-domain, a field id
+ * is bad or repeated, or nfields is out of range; LES_ERR_CUDA if a launch or
+ * the callback fails. */
+int les_dd_halo_exchange(les_dd *d, les_handle *h, const les_dd_ops *ops, int32_t nfields, const int32_t *fields);
+/* The SOLVE stage of the widened handle h (in les_stage's order, in place of
+ * les_stage(h, LES_STAGE_SOLVE)), over the partition: the Poisson right side
+ * (Eq. pressure_correction with App. A) is formed again from h's u^ (its halo
+ * exchanged) and psi, the solve runs on the owned nodes by the decomposed CG
+ * above from h's first guess (LES_WARM_ZERO or LES_WARM_PREV), and psi's owned
+ * nodes receive the solution (its halo is stale until exchanged).  Every rank
+ * calls it with the same configuration.  Returns as les_stage's solve stage
+ * (LES_OK, LES_ERR_NOT_CONVERGED, ...); LES_ERR_STATE out of order;
+ * LES_ERR_INVALID_ARG for a handle that is not d's widened sub-domain or asks
+ * for the learned warm start or preconditioner. */
+int les_dd_stage_solve(les_dd *d, les_handle *h, const les_dd_ops *ops, les_step_stats *stats);
 
 /* ---- ensembles -----------------------------------------------------------------
  * Independent members -- different grids, seeds and forcings, as in ensembles

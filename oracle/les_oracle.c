@@ -575,7 +575,18 @@ void orc_momentum_stage(void *vs) {
         }
       }
 
-  /* Poisson right-hand side */
+  orc_poisson_rhs(s);
+}
+
+/* The Poisson right side (Eq. pressure_correction with App. A) from the
+ * predicted momentum u^ and the last increment psi:
+ * rhs = alpha0 / dt D(rho0 u^) - C^k (compact operator), or D(rho0 u^) / dt. */
+void orc_poisson_rhs(void *vs) {
+  orc *s = (orc *)vs;
+  const int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
+  const double dt = s->dt;
+  const double *hat[3] = {s->f[ORC_UH], s->f[ORC_VH], s->f[ORC_WH]};
+  const int gh[3] = {GH_UV, GH_UV, GH_ODD};
   double *rhs = s->f[ORC_RHS];
   const double *psi = s->f[ORC_PSI];
 #pragma omp parallel for schedule(static)

@@ -84,6 +84,7 @@ void    orc_profiles(void *s, double *rho0, double *p0);
 int  orc_begin_step(void *s);
 void orc_scalar_stage(void *s);
 void orc_momentum_stage(void *s);
+void orc_poisson_rhs(void *s); /* the right side alone, from u^ and psi */
 int  orc_solve_stage(void *s, int32_t *iters, double *res);
 void orc_correct_stage(void *s);
 void orc_end_step(void *s);

@@ -83,7 +83,7 @@ def _load():
         lib.orc_profiles.argtypes = [vp, dp, dp]
         lib.orc_begin_step.restype = C.c_int
         lib.orc_begin_step.argtypes = [vp]
-        for fn in ("orc_scalar_stage", "orc_momentum_stage", "orc_correct_stage", "orc_end_step"):
+        for fn in ("orc_scalar_stage", "orc_momentum_stage", "orc_poisson_rhs", "orc_correct_stage", "orc_end_step"):
             getattr(lib, fn).argtypes = [vp]
         lib.orc_solve_stage.restype = C.c_int
         lib.orc_solve_stage.argtypes = [vp, ip, dp]
@@ -194,6 +194,11 @@ class Oracle:
 
     def momentum_stage(self) -> None:
         self._lib.orc_momentum_stage(self._h)
+
+    def poisson_rhs(self) -> None:
+        """the Poisson right side alone, from u^ and psi (the momentum stage
+        ends with it)"""
+        self._lib.orc_poisson_rhs(self._h)
 
     def solve_stage(self):
         it = C.c_int32(0)

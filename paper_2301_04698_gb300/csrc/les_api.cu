@@ -363,6 +363,19 @@ int stage_scalar(les_handle* h) {
   return LES_OK;
 }
 
+// the Poisson right side (Eq. pressure_correction with App. A) from u^ and psi
+template <typename T>
+cudaError_t launch_stage_rhs(les_handle* h, const StageArgs<T>& a) {
+  T* const* F = (T* const*)h->fixed;
+  if ((h->fused.stencil_path == 0 || h->fused.stencil_path == 4) && col_eligible<T>(a.g))
+    return launch_rhs_col<T>(a, h->L.max_blocks, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI],
+                             F[B_RHS]);
+  if (h->fused.stencil_path == 0 || h->fused.stencil_path == 3 || h->fused.stencil_path == 4)
+    return launch_rhs_roll<T>(a, h->L.max_blocks, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI],
+                              F[B_RHS]);
+  return launch_rhs<T>(a, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI], F[B_RHS]);
+}
+
 template <typename T>
 int stage_momentum(les_handle* h) {
   auto a = stage_args<T>(h);
@@ -388,15 +401,7 @@ int stage_momentum(les_handle* h) {
                                 F[B_P], F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess)
       return h->cuda_fail(e, "momentum predictor");
   }
-  if ((h->fused.stencil_path == 0 || h->fused.stencil_path == 4) && col_eligible<T>(a.g))
-    e = launch_rhs_col<T>(a, h->L.max_blocks, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI],
-                          F[B_RHS]);
-  else if (h->fused.stencil_path == 0 || h->fused.stencil_path == 3 || h->fused.stencil_path == 4)
-    e = launch_rhs_roll<T>(a, h->L.max_blocks, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI],
-                           F[B_RHS]);
-  else
-    e = launch_rhs<T>(a, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI], F[B_RHS]);
-  if (e != cudaSuccess) return h->cuda_fail(e, "poisson rhs");
+  if ((e = launch_stage_rhs<T>(h, a)) != cudaSuccess) return h->cuda_fail(e, "poisson rhs");
   return LES_OK;
 }
 
@@ -451,6 +456,58 @@ int stage_solve(les_handle* h, les_step_stats* st) {
   }
   if (rc == LES_ERR_NOT_CONVERGED) h->err = "Poisson solve reached maxit";
   return rc;
+}
+
+// The solve stage over a domain decomposition: h holds the widened
+// sub-domain of d (LES_DD_HALO nodes on each side in x and y).
+template <typename T>
+int stage_solve_dd(les_handle* h, les_dd* d, const les_dd_ops* ops, les_step_stats* st) {
+  const size_t bytes = h->n * sizeof(T);
+  cudaError_t e;
+  auto a = stage_args<T>(h);
+  // the halo of u^ is fresh now; the momentum stage's right side was not
+  if ((e = launch_stage_rhs<T>(h, a)) != cudaSuccess) return h->cuda_fail(e, "poisson rhs");
+  T* psi = (T*)h->fixed[B_PSI];
+  const int k = std::min(h->sub, h->cfg.n_subiter - 1);
+  if (h->cfg.warm_start == LES_WARM_PREV) {
+    if ((e = cudaMemcpyAsync(psi, h->prev[k], bytes, cudaMemcpyDeviceToDevice, h->st)) != cudaSuccess)
+      return h->cuda_fail(e, "warm start");
+  } else if ((e = cudaMemsetAsync(psi, 0, bytes, h->st)) != cudaSuccess) {
+    return h->cuda_fail(e, "memset");
+  }
+  // the decomposed CG runs on the sub-domain's own stream
+  if ((e = cudaStreamSynchronize(h->st)) != cudaSuccess) return h->cuda_fail(e, "solve set-up");
+  const int H = LES_DD_HALO;
+  const les::DdLayout lay{(long long)H * h->cfg.nx + H, (long long)h->cfg.nx * h->cfg.ny, h->cfg.nx};
+  int iters = 0;
+  double rel = 0;
+  std::string err;
+  const int rc = les::dd_solve<T>(d, ops, (const T*)h->fixed[B_RHS], psi, lay, h->cfg.poisson_tol,
+                                  h->cfg.poisson_maxit, &iters, &rel, &err);
+  if (rc != LES_OK && rc != LES_ERR_NOT_CONVERGED) return h->fail(rc, err);
+  if (h->cfg.warm_start == LES_WARM_PREV) {
+    if ((e = cudaMemcpyAsync(h->prev[k], psi, bytes, cudaMemcpyDeviceToDevice, h->st)) != cudaSuccess)
+      return h->cuda_fail(e, "warm start save");
+  }
+  if (st) {
+    st->solves += 1;
+    st->iters_total += iters;
+    st->iters_max = std::max(st->iters_max, iters);
+    st->res_max = std::max(st->res_max, rel);
+    if (rc == LES_ERR_NOT_CONVERGED) st->not_converged += 1;
+  }
+  if (rc == LES_ERR_NOT_CONVERGED) h->err = "Poisson solve reached maxit";
+  return rc;
+}
+
+// h is the widened sub-domain of d
+bool dd_matches(const les_dd* d, const les_handle* h) {
+  int nxe, nye, nz;
+  les::dd_widened_shape(d, &nxe, &nye, &nz);
+  const les_config& g = les::dd_config(d);
+  const les_config& c = h->cfg;
+  return c.nx == nxe && c.ny == nye && c.nz == nz && c.precision == g.precision && c.bc_z == g.bc_z &&
+         c.dx == g.dx && c.dy == g.dy && c.dz == g.dz && c.poisson_op == LES_OP_COMPACT;
 }
 
 template <typename T>
@@ -739,6 +796,47 @@ int les_step(les_handle* h, int32_t nsteps, les_step_stats* stats) {
   }
   st->dt = h->dt;
   return worst;
+}
+
+int les_dd_step_config(const les_dd* d, les_config* out) {
+  if (!d || !out) return LES_ERR_INVALID_ARG;
+  int nxe, nye, nz;
+  les::dd_widened_shape(d, &nxe, &nye, &nz);
+  *out = les::dd_config(d);
+  out->nx = nxe;
+  out->ny = nye;
+  return LES_OK;
+}
+
+int les_dd_halo_exchange(les_dd* d, les_handle* h, const les_dd_ops* ops, int32_t nfields, const int32_t* fields) {
+  if (!d || !h || !ops || !ops->exchange || !fields) return LES_ERR_INVALID_ARG;
+  if (!dd_matches(d, h)) return h->fail(LES_ERR_INVALID_ARG, "the handle is not the widened sub-domain");
+  if (nfields < 1 || nfields > LES_DD_MAX_FIELDS) return h->fail(LES_ERR_INVALID_ARG, "bad field count");
+  void* ptr[LES_DD_MAX_FIELDS];
+  for (int q = 0; q < nfields; ++q) {
+    ptr[q] = h->field_ptr(fields[q]);
+    if (!ptr[q]) return h->fail(LES_ERR_INVALID_ARG, "bad field id");
+    for (int r = 0; r < q; ++r)
+      if (ptr[r] == ptr[q]) return h->fail(LES_ERR_INVALID_ARG, "repeated field");
+  }
+  std::string err;
+  const int rc = les::dd_halo_exchange(d, ops, ptr, nfields, h->st, &err);
+  if (rc != LES_OK) return h->fail(rc, err);
+  return LES_OK;
+}
+
+int les_dd_stage_solve(les_dd* d, les_handle* h, const les_dd_ops* ops, les_step_stats* stats) {
+  if (!d || !h || !ops || !ops->exchange || !ops->allreduce) return LES_ERR_INVALID_ARG;
+  if (!dd_matches(d, h)) return h->fail(LES_ERR_INVALID_ARG, "the handle is not the widened sub-domain");
+  if (h->cfg.warm_start == LES_WARM_LEARNED || h->cfg.precond != LES_PRECOND_NONE)
+    return h->fail(LES_ERR_INVALID_ARG, "the decomposed solve has no learned warm start or preconditioner");
+  if (h->next_stage != LES_STAGE_SOLVE)
+    return h->fail(LES_ERR_STATE, "solve stage called, expected " + std::to_string(h->next_stage));
+  const int rc = h->cfg.precision == 64 ? stage_solve_dd<double>(h, d, ops, stats)
+                                        : stage_solve_dd<float>(h, d, ops, stats);
+  if (rc == LES_OK || rc == LES_ERR_NOT_CONVERGED) h->next_stage = expected_after(h, LES_STAGE_SOLVE);
+  if (stats) stats->dt = h->dt;
+  return rc;
 }
 
 int les_ensemble_step(les_handle* const* hs, int32_t m, int32_t nsteps, les_step_stats* stats,

@@ -12,6 +12,11 @@
 // products of an iteration (p.q, r.r, r.q, q.q, FP64 over the sub-domain)
 // are summed over ranks by one caller-supplied all-reduce, and r'.r' =
 // r.r - 2 alpha r.q + alpha^2 q.q gives beta without a second reduction.
+//
+// The decomposed step keeps a sub-domain's fields in a handle widened by
+// LES_DD_HALO nodes on each side in x and y; this file also packs and unpacks
+// those fields' halos (two exchanges: x strips over the owned rows, then y
+// strips over the whole widened width, which carries the corners).
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -31,6 +36,10 @@ struct les_dd {
   void *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
   void *send[4] = {}, *recv[4] = {};
   size_t face_bytes[4] = {};
+  // strips of the decomposed step's field halos (LES_DD_HALO deep, up to
+  // LES_DD_MAX_FIELDS fields), fcap bytes each
+  void *fsend[4] = {}, *frecv[4] = {};
+  size_t fcap = 0;
   double* partials = nullptr;  // [4][nblk]
   double* sums = nullptr;      // [4]
   double host[4] = {};         // host copy of the sums
@@ -53,25 +62,88 @@ __host__ __device__ inline long long pidx(const DdGeom& g, int i, int j, int k) 
   return (long long)k * g.pstride + (long long)(j + 1) * g.rowlen + (i + 1);
 }
 
-// copy the unpadded local array into the padded interior (or back)
+// copy the caller's local array (node (i, j, k) at off + k sxy + j sx + i)
+// into the padded interior, or back
 template <typename T>
-__global__ void k_dd_in(DdGeom g, const T* __restrict__ src, T* __restrict__ dst) {
+__global__ void k_dd_in(DdGeom g, les::DdLayout lay, const T* __restrict__ src, T* __restrict__ dst) {
   const long long n = (long long)g.nx * g.ny * g.nz;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % g.nx);
     const int j = (int)((t / g.nx) % g.ny);
     const int k = (int)(t / ((long long)g.nx * g.ny));
-    dst[pidx(g, i, j, k)] = src[t];
+    dst[pidx(g, i, j, k)] = src[lay.off + k * lay.sxy + (long long)j * lay.sx + i];
   }
 }
 template <typename T>
-__global__ void k_dd_out(DdGeom g, const T* __restrict__ src, T* __restrict__ dst) {
+__global__ void k_dd_out(DdGeom g, les::DdLayout lay, const T* __restrict__ src, T* __restrict__ dst) {
   const long long n = (long long)g.nx * g.ny * g.nz;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % g.nx);
     const int j = (int)((t / g.nx) % g.ny);
     const int k = (int)(t / ((long long)g.nx * g.ny));
-    dst[t] = src[pidx(g, i, j, k)];
+    dst[lay.off + k * lay.sxy + (long long)j * lay.sx + i] = src[pidx(g, i, j, k)];
+  }
+}
+
+// halos of the decomposed step's fields.  The widened sub-domain is
+// nxe = nx + 2H by nye = ny + 2H by nz, owned nodes at [H, H + nx) x [H, H + ny).
+// Phase 0 (x): the west strip is the owned columns H .. 2H-1, the east strip
+// nx .. nx+H-1, over the owned rows; strip element ((f nz + k) ny + j) H + c.
+// Phase 1 (y): the south strip is the rows H .. 2H-1, the north strip
+// ny .. ny+H-1, over all nxe columns (the x halos filled in phase 0 carry
+// the corners); element ((f nz + k) H + r) nxe + i.
+struct FieldSet {
+  void* f[LES_DD_MAX_FIELDS];
+  int nf;
+};
+struct HaloGeom {
+  int nx, ny, nz, nxe, nye;  // owned, widened
+};
+__host__ __device__ inline long long fidx(const HaloGeom& g, int i, int j, int k) {
+  return ((long long)k * g.nye + j) * g.nxe + i;
+}
+template <typename T>
+__global__ void k_dd_fpack(HaloGeom g, FieldSet fs, int phase, T* __restrict__ a, T* __restrict__ b) {
+  constexpr int H = LES_DD_HALO;
+  const int len = phase == 0 ? g.ny * H : g.nxe * H;  // one strip plane (per field and z)
+  const long long n = (long long)fs.nf * g.nz * len;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(t % len);
+    const long long fk = t / len;
+    const int k = (int)(fk % g.nz), f = (int)(fk / g.nz);
+    const T* v = (const T*)fs.f[f];
+    if (phase == 0) {
+      const int j = H + e / H, c = e % H;
+      a[t] = v[fidx(g, H + c, j, k)];
+      b[t] = v[fidx(g, g.nx + c, j, k)];
+    } else {
+      const int r = e / g.nxe, i = e % g.nxe;
+      a[t] = v[fidx(g, i, H + r, k)];
+      b[t] = v[fidx(g, i, g.ny + r, k)];
+    }
+  }
+}
+// a: from the west (south) neighbour, its east (north) strip, into the halo
+// below the owned range; b: from the east (north), into the halo above
+template <typename T>
+__global__ void k_dd_funpack(HaloGeom g, FieldSet fs, int phase, const T* __restrict__ a, const T* __restrict__ b) {
+  constexpr int H = LES_DD_HALO;
+  const int len = phase == 0 ? g.ny * H : g.nxe * H;
+  const long long n = (long long)fs.nf * g.nz * len;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(t % len);
+    const long long fk = t / len;
+    const int k = (int)(fk % g.nz), f = (int)(fk / g.nz);
+    T* v = (T*)fs.f[f];
+    if (phase == 0) {
+      const int j = H + e / H, c = e % H;
+      v[fidx(g, c, j, k)] = a[t];
+      v[fidx(g, g.nx + H + c, j, k)] = b[t];
+    } else {
+      const int r = e / g.nxe, i = e % g.nxe;
+      v[fidx(g, i, r, k)] = a[t];
+      v[fidx(g, i, g.ny + H + r, k)] = b[t];
+    }
   }
 }
 
@@ -261,6 +333,10 @@ size_t layout(les_dd* d, char* base, bool dry) {
   d->face_bytes[2] = d->face_bytes[3] = (size_t)d->nx * d->nz * es;
   for (int f = 0; f < 4; ++f) d->send[f] = take(d->face_bytes[f]);
   for (int f = 0; f < 4; ++f) d->recv[f] = take(d->face_bytes[f]);
+  const int H = LES_DD_HALO;
+  d->fcap = (size_t)LES_DD_MAX_FIELDS * d->nz * H * std::max(d->ny, d->nx + 2 * H) * es;
+  for (int f = 0; f < 4; ++f) d->fsend[f] = take(d->fcap);
+  for (int f = 0; f < 4; ++f) d->frecv[f] = take(d->fcap);
   d->partials = (double*)take((size_t)4 * d->nblk * sizeof(double));
   d->sums = (double*)take(4 * sizeof(double));
   return off + 256;
@@ -272,7 +348,8 @@ int fail(les_dd* d, int rc, const std::string& m) {
 }
 
 template <typename T>
-int solve(les_dd* d, const les_dd_ops* ops, const T* rhs, T* xout, double tol, int maxit, int* iters, double* rel) {
+int solve(les_dd* d, const les_dd_ops* ops, const T* rhs, T* xout, const les::DdLayout& lay, double tol, int maxit,
+          int* iters, double* rel) {
   const DdGeom g = geom(d);
   const int nb = d->nblk;
   cudaStream_t st = d->st;
@@ -304,8 +381,8 @@ int solve(les_dd* d, const les_dd_ops* ops, const T* rhs, T* xout, double tol, i
   };
   const double ntot = (double)d->cfg.nx * d->cfg.ny * d->cfg.nz;
   // b (mean-free) lives in q until the first matvec; x from the caller
-  k_dd_in<T><<<nb, 256, 0, st>>>(g, rhs, q);
-  k_dd_in<T><<<nb, 256, 0, st>>>(g, xout, x);
+  k_dd_in<T><<<nb, 256, 0, st>>>(g, lay, rhs, q);
+  k_dd_in<T><<<nb, 256, 0, st>>>(g, lay, xout, x);
   if (ck("copy in") != LES_OK) return LES_ERR_CUDA;
   double s1[4];
   k_dd_sum<T><<<nb, 256, 0, st>>>(g, q, (const T*)nullptr, d->partials);
@@ -356,7 +433,7 @@ int solve(les_dd* d, const les_dd_ops* ops, const T* rhs, T* xout, double tol, i
   k_dd_sum<T><<<nb, 256, 0, st>>>(g, x, (const T*)nullptr, d->partials);
   if (reduce(1, s1) != LES_OK) return LES_ERR_CUDA;
   k_dd_shift<T><<<nb, 256, 0, st>>>(g, x, s1[0] / ntot);
-  k_dd_out<T><<<nb, 256, 0, st>>>(g, x, xout);
+  k_dd_out<T><<<nb, 256, 0, st>>>(g, lay, x, xout);
   if (ck("copy out") != LES_OK) return LES_ERR_CUDA;
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(d, LES_ERR_CUDA, cudaGetErrorString(e));
   if (iters) *iters = it;
@@ -365,6 +442,71 @@ int solve(les_dd* d, const les_dd_ops* ops, const T* rhs, T* xout, double tol, i
 }
 
 }  // namespace
+
+namespace les {
+
+template <typename T>
+int dd_solve(les_dd* d, const les_dd_ops* ops, const T* rhs, T* x, const DdLayout& lay, double tol, int maxit,
+             int* iters, double* rel, std::string* err) {
+  const int rc = solve<T>(d, ops, rhs, x, lay, tol, maxit, iters, rel);
+  if (rc != LES_OK && rc != LES_ERR_NOT_CONVERGED && err) *err = d->err;
+  return rc;
+}
+template int dd_solve<float>(les_dd*, const les_dd_ops*, const float*, float*, const DdLayout&, double, int, int*,
+                             double*, std::string*);
+template int dd_solve<double>(les_dd*, const les_dd_ops*, const double*, double*, const DdLayout&, double, int,
+                              int*, double*, std::string*);
+
+void dd_widened_shape(const les_dd* d, int* nxe, int* nye, int* nz) {
+  *nxe = d->nx + 2 * LES_DD_HALO;
+  *nye = d->ny + 2 * LES_DD_HALO;
+  *nz = d->nz;
+}
+
+const les_config& dd_config(const les_dd* d) { return d->cfg; }
+
+template <typename T>
+static int halo_exchange_t(les_dd* d, const les_dd_ops* ops, void* const* fields, int nf, cudaStream_t st,
+                           std::string* err) {
+  constexpr int H = LES_DD_HALO;
+  HaloGeom g{d->nx, d->ny, d->nz, d->nx + 2 * H, d->ny + 2 * H};
+  FieldSet fs{};
+  for (int f = 0; f < nf; ++f) fs.f[f] = fields[f];
+  fs.nf = nf;
+  for (int phase = 0; phase < 2; ++phase) {
+    const long long len = phase == 0 ? (long long)g.ny * H : (long long)g.nxe * H;
+    const long long n = (long long)nf * g.nz * len;
+    const size_t b = (size_t)n * sizeof(T);
+    const size_t sizes[4] = {phase == 0 ? b : 0, phase == 0 ? b : 0, phase == 1 ? b : 0, phase == 1 ? b : 0};
+    const int lo = phase == 0 ? 0 : 2, hi = lo + 1;
+    const unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 1024);
+    k_dd_fpack<T><<<nb, 256, 0, st>>>(g, fs, phase, (T*)d->fsend[lo], (T*)d->fsend[hi]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      if (err) *err = std::string("halo pack: ") + cudaGetErrorString(e);
+      return LES_ERR_CUDA;
+    }
+    if (ops->exchange(ops->ctx, d->fsend, d->frecv, sizes, st) != 0) {
+      if (err) *err = "halo exchange callback failed";
+      return LES_ERR_CUDA;
+    }
+    k_dd_funpack<T><<<nb, 256, 0, st>>>(g, fs, phase, (const T*)d->frecv[lo], (const T*)d->frecv[hi]);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+      if (err) *err = std::string("halo unpack: ") + cudaGetErrorString(e);
+      return LES_ERR_CUDA;
+    }
+  }
+  return LES_OK;
+}
+
+int dd_halo_exchange(les_dd* d, const les_dd_ops* ops, void* const* fields, int nf, cudaStream_t st,
+                     std::string* err) {
+  if (nf < 1 || nf > LES_DD_MAX_FIELDS) return LES_ERR_INVALID_ARG;
+  return d->cfg.precision == 64 ? halo_exchange_t<double>(d, ops, fields, nf, st, err)
+                                : halo_exchange_t<float>(d, ops, fields, nf, st, err);
+}
+
+}  // namespace les
 
 extern "C" {
 
@@ -430,9 +572,10 @@ int les_dd_poisson_solve(les_dd* d, const les_dd_ops* ops, const void* d_rhs, vo
     return LES_ERR_INVALID_ARG;
   int it = 0;
   double rel = 0.0;
+  const les::DdLayout lay{0, (long long)d->nx * d->ny, d->nx};  // contiguous local arrays
   const int rc = d->cfg.precision == 64
-                     ? solve<double>(d, ops, (const double*)d_rhs, (double*)d_x, rtol, maxit, &it, &rel)
-                     : solve<float>(d, ops, (const float*)d_rhs, (float*)d_x, rtol, maxit, &it, &rel);
+                     ? solve<double>(d, ops, (const double*)d_rhs, (double*)d_x, lay, rtol, maxit, &it, &rel)
+                     : solve<float>(d, ops, (const float*)d_rhs, (float*)d_x, lay, rtol, maxit, &it, &rel);
   if (iters) *iters = it;
   if (rel_res) *rel_res = rel;
   return rc;

@@ -350,7 +350,7 @@ int unet_predict(les_unet* u, int precision, const void* b, void* psi0, cudaStre
 int unet_grid(const les_unet* u);
 
 // Flexible CG with the learned network as the preconditioner (les_fcg.cu);
-// *fallbacks counts the iterations that took z = r.
+// *fallbacks counts the iterations that took z = -r.
 template <typename T>
 int poisson_solve_fcg(const SolverArgs<T>& a, les_unet* model, const T* b, T* x, double tol, int maxit, int* iters,
                       double* rel, int* fallbacks, std::string* err);
@@ -359,5 +359,20 @@ int poisson_solve_fcg(const SolverArgs<T>& a, les_unet* model, const T* b, T* x,
 template <typename T>
 int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxit, int* iters,
                   double* rel, std::string* err);
+
+// Domain decomposition (les_dd.cu).  A local array as the dd solve reads
+// and writes it: node (i, j, k) of the sub-domain at off + k sxy + j sx + i.
+struct DdLayout {
+  long long off, sxy;
+  int sx;
+};
+template <typename T>
+int dd_solve(les_dd* d, const les_dd_ops* ops, const T* rhs, T* x, const DdLayout& lay, double tol, int maxit,
+             int* iters, double* rel, std::string* err);
+// fill the LES_DD_HALO-deep x-y halos of nf fields of the widened sub-domain
+int dd_halo_exchange(les_dd* d, const les_dd_ops* ops, void* const* fields, int nf, cudaStream_t st,
+                     std::string* err);
+void dd_widened_shape(const les_dd* d, int* nxe, int* nye, int* nz);
+const les_config& dd_config(const les_dd* d);
 
 }  // namespace les

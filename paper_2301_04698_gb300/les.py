@@ -45,7 +45,8 @@ EXPORTED = ("les_config_default", "les_workspace_bytes", "les_init", "les_destro
             "les_unet_forward", "les_unet_loss_grad", "les_unet_train_step", "les_unet_last_error",
             "les_set_warm_model", "les_unet_set_output_scale", "les_unet_get_output_scale", "les_unet_set_loss",
             "les_ensemble_step", "les_set_states", "les_dd_workspace_bytes", "les_dd_create", "les_dd_destroy",
-            "les_dd_local_shape", "les_dd_poisson_solve", "les_dd_last_error")
+            "les_dd_local_shape", "les_dd_poisson_solve", "les_dd_last_error", "les_dd_step_config",
+            "les_dd_halo_exchange", "les_dd_stage_solve")
 
 
 class LesConfig(C.Structure):
@@ -200,6 +201,12 @@ def load_library(path: str = LIB_PATH):
     lib.les_dd_poisson_solve.argtypes = [vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl)]
     lib.les_dd_last_error.restype = C.c_char_p
     lib.les_dd_last_error.argtypes = [vp]
+    lib.les_dd_step_config.restype = C.c_int
+    lib.les_dd_step_config.argtypes = [vp, cfgp]
+    lib.les_dd_halo_exchange.restype = C.c_int
+    lib.les_dd_halo_exchange.argtypes = [vp, vp, vp, i32, C.POINTER(i32)]
+    lib.les_dd_stage_solve.restype = C.c_int
+    lib.les_dd_stage_solve.argtypes = [vp, vp, vp, C.POINTER(LesStepStats)]
     lib.les_set_warm_model.restype = C.c_int
     lib.les_set_warm_model.argtypes = [vp, vp]
     lib.les_poisson_solve_static.restype = C.c_int

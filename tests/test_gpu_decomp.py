@@ -97,3 +97,136 @@ def test_decomposed_solve_rejects_bad_partitions(mods):
         decomp.Subdomain(case, 4, 1, 0)          # 4 does not divide 30
     with pytest.raises(Exception):
         decomp.Subdomain(case.replace(op="wide"), 2, 1, 0)
+
+
+# ---- the decomposed step ------------------------------------------------------
+
+STEPS = 2
+SNAP = {("begin", 0): ("b", "T", "q_l", "s_rad", "u_n", "theta_l_half"),
+        ("momentum", 0): ("theta_l", "q_t", "u_hat", "v_hat", "w_hat")}
+FINAL = ("u", "v", "w", "p", "theta_l", "q_t")
+
+
+def _cbl_state(case):
+    st = inputs.initial_state(case)
+    for s, k in enumerate(("u", "v", "w")):
+        st[k] = st[k] + inputs.uniform(5, 40 + s, case.n, -0.5, 0.5).reshape(case.shape)
+    return st
+
+
+class _Whole:
+    """The undivided domain through the same schedule (no exchanges)."""
+
+    def __init__(self, sim):
+        self.sim = sim
+
+    def exchange(self, names):
+        pass
+
+    def stage(self, name):
+        self.sim.stage(name)
+
+    def solve(self):
+        return self.sim.stage("solve")
+
+
+@pytest.mark.parametrize("precision,px,py", [(64, 2, 2), (64, 2, 1), (64, 1, 2), (32, 2, 2)])
+def test_decomposed_step_matches_single_domain(mods, precision, px, py):
+    """Sub-domains of one GPU, each stepped by its own thread through
+    decomp.decomposed_step with the library's halo exchange (two-node halos,
+    LocalExchange) and decomposed solve, against the single-domain step on
+    the same kernels (the rolling predictors on both): after the step's
+    thermodynamics every node of each widened sub-domain, halos included,
+    and after the first predictors every owned node equal bit for bit; after
+    two steps the fields equal to the solver tolerance."""
+    les, decomp = mods
+    case = inputs.cbl(nx=32, ny=24, nz=24, dx=35.0, dz=40.0, precision=precision,
+                      tol=1e-10 if precision == 64 else 1e-6)
+    state = _cbl_state(case)
+    sim = les.Simulation(case)
+    sim.set_tuning(stencil_path=3)
+    sim.set_state(state)
+    snaps = {}
+
+    def after(stage, k):
+        if (stage, k) in SNAP and (stage, k) not in snaps:
+            snaps[(stage, k)] = {n: sim.get(n) for n in SNAP[(stage, k)]}
+
+    tot = decomp.decomposed_step(_Whole(sim), case.K, STEPS, after)
+    final = {n: sim.get(n) for n in FINAL}
+    sim.close()
+
+    ex = decomp.LocalExchange(px, py)
+    nr = px * py
+    subs = []
+    for r in range(nr):
+        sd = decomp.DecomposedSimulation(case, px, py, r, lambda s, rv, st, r=r: ex.exchange(r, s, rv, st),
+                                         lambda v, r=r: ex.allreduce(r, v))
+        sd.sim.set_tuning(stencil_path=3)
+        sd.set_global_state(state)
+        subs.append(sd)
+    out = [None] * nr
+    errors = []
+
+    def run(r):
+        try:
+            torch.cuda.set_device(0)
+            sd = subs[r]
+            mine = {}
+
+            def grab(stage, k):
+                if (stage, k) in SNAP and (stage, k) not in mine:
+                    mine[(stage, k)] = {n: (sd.sim.get(n) if stage == "begin" else sd.owned(n))
+                                        for n in SNAP[(stage, k)]}
+
+            t = sd.step(STEPS, grab)
+            out[r] = (mine, {n: sd.owned(n) for n in FINAL}, t)
+        except Exception as e:  # surfaced below
+            errors.append(e)
+            ex.barrier.abort()
+
+    threads = [threading.Thread(target=run, args=(r,)) for r in range(nr)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(600)
+    assert not errors, errors[0]
+    rtol = 1e-8 if precision == 64 else 2e-4
+    for r, sd in enumerate(subs):
+        mine, fin, t = out[r]
+        iy, ix = sd.window
+        for n in SNAP[("begin", 0)]:
+            assert np.array_equal(mine[("begin", 0)][n], snaps[("begin", 0)][n][:, iy][:, :, ix]), n
+        ys, xs = slice(sd.sub.y0, sd.sub.y0 + sd.sub.ny), slice(sd.sub.x0, sd.sub.x0 + sd.sub.nx)
+        for n in SNAP[("momentum", 0)]:
+            assert np.array_equal(mine[("momentum", 0)][n], snaps[("momentum", 0)][n][:, ys, xs]), n
+        for n in FINAL:
+            g = final[n][:, ys, xs].astype(np.float64)
+            scale = np.abs(final[n]).max() + 1e-30
+            err = np.abs(fin[n].astype(np.float64) - g).max() / scale
+            assert err <= rtol, (n, err)
+        assert t["not_converged"] == 0
+        print(f"rank {r}: {t['iters_total']} CG iterations over {STEPS} steps (single domain {tot['iters_total']})")
+    assert len({out[r][2]["iters_total"] for r in range(nr)}) == 1
+    for sd in subs:
+        sd.close()
+
+
+def test_decomposed_step_rejects_a_plain_handle(mods):
+    """les_dd_halo_exchange and les_dd_stage_solve refuse a handle that is not
+    the widened sub-domain, and the solve stage keeps the stage order."""
+    les, decomp = mods
+    import ctypes as C
+    case = inputs.cbl(nx=32, ny=24, nz=24, dx=35.0, dz=40.0, precision=64)
+    ex = decomp.LocalExchange(2, 1)
+    sd = decomp.DecomposedSimulation(case, 2, 1, 0, lambda s, rv, st: ex.exchange(0, s, rv, st),
+                                     lambda v: ex.allreduce(0, v))
+    plain = les.Simulation(case)
+    ids = (C.c_int32 * 1)(les.FIELDS["u"])
+    assert sd.lib.les_dd_halo_exchange(sd.sub.h, plain.h, sd._opsp, 1, ids) == les.LES_ERR_INVALID_ARG
+    st = les.LesStepStats()
+    assert sd.lib.les_dd_stage_solve(sd.sub.h, sd.sim.h, sd._opsp, C.byref(st)) == les.LES_ERR_STATE
+    two = (C.c_int32 * 2)(les.FIELDS["u"], les.FIELDS["u"])
+    assert sd.lib.les_dd_halo_exchange(sd.sub.h, sd.sim.h, sd._opsp, 2, two) == les.LES_ERR_INVALID_ARG
+    plain.close()
+    sd.close()
