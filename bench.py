@@ -112,6 +112,10 @@ def parse():
     ap.add_argument("--iters", type=int, default=20, help="--poisson-only: CG iterations (tolerance unreachable)")
     ap.add_argument("--repeat", type=int, default=2, help="--poisson-only: solves")
     ap.add_argument("--fp64", action="store_true", help="--poisson-only: FP64 fields")
+    ap.add_argument("--max-blocks", type=int, default=0,
+                    help="--poisson-only: les_tuning.cg_max_blocks (0: the library's choice, all SMs)")
+    ap.add_argument("--stencil-path", type=int, default=-1,
+                    help="les_tuning.stencil_path of the timed workload (-1: the library's default)")
     return ap.parse_args()
 
 
@@ -345,6 +349,8 @@ def poisson_only(args):
                        precision=prec, init="zero", physics=())
     sim = les.Simulation(case)
     sim.set_tuning(cg_variant=args.variant, cg_resident=args.resident)
+    if args.max_blocks > 0:
+        sim.set_tuning(cg_max_blocks=args.max_blocks)
     dt = torch.float64 if prec == 64 else torch.float32
     b = torch.from_numpy(inputs.uniform(1, 0, case.n, -1, 1).reshape(case.shape)).to("cuda", dt)
     for _ in range(args.repeat):
@@ -355,7 +361,8 @@ def poisson_only(args):
         t1.record()
         t1.synchronize()
         print(json.dumps({"grid": [nx, ny, nz], "precision": prec, "variant": args.variant,
-                          "resident": args.resident, "iters": it, "rel": rel, "ms": t0.elapsed_time(t1)}),
+                          "resident": args.resident, "max_blocks": args.max_blocks, "iters": it, "rel": rel,
+                          "ms": t0.elapsed_time(t1)}),
               flush=True)
     sim.close()
     return 0
@@ -553,6 +560,8 @@ def main():
     aux_e2e = aux or (min(args.steps, 5) if big else args.steps)
     st0 = inputs.initial_state(case)
     sim = les.Simulation(case)
+    if args.stencil_path >= 0:
+        sim.set_tuning(stencil_path=args.stencil_path)
     sim.set_state(st0)
     del st0
     stream = sim.stream

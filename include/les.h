@@ -417,7 +417,7 @@ int les_ensemble_step(les_handle *const *hs, int32_t m, int32_t nsteps, les_step
 
 /* ---- tuning of the persistent CG solve ---------------------------------------
  * The CG solve runs as one persistent cooperative launch when solver_path = 0
- * (compact operator).  For cg_variant 1 and 2 a thread block of
+ * (compact operator).  For cg_variant 2 a thread block of
  * 32 x cg_tile_rows threads owns a tile of (32 * 16 B of cells) x
  * cg_tile_rows x cg_tile_planes nodes; every grid is capped by occupancy and
  * cg_max_blocks.  Each grid-barrier wait ends
@@ -425,14 +425,12 @@ int les_ensemble_step(les_handle *const *hs, int32_t m, int32_t nsteps, les_step
  * device stays usable.  fault_missing_arrivals is a failure-detection test
  * hook: the barrier then waits for that many blocks that never arrive, so
  * every wait runs out; it must be 0 otherwise.  stencil_path selects the
- * stencil kernels (same results to rounding): 0 (default) column marches
- * over 16-byte lanes for the correction, the Poisson right side and the
- * scalar predictor where the grid allows them (nx a multiple of 128 floats /
- * 64 doubles, ny a multiple of 8), the momentum predictor as in 3; 1
- * direct-load kernels with nu_t stored between kernels; 2 both predictors in
- * shared-memory 3-D tiles; 3 rolling z-marches through shared-memory plane
- * rings; 4 as 0 with the momentum predictor as a column march too.  Paths 0,
- * 2, 3 and 4 compute nu_t in place.  With
+ * stencil kernels (same results to rounding; both compute nu_t in place):
+ * 0 (default) column marches where the grid allows them -- the correction
+ * and the Poisson right side over 16-byte lanes (nx a multiple of 128 floats
+ * / 64 doubles), the scalar and momentum predictors over two-node lanes (nx
+ * a multiple of 64), ny a multiple of 8 -- and rolling z-marches elsewhere;
+ * 1 rolling z-marches through shared-memory plane rings everywhere.  With
  * cg_resident = 0 the standard CG solve first tries a decomposition of the
  * grid into one brick per thread block (x extent 32, 64 or 128 dividing nx,
  * y and z extents dividing ny and nz, at most one block per SM, x, r and p
@@ -448,25 +446,22 @@ typedef struct les_tuning {
   int32_t  cg_max_blocks;          /* >= 1                                  */
   double   barrier_timeout_ms;     /* > 0                                   */
   int32_t  fault_missing_arrivals; /* 0 in production                      */
-  int32_t  stencil_path;           /* 0 columns (default), 1 direct, 2 tiled,
-                                      3 rolling, 4 columns incl. momentum  */
+  int32_t  stencil_path;           /* 0 columns (default), 1 rolling      */
   int32_t  cg_variant;             /* persistent CG: 0 (default) the
                                       standard CG iterates -- in shared
                                       memory when the grid fits there (see
                                       cg_resident), else variant 4 for
                                       FP32 grids of whole columns,
                                       else variant 2 on tile-aligned grids,
-                                      else variant 3;
-                                      1 Chronopoulos-Gear (one barrier; its
-                                      vector recurrences drift in FP32 and
-                                      may need more iterations); 2 the
+                                      else variant 3; 1 is not accepted;
+                                      2 the
                                       two-phase streaming CG (two barriers
                                       per iteration); 3 one pass over memory
                                       and one grid reduction per iteration,
                                       any grid; 4 the same in 64 x 16 or
                                       32 x 32 columns with the z neighbours
                                       in registers (nx a multiple of 64 and
-                                      ny of 16, or both of 32; else as 3).  1 and 2 need nx a
+                                      ny of 16, or both of 32; else as 3).  2 needs nx a
                                       multiple of 128 (FP32) / 64 (FP64)
                                       and ny of cg_tile_rows, else the
                                       per-phase launches run               */

@@ -259,13 +259,11 @@ int fields_per_cell(const les_config& c, int id) {
   switch (id) {
     case KI_THERMO: return 6;
     case KI_RADIATION: return 3;
-    case KI_NU: return 4 + (fb ? 1 : 0);
-    case KI_NU_HALF: return 10 + (fb ? 1 : 0);
-    // tiled predictors (nu_t in-tile): scalar reads u, v, w, phi^k (2),
+    // predictors (nu_t in place): scalar reads u, v, w, phi^k (2),
     // phi^{n+1/2} (2) [+ b for f_B, + radiative source], writes 2; momentum
-    // reads u^k (3), u^n (3), p, b and writes 3
+    // reads u^k (3), u^n (3), p [+ b for buoyancy or f_B] and writes 3
     case KI_SCALAR: return 9 + (fb ? 1 : 0) + ((c.physics & LES_PHYS_RAD) ? 1 : 0);
-    case KI_MOMENTUM: return 11;
+    case KI_MOMENTUM: return 10 + ((c.physics & (LES_PHYS_BUOY | LES_PHYS_FB)) ? 1 : 0);
     case KI_RHS: return c.poisson_op == LES_OP_COMPACT ? 5 : 4;
     case KI_CORRECT: return 9;
     case KI_DIAG: return 7;
@@ -339,25 +337,13 @@ int stage_scalar(les_handle* h) {
   T* const* F = (T* const*)h->fixed;
   const int ti = h->cur ? B_THB : B_THA, qi = h->cur ? B_QTB : B_QTA;
   const int to = h->cur ? B_THA : B_THB, qo = h->cur ? B_QTA : B_QTB;
-  if ((h->fused.stencil_path == 0 || h->fused.stencil_path == 4) && pcol_eligible<T>(a.g)) {
+  if (h->fused.stencil_path == 0 && pcol_eligible<T>(a.g)) {
     if ((e = launch_scalar_col<T>(a, h->L.max_blocks / 8, F[B_U], F[B_V], F[B_W], F[B_B], F[ti], F[qi], F[B_THH],
                                   F[B_QTH], F[B_SRAD], F[to], F[qo])) != cudaSuccess)
       return h->cuda_fail(e, "scalar predictor");
-  } else if (h->fused.stencil_path == 0 || h->fused.stencil_path == 3 || h->fused.stencil_path == 4) {
-    if ((e = launch_scalar_roll<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_B], F[ti], F[qi], F[B_THH],
-                                   F[B_QTH], F[B_SRAD], F[to], F[qo])) != cudaSuccess)
-      return h->cuda_fail(e, "scalar predictor");
-  } else if (h->fused.stencil_path == 2) {
-    if ((e = launch_scalar_tiled<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_B], F[ti], F[qi], F[B_THH],
-                                    F[B_QTH], F[B_SRAD], F[to], F[qo])) != cudaSuccess)
-      return h->cuda_fail(e, "scalar predictor");
-  } else {
-    if ((e = launch_nu<T>(a, F[B_U], F[B_V], F[B_W], nullptr, nullptr, nullptr, F[B_B], nullptr, nullptr,
-                          nullptr, F[B_NU])) != cudaSuccess)
-      return h->cuda_fail(e, "nu (scalars)");
-    if ((e = launch_scalar<T>(a, F[B_U], F[B_V], F[B_W], F[B_NU], F[ti], F[qi], F[B_THH], F[B_QTH], F[B_SRAD],
-                              F[to], F[qo])) != cudaSuccess)
-      return h->cuda_fail(e, "scalar predictor");
+  } else if ((e = launch_scalar_roll<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_B], F[ti], F[qi], F[B_THH],
+                                        F[B_QTH], F[B_SRAD], F[to], F[qo])) != cudaSuccess) {
+    return h->cuda_fail(e, "scalar predictor");
   }
   h->cur ^= 1;
   return LES_OK;
@@ -367,13 +353,11 @@ int stage_scalar(les_handle* h) {
 template <typename T>
 cudaError_t launch_stage_rhs(les_handle* h, const StageArgs<T>& a) {
   T* const* F = (T* const*)h->fixed;
-  if ((h->fused.stencil_path == 0 || h->fused.stencil_path == 4) && col_eligible<T>(a.g))
+  if (h->fused.stencil_path == 0 && col_eligible<T>(a.g))
     return launch_rhs_col<T>(a, h->L.max_blocks, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI],
                              F[B_RHS]);
-  if (h->fused.stencil_path == 0 || h->fused.stencil_path == 3 || h->fused.stencil_path == 4)
-    return launch_rhs_roll<T>(a, h->L.max_blocks, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI],
-                              F[B_RHS]);
-  return launch_rhs<T>(a, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI], F[B_RHS]);
+  return launch_rhs_roll<T>(a, h->L.max_blocks, h->cfg.poisson_op, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI],
+                            F[B_RHS]);
 }
 
 template <typename T>
@@ -381,25 +365,13 @@ int stage_momentum(les_handle* h) {
   auto a = stage_args<T>(h);
   cudaError_t e;
   T* const* F = (T* const*)h->fixed;
-  if (h->fused.stencil_path == 4 && pcol_eligible<T>(a.g)) {
+  if (h->fused.stencil_path == 0 && pcol_eligible<T>(a.g)) {
     if ((e = launch_momentum_col<T>(a, h->L.max_blocks / 8, F[B_U], F[B_V], F[B_W], F[B_UN], F[B_VN], F[B_WN],
                                     F[B_P], F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess)
       return h->cuda_fail(e, "momentum predictor");
-  } else if (h->fused.stencil_path == 0 || h->fused.stencil_path == 3 || h->fused.stencil_path == 4) {
-    if ((e = launch_momentum_roll<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_UN], F[B_VN], F[B_WN],
-                                     F[B_P], F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess)
-      return h->cuda_fail(e, "momentum predictor");
-  } else if (h->fused.stencil_path == 2) {
-    if ((e = launch_momentum_tiled<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_UN], F[B_VN], F[B_WN],
-                                      F[B_P], F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess)
-      return h->cuda_fail(e, "momentum predictor");
-  } else {
-    if ((e = launch_nu<T>(a, F[B_U], F[B_V], F[B_W], F[B_UN], F[B_VN], F[B_WN], F[B_B], F[B_UHALF],
-                          F[B_VHALF], F[B_WHALF], F[B_NU])) != cudaSuccess)
-      return h->cuda_fail(e, "nu (momentum)");
-    if ((e = launch_momentum<T>(a, F[B_UHALF], F[B_VHALF], F[B_WHALF], F[B_UN], F[B_VN], F[B_WN], F[B_NU],
-                                F[B_P], F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess)
-      return h->cuda_fail(e, "momentum predictor");
+  } else if ((e = launch_momentum_roll<T>(a, h->L.max_blocks, F[B_U], F[B_V], F[B_W], F[B_UN], F[B_VN], F[B_WN],
+                                          F[B_P], F[B_B], F[B_UHAT], F[B_VHAT], F[B_WHAT])) != cudaSuccess) {
+    return h->cuda_fail(e, "momentum predictor");
   }
   if ((e = launch_stage_rhs<T>(h, a)) != cudaSuccess) return h->cuda_fail(e, "poisson rhs");
   return LES_OK;
@@ -515,7 +487,7 @@ int stage_correct(les_handle* h) {
   auto a = stage_args<T>(h);
   T* const* F = (T* const*)h->fixed;
   cudaError_t e =
-      (h->fused.stencil_path == 0 || h->fused.stencil_path == 4) && col_eligible<T>(a.g)
+      h->fused.stencil_path == 0 && col_eligible<T>(a.g)
           ? launch_correct_col<T>(a, h->L.max_blocks, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI], F[B_U], F[B_V],
                                   F[B_W], F[B_P])
           : launch_correct<T>(a, F[B_UHAT], F[B_VHAT], F[B_WHAT], F[B_PSI], F[B_U], F[B_V], F[B_W], F[B_P]);
@@ -564,7 +536,7 @@ int do_stage(les_handle* h, int stage, les_step_stats* st) {
 namespace les {
 
 const char* const kKernelNames[KI_COUNT] = {
-    "thermo", "radiation", "nu", "nu_half", "scalar", "momentum", "rhs", "correct", "diag",
+    "thermo", "radiation", "scalar", "momentum", "rhs", "correct", "diag",
     "cfl", "apply", "sum", "cg_init", "cg_matvec", "cg_update", "jacobi", "finish", "ctl", "cg_fused",
     "unet_conv", "unet_wgrad", "unet_adam", "cg_resident", "cg_roll", "cg_wave"};
 
@@ -964,11 +936,11 @@ int les_set_tuning(les_handle* h, const les_tuning* in) {
     h->fused.spin_cycles = (long long)(in->barrier_timeout_ms * (double)khz);
   }
   h->fused.missing = in->fault_missing_arrivals;
-  if (in->stencil_path < 0 || in->stencil_path > 4)
-    return h->fail(LES_ERR_INVALID_ARG, "stencil_path must be 0 .. 4");
+  if (in->stencil_path < 0 || in->stencil_path > 1)
+    return h->fail(LES_ERR_INVALID_ARG, "stencil_path must be 0 (columns) or 1 (rolling)");
   h->fused.stencil_path = in->stencil_path;
-  if (in->cg_variant < 0 || in->cg_variant > 4)
-    return h->fail(LES_ERR_INVALID_ARG, "cg_variant must be 0, 1, 2, 3 or 4");
+  if (in->cg_variant < 0 || in->cg_variant > 4 || in->cg_variant == 1)
+    return h->fail(LES_ERR_INVALID_ARG, "cg_variant must be 0, 2, 3 or 4");
   h->fused.variant = in->cg_variant;
   if (in->cg_resident != 0 && in->cg_resident != 1) return h->fail(LES_ERR_INVALID_ARG, "cg_resident must be 0 or 1");
   h->fused.resident = in->cg_resident;

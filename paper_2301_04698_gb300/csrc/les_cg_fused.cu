@@ -71,9 +71,6 @@ struct FusedArgs {
   T* p0;
   T* p1;
   T* q;
-  T* e0;  // Chronopoulos-Gear: second buffers of r, w, s
-  T* e1;
-  T* e2;
   double* partials;  // [4][gridDim.x]
   FusedBar* bar;
   SolverCtl* ctl;
@@ -359,208 +356,6 @@ __global__ void __launch_bounds__(256, 2) k_cg_fused(FusedArgs<T> f) {
   }
 }
 
-// Chronopoulos-Gear CG: the same Krylov iterates with both dot products of
-// an iteration reduced together, so one grid barrier per iteration.  With
-// s = A p and w = A r kept by recurrence,
-//   p = r + beta p,  s = w + beta s,  x += alpha p,  r' = r - alpha s,
-//   w' = A r',  gamma' = r'.r',  delta' = w'.r',
-//   beta' = gamma'/gamma,  alpha' = gamma' / (delta' - beta' gamma' / alpha).
-// r' is formed on the fly wherever the stencil needs it.
-template <typename T>
-__global__ void __launch_bounds__(256, 2) k_cg_cgg(FusedArgs<T> f) {
-  constexpr int VW = VT<T>::VW;
-  extern __shared__ unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw);
-  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  const long long gstride = (long long)gridDim.x * blockDim.x * blockDim.y;
-  const long long gtid = (long long)blockIdx.x * blockDim.x * blockDim.y + tid;
-  GridSync gs{f.bar, f.partials, f.spin_cycles, f.expected, 0u};
-  int status = 0;
-  double s1[1] = {0.0};
-  for (long long v = gtid; v < f.nv; v += gstride) {
-    T bv[VW];
-    ldv(bv, f.b + v * VW);
-#pragma unroll
-    for (int e = 0; e < VW; ++e) s1[0] += (double)bv[e];
-  }
-  if (!grid_sum<1>(s1, gs)) status = 5;
-  const T mean = (T)(s1[0] / (double)f.n);
-  T* rc = f.r;   // r, w, s of the current iteration
-  T* wc = f.q;
-  T* sc = f.p1;
-  T* rn = f.e0;  // and of the next one
-  T* wn = f.e1;
-  T* sn = f.e2;
-  T* p = f.p0;
-  double s2[2] = {0.0, 0.0};
-  if (!status) {
-    auto loadX = [&](T (&o)[VW], size_t m) { ldv(o, f.x + m); };
-    auto loadX1 = [&](size_t m) { return __ldcg(f.x + m); };
-    auto emitR = [&](size_t m, const T (&P)[VW], const T (&qv)[VW]) {
-      T bv[VW], rv[VW];
-      ldv(bv, f.b + m);
-#pragma unroll
-      for (int e = 0; e < VW; ++e) {
-        bv[e] -= mean;
-        rv[e] = bv[e] - qv[e];
-      }
-      stv(rc + m, rv);
-      s2[0] += vdot(rv, rv);
-      s2[1] += vdot(bv, bv);
-    };
-    stencil_sweep(f, sm, loadX, loadX1, emitR);
-    if (!grid_sum<2>(s2, gs)) status = 5;
-  }
-  // the plain solver judges a learned first guess: if it leaves a larger
-  // residual than x0 = 0, restart from zero (r = b - mean b, r.r = |b|^2)
-  if (!status && f.guard && s2[0] > s2[1]) {
-    for (long long v = gtid; v < f.nv; v += gstride) {
-      T bv[VW], zv[VW];
-      ldv(bv, f.b + v * VW);
-#pragma unroll
-      for (int e = 0; e < VW; ++e) {
-        bv[e] -= mean;
-        zv[e] = T(0);
-      }
-      stv(f.x + v * VW, zv);
-      stv(rc + v * VW, bv);
-    }
-    double sz[1] = {0.0};
-    if (!grid_sum<1>(sz, gs)) status = 5;
-    s2[0] = s2[1];
-  }
-  double gamma = s2[0];
-  const double bb = s2[1];
-  double rel = 0.0;
-  if (!status) {
-    if (bb == 0.0) status = 4;
-    else {
-      rel = sqrt(gamma / bb);
-      if (rel <= f.tol) status = 1;
-      else if (f.maxit <= 0) status = 2;
-    }
-  }
-  double delta = 0.0;
-  if (!status) {
-    // w0 = A r0, delta0 = w0.r0
-    double sd[1] = {0.0};
-    auto loadR = [&](T (&o)[VW], size_t m) { ldv(o, rc + m); };
-    auto loadR1 = [&](size_t m) { return __ldcg(rc + m); };
-    auto emitW = [&](size_t m, const T (&P)[VW], const T (&qv)[VW]) {
-      stv(wc + m, qv);
-      sd[0] += vdot(qv, P);
-    };
-    stencil_sweep(f, sm, loadR, loadR1, emitW);
-    if (!grid_sum<1>(sd, gs)) status = 5;
-    delta = sd[0];
-    if (!status && (delta == 0.0 || !isfinite(delta))) status = 3;
-  }
-  double alpha = status ? 0.0 : gamma / delta;
-  double beta = 0.0;
-  bool first = true;
-  int iter = 0;
-  while (!status) {
-    const T ta = (T)alpha, tb = (T)beta;
-    const T* r0 = rc;
-    const T* w0 = wc;
-    const T* s0 = sc;
-    // r' at any node: r - alpha (w + beta s_old)
-    auto loadRn = [&](T (&o)[VW], size_t m) {
-      T rv[VW], wv[VW];
-      ldv(rv, r0 + m);
-      ldv(wv, w0 + m);
-      if (!first) {
-        T sv[VW];
-        ldv(sv, s0 + m);
-#pragma unroll
-        for (int e = 0; e < VW; ++e) wv[e] += tb * sv[e];
-      }
-#pragma unroll
-      for (int e = 0; e < VW; ++e) o[e] = rv[e] - ta * wv[e];
-    };
-    auto loadRn1 = [&](size_t m) {
-      T wv = __ldcg(w0 + m);
-      if (!first) wv += tb * __ldcg(s0 + m);
-      return __ldcg(r0 + m) - ta * wv;
-    };
-    double sg[2] = {0.0, 0.0};
-    auto emitIt = [&](size_t m, const T (&Rn)[VW], const T (&qv)[VW]) {
-      T rv[VW], wv[VW], pv[VW], xv[VW];
-      ldv(rv, r0 + m);
-      ldv(wv, w0 + m);
-      ldv(xv, f.x + m);
-      if (!first) {
-        T sv[VW], po[VW];
-        ldv(sv, s0 + m);
-        ldv(po, p + m);
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-          pv[e] = rv[e] + tb * po[e];
-          wv[e] += tb * sv[e];
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < VW; ++e) pv[e] = rv[e];
-      }
-#pragma unroll
-      for (int e = 0; e < VW; ++e) xv[e] += ta * pv[e];
-      stv(p + m, pv);
-      stv(sn + m, wv);  // s = w + beta s_old
-      stv(f.x + m, xv);
-      stv(rn + m, Rn);
-      stv(wn + m, qv);
-      sg[0] += vdot(Rn, Rn);
-      sg[1] += vdot(qv, Rn);
-    };
-    stencil_sweep(f, sm, loadRn, loadRn1, emitIt);
-    if (!grid_sum<2>(sg, gs)) {
-      status = 5;
-      break;
-    }
-    iter += 1;
-    const double g_new = sg[0], d_new = sg[1];
-    rel = sqrt(g_new / bb);
-    T* t;
-    t = rc; rc = rn; rn = t;
-    t = wc; wc = wn; wn = t;
-    t = sc; sc = sn; sn = t;
-    first = false;
-    if (rel <= f.tol) { status = 1; break; }
-    if (iter >= f.maxit) { status = 2; break; }
-    if (!isfinite(g_new)) { status = 3; break; }
-    beta = g_new / gamma;
-    const double den = d_new - beta * g_new / alpha;
-    if (den == 0.0 || !isfinite(den)) { status = 3; break; }
-    alpha = g_new / den;
-    gamma = g_new;
-  }
-  if (status != 5) {
-    double sx[1] = {0.0};
-    for (long long v = gtid; v < f.nv; v += gstride) {
-      T xv[VW];
-      ldv(xv, f.x + v * VW);
-#pragma unroll
-      for (int e = 0; e < VW; ++e) sx[0] += (double)xv[e];
-    }
-    if (!grid_sum<1>(sx, gs)) {
-      status = 5;
-    } else {
-      const T mx = (T)(sx[0] / (double)f.n);
-      for (long long v = gtid; v < f.nv; v += gstride) {
-        T xv[VW];
-        ldv(xv, f.x + v * VW);
-#pragma unroll
-        for (int e = 0; e < VW; ++e) xv[e] = status == 4 ? T(0) : xv[e] - mx;
-        stv(f.x + v * VW, xv);
-      }
-    }
-  }
-  if (blockIdx.x == 0 && tid == 0) {
-    f.ctl->iter = iter;
-    f.ctl->rel = rel;
-    f.ctl->done = status;
-  }
-}
 
 }  // namespace
 
@@ -596,9 +391,6 @@ int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, 
   f.p0 = a.p0;
   f.p1 = a.p1;
   f.q = a.q;
-  f.e0 = a.e0;
-  f.e1 = a.e1;
-  f.e2 = a.e2;
   f.partials = a.partials;
   f.bar = a.bar;
   f.ctl = a.ctl;
@@ -607,8 +399,7 @@ int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, 
   f.spin_cycles = fc.spin_cycles;
   const dim3 block(32, fc.ty);
   const size_t smem = (size_t)(f.zc + 2) * (fc.ty + 2) * (W + 2) * sizeof(T);
-  const bool cgg = fc.variant == 1 && a.e0 && a.e1 && a.e2;
-  const void* kern = cgg ? (const void*)k_cg_cgg<T> : (const void*)k_cg_fused<T>;
+  const void* kern = (const void*)k_cg_fused<T>;
   int per_sm = 0, dev = 0, nsm = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
@@ -647,10 +438,8 @@ int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, 
   if (rel) *rel = c.rel;
   // algorithmic traffic of the solve (kCgIterFields per iteration; this
   // kernel streams 10: phase A r, p_old in, p, q out; phase B x, p, r, q in,
-  // x, r out; Chronopoulos-Gear adds one prologue sweep, w0 = A r0)
-  if (a.prof)
-    a.prof->bytes[KI_CG_FUSED] +=
-        (kCgSetupFields + (cgg ? 2.0 : 0.0) + kCgIterFields * c.iter) * (double)f.n * sizeof(T);
+  // x, r out)
+  if (a.prof) a.prof->bytes[KI_CG_FUSED] += (kCgSetupFields + kCgIterFields * c.iter) * (double)f.n * sizeof(T);
   switch (c.done) {
     case 1:
     case 4: return LES_OK;

@@ -101,11 +101,10 @@ struct FusedCfg {
   long long spin_cycles = 4000000000LL; // barrier wait limit (~2 s at 2 GHz)
   double timeout_ms = 2000.0;
   int missing = 0;                      // test hook: arrivals that never come
-  int stencil_path = 0;                 // 0 column marches where eligible (momentum as 3), 1 direct-load,
-                                        // 2 tiled, 3 rolling z-march, 4 as 0 with a column momentum march
-  int variant = 0;                      // 0 standard iterates (resident, else two-phase streaming when
-                                        // tile-aligned, else one-pass), 1 Chronopoulos-Gear,
-                                        // 2 two-phase streaming, 3 one-pass one-reduction
+  int stencil_path = 0;                 // 0 column marches where eligible (else rolling), 1 rolling z-march
+  int variant = 0;                      // 0 standard iterates (resident, else FP32 columns, else
+                                        // two-phase streaming when tile-aligned, else one-pass),
+                                        // 2 two-phase streaming, 3 one-pass one-reduction, 4 columns
   int resident = 0;                     // 0 shared-memory-resident CG when the grid fits, 1 never
 };
 
@@ -115,7 +114,7 @@ struct LaunchCfg {
 
 // Kernel classes for launch counting and the optional event profiler.
 enum KernelId : int {
-  KI_THERMO = 0, KI_RADIATION, KI_NU, KI_NU_HALF, KI_SCALAR, KI_MOMENTUM, KI_RHS, KI_CORRECT,
+  KI_THERMO = 0, KI_RADIATION, KI_SCALAR, KI_MOMENTUM, KI_RHS, KI_CORRECT,
   KI_DIAG, KI_CFL, KI_APPLY, KI_SUM, KI_CG_INIT, KI_CG_MATVEC, KI_CG_UPDATE, KI_JACOBI, KI_FINISH,
   KI_CTL, KI_CG_FUSED, KI_UNET_CONV, KI_UNET_WGRAD, KI_UNET_ADAM, KI_CG_RESIDENT, KI_CG_ROLL, KI_CG_WAVE, KI_COUNT
 };
@@ -218,26 +217,6 @@ struct StageArgs {
 template <typename T>
 cudaError_t launch_thermo(const StageArgs<T>& a, const T* th, const T* qt, T* temp, T* ql, T* b,
                           T* srad);
-template <typename T>
-cudaError_t launch_nu(const StageArgs<T>& a, const T* u, const T* v, const T* w, const T* un,
-                      const T* vn, const T* wn, const T* b, T* uh, T* vh, T* wh, T* nu);
-template <typename T>
-cudaError_t launch_scalar(const StageArgs<T>& a, const T* u, const T* v, const T* w, const T* nu,
-                          const T* thk, const T* qtk, const T* thh, const T* qth, const T* srad,
-                          T* th_out, T* qt_out);
-template <typename T>
-cudaError_t launch_momentum(const StageArgs<T>& a, const T* uh, const T* vh, const T* wh,
-                            const T* un, const T* vn, const T* wn, const T* nu, const T* p,
-                            const T* b, T* ou, T* ov, T* ow);
-// shared-memory tiled predictors with nu_t computed in-tile (les_stencil_tiled.cu)
-template <typename T>
-cudaError_t launch_scalar_tiled(const StageArgs<T>& a, int max_blocks, const T* u, const T* v, const T* w,
-                                const T* b, const T* thk, const T* qtk, const T* thh, const T* qth,
-                                const T* srad, T* th_out, T* qt_out);
-template <typename T>
-cudaError_t launch_momentum_tiled(const StageArgs<T>& a, int max_blocks, const T* uk, const T* vk, const T* wk,
-                                  const T* un, const T* vn, const T* wn, const T* p, const T* b, T* ou, T* ov,
-                                  T* ow);
 // rolling-window predictors and Poisson right side (les_stencil_roll.cu)
 template <typename T>
 cudaError_t launch_rhs_roll(const StageArgs<T>& a, int max_blocks, int op, const T* ou, const T* ov, const T* ow,
@@ -250,9 +229,6 @@ template <typename T>
 cudaError_t launch_momentum_roll(const StageArgs<T>& a, int max_blocks, const T* uk, const T* vk, const T* wk,
                                  const T* un, const T* vn, const T* wn, const T* p, const T* b, T* ou, T* ov,
                                  T* ow);
-template <typename T>
-cudaError_t launch_rhs(const StageArgs<T>& a, int op, const T* ou, const T* ov, const T* ow,
-                       const T* psi, T* rhs);
 // column marches over 16-byte lanes (les_stencil_col.cu): nx a multiple of
 // 32 lanes x (16 bytes / element size), ny a multiple of 8
 template <typename T>

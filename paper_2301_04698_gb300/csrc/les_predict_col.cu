@@ -1,16 +1,16 @@
 // les_predict_col.cu -- the scalar predictor (Eq. scalar_prediction_step,
 // Sec. 2.3-2.4: QUICK or WENO3 advection by the u^k mass flux, Smagorinsky-
 // Lilly diffusion with f_B, subsidence, radiation and surface fluxes) as a
-// column march over 16-byte lanes.
+// column march over two-node lanes.
 //
-// Tile: 32 lanes x 8 rows; a lane owns V consecutive x nodes of its row (V =
-// 16 bytes / element size), so a tile is 32 V nodes wide.  A block has ten
+// Tile: 32 lanes x 8 rows; a lane owns V = 2 consecutive x nodes of its row
+// (an 8-byte chunk in FP32, 16 bytes in FP64), so a tile is 64 nodes wide.  A block has ten
 // warps: warps 0-7 own the tile's rows, warps 8 and 9 the rows just below
 // and above it, whose nu_t the y faces need.  The block marches its tile up
 // a run of z-planes.  Every input plane is staged into shared memory as 12
 // rows (the tile's 8 rows and two on each side) of 32 V + 2 V nodes (one
-// 16-byte chunk beyond each end): u^k, v^k, w^k (and b for f_B) by one
-// 16-byte cp.async per lane and row into a four-plane ring, issued a plane
+// lane chunk beyond each end): u^k, v^k, w^k (and b for f_B) by one chunk-
+// sized cp.async per lane and row into a four-plane ring, issued a plane
 // ahead; theta_l and q_t as phibar = (phi^k + phi^{n+1/2}) / 2 in a
 // four-plane ring, averaged from a raw staging plane.  Planes beyond a wall
 // take the mirror rule; the few whose rule flips a sign are staged through
@@ -34,12 +34,18 @@ constexpr int PWARP = PR + 2;     // row warps + two halo-row warps
 constexpr int NROW = PR + 4;      // staged rows: j0-2 .. j0+9
 constexpr int NUROW = PR + 2;     // nu rows: j0-1 .. j0+8
 
+// a lane owns two consecutive x nodes (8 bytes in FP32, 16 in FP64): FP32
+// blocks then fit twice per SM (about 97 KB of shared memory each)
 template <typename T>
-constexpr int kV = 16 / (int)sizeof(T);
+constexpr int kV = 2;
+template <typename T>
+constexpr int kLB = kV<T> * (int)sizeof(T);     // bytes of a lane's chunk
+template <typename T>
+constexpr int kMinBlocks = sizeof(T) == 4 ? 2 : 1;  // resident blocks per SM
 template <typename T>
 constexpr int kTW = PW * kV<T>;                 // tile width
 template <typename T>
-constexpr int kRL = kTW<T> + 2 * kV<T>;         // staged row length (a 16-byte chunk each side)
+constexpr int kRL = kTW<T> + 2 * kV<T>;         // staged row length (a lane chunk each side)
 template <typename T>
 constexpr int kPL = NROW * kRL<T>;              // elements of one staged field-plane
 template <typename T>
@@ -53,8 +59,8 @@ template <typename T>
 __device__ __forceinline__ Vec<T> lds(const T* p) {
   Vec<T> r;
   if constexpr (sizeof(T) == 4) {
-    const float4 q = *reinterpret_cast<const float4*>(p);
-    r.v[0] = q.x, r.v[1] = q.y, r.v[2] = q.z, r.v[3] = q.w;
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    r.v[0] = q.x, r.v[1] = q.y;
   } else {
     const double2 q = *reinterpret_cast<const double2*>(p);
     r.v[0] = q.x, r.v[1] = q.y;
@@ -63,15 +69,15 @@ __device__ __forceinline__ Vec<T> lds(const T* p) {
 }
 template <typename T>
 __device__ __forceinline__ void sts(T* p, const Vec<T>& r) {
-  if constexpr (sizeof(T) == 4) *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  if constexpr (sizeof(T) == 4) *reinterpret_cast<float2*>(p) = make_float2(r.v[0], r.v[1]);
   else *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
 }
 template <typename T>
-__device__ __forceinline__ Vec<T> ldg16(const T* p) {
+__device__ __forceinline__ Vec<T> ldgv(const T* p) {
   Vec<T> r;
   if constexpr (sizeof(T) == 4) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-    r.v[0] = q.x, r.v[1] = q.y, r.v[2] = q.z, r.v[3] = q.w;
+    const float2 q = __ldg(reinterpret_cast<const float2*>(p));
+    r.v[0] = q.x, r.v[1] = q.y;
   } else {
     const double2 q = __ldg(reinterpret_cast<const double2*>(p));
     r.v[0] = q.x, r.v[1] = q.y;
@@ -79,8 +85,8 @@ __device__ __forceinline__ Vec<T> ldg16(const T* p) {
   return r;
 }
 template <typename T>
-__device__ __forceinline__ void stg16(T* p, const Vec<T>& r) {
-  if constexpr (sizeof(T) == 4) __stcs(reinterpret_cast<float4*>(p), make_float4(r.v[0], r.v[1], r.v[2], r.v[3]));
+__device__ __forceinline__ void stgv(T* p, const Vec<T>& r) {
+  if constexpr (sizeof(T) == 4) __stcs(reinterpret_cast<float2*>(p), make_float2(r.v[0], r.v[1]));
   else __stcs(reinterpret_cast<double2*>(p), make_double2(r.v[0], r.v[1]));
 }
 
@@ -123,7 +129,11 @@ __device__ __forceinline__ double c_sin(double a) { return sin(a); }
 template <typename T>
 __device__ __forceinline__ int zsrc(const Grid<T>& g, int kk, int gh, T& sgn) {
   sgn = T(1);
-  if (!g.walls) return ((kk % g.nz) + g.nz) % g.nz;
+  if (!g.walls) {
+    while (kk < 0) kk += g.nz;
+    while (kk >= g.nz) kk -= g.nz;
+    return kk;
+  }
   if (kk < 0) {
     if (gh == G_ODD) sgn = T(-1);
     kk = -1 - kk;
@@ -137,17 +147,18 @@ __device__ __forceinline__ int zsrc(const Grid<T>& g, int kk, int gh, T& sgn) {
 
 // nu_t = (c_s Delta)^2 f_B S (Sec. 2.3) of the lane's V nodes on staged row r
 // of level kk, from the velocity rings (planes kk-1 .. kk+1) and the b ring;
-// x neighbours by shuffles (lext), y and z neighbours by 16-byte loads.
+// x neighbours by shuffles (lext), y and z neighbours by chunk loads.
 template <typename T>
 __device__ __forceinline__ void nu_lane(const T* sm, int ringU, int ringB, int kk, int r, int xl, int lane,
-                                        const Grid<T>& g, const Phys<T>& ph, bool fb, T (&out)[kV<T>]) {
+                                        const Grid<T>& g, const Phys<T>& ph, unsigned flags, bool fb,
+                                        T (&out)[kV<T>]) {
   constexpr int V = kV<T>, RL = kRL<T>, PL = kPL<T>;
-  if (ph.flags & LES_PHYS_CONST_NU) {
+  if (flags & LES_PHYS_CONST_NU) {
 #pragma unroll
     for (int n = 0; n < V; ++n) out[n] = ph.nu_const;
     return;
   }
-  if (!(ph.flags & LES_PHYS_SGS)) {
+  if (!(flags & LES_PHYS_SGS)) {
 #pragma unroll
     for (int n = 0; n < V; ++n) out[n] = T(0);
     return;
@@ -213,21 +224,23 @@ struct ScaSmem {
   static constexpr size_t bytes() { return ((size_t)NPLANES * kPL<T> + 2 * (size_t)kNPL<T>) * sizeof(T); }
 };
 
-template <typename T, int ADV>
-__global__ void __launch_bounds__(PW* PWARP, 1) k_scalar_col(ScaCol<T> a) {
+template <typename T, int ADV, unsigned FIX>
+__global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_scalar_col(ScaCol<T> a) {
   constexpr int VV = kV<T>, TW = kTW<T>, RL = kRL<T>, PL = kPL<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   T* NU = sm + (size_t)ScaSmem<T>::NPLANES * PL;
   const Grid<T>& g = a.g;
   const Phys<T>& ph = a.ph;
+  // the physics switches, fixed at compile time for the common set
+  const unsigned flags = FIX ? FIX : ph.flags;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const size_t plane = (size_t)g.nx * g.ny;
   const long long ncol = (long long)a.ntx * a.nty;
   const long long nblk = ncol * a.nchunk;
-  const bool fb = ph.flags & LES_PHYS_FB;
-  const bool adv_on = ph.flags & LES_PHYS_ADV;
-  const bool sgs = ph.flags & LES_PHYS_SGS, cst = ph.flags & LES_PHYS_CONST_NU;
+  const bool fb = flags & LES_PHYS_FB;
+  const bool adv_on = flags & LES_PHYS_ADV;
+  const bool sgs = flags & LES_PHYS_SGS, cst = flags & LES_PHYS_CONST_NU;
   const T hx = T(0.5) * g.idx, hy = T(0.5) * g.idy, hz = T(0.5) * g.idz;
   constexpr int RINGU = ScaSmem<T>::U, RINGB = ScaSmem<T>::B;
   const T inv_s[2] = {ph.inv_pr, ph.inv_sc};
@@ -269,15 +282,15 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_scalar_col(ScaCol<T> a) {
       for (int q = 0; q < nst; ++q) {
         const int r = q == 0 ? st0 : st1;
         if (sg == T(1)) {
-          cp_async_bytes<16>(at(dstp, r, xl), s0 + src_own[q]);
-          if (edge) cp_async_bytes<16>(at(dstp, r, dst_ext), s0 + src_ext[q]);
+          cp_async_bytes<kLB<T>>(at(dstp, r, xl), s0 + src_own[q]);
+          if (edge) cp_async_bytes<kLB<T>>(at(dstp, r, dst_ext), s0 + src_ext[q]);
         } else {
-          Vec<T> x = ldg16(s0 + src_own[q]);
+          Vec<T> x = ldgv(s0 + src_own[q]);
 #pragma unroll
           for (int c = 0; c < VV; ++c) x.v[c] = -x.v[c];
           sts(at(dstp, r, xl), x);
           if (edge) {
-            Vec<T> y = ldg16(s0 + src_ext[q]);
+            Vec<T> y = ldgv(s0 + src_ext[q]);
 #pragma unroll
             for (int c = 0; c < VV; ++c) y.v[c] = -y.v[c];
             sts(at(dstp, r, dst_ext), y);
@@ -302,8 +315,8 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_scalar_col(ScaCol<T> a) {
         const T* s0 = src[f] + (size_t)gz * plane;
         for (int q = 0; q < nst; ++q) {
           const int r = q == 0 ? st0 : st1;
-          cp_async_bytes<16>(at(dstp, r, xl), s0 + src_own[q]);
-          if (edge) cp_async_bytes<16>(at(dstp, r, dst_ext), s0 + src_ext[q]);
+          cp_async_bytes<kLB<T>>(at(dstp, r, xl), s0 + src_own[q]);
+          if (edge) cp_async_bytes<kLB<T>>(at(dstp, r, dst_ext), s0 + src_ext[q]);
         }
       }
     };
@@ -333,13 +346,13 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_scalar_col(ScaCol<T> a) {
         const T* sh = src[2 * s + 1] + (size_t)gz * plane;
         for (int q = 0; q < nst; ++q) {
           const int r = q == 0 ? st0 : st1;
-          const Vec<T> x = ldg16(sk + src_own[q]), y = ldg16(sh + src_own[q]);
+          const Vec<T> x = ldgv(sk + src_own[q]), y = ldgv(sh + src_own[q]);
           Vec<T> z;
 #pragma unroll
           for (int c = 0; c < VV; ++c) z.v[c] = T(0.5) * (x.v[c] + y.v[c]);
           sts(at(dstp, r, xl), z);
           if (edge) {
-            const Vec<T> xe = ldg16(sk + src_ext[q]), ye = ldg16(sh + src_ext[q]);
+            const Vec<T> xe = ldgv(sk + src_ext[q]), ye = ldgv(sh + src_ext[q]);
 #pragma unroll
             for (int c = 0; c < VV; ++c) z.v[c] = T(0.5) * (xe.v[c] + ye.v[c]);
             sts(at(dstp, r, dst_ext), z);
@@ -385,7 +398,7 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_scalar_col(ScaCol<T> a) {
     auto nu_row = [&](int kk) {
       T* nr = nup(kk) + nurow * RL + VV;
       Vec<T> o;
-      nu_lane<T>(sm, RINGU, RINGB, kk, nurow + 1, xl, lane, g, ph, fb, o.v);
+      nu_lane<T>(sm, RINGU, RINGB, kk, nurow + 1, xl, lane, g, ph, flags, fb, o.v);
       sts(nr + xl, o);
       if (edge) {
         const int xo = lane == 0 ? -1 : TW;
@@ -408,7 +421,7 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_scalar_col(ScaCol<T> a) {
     // nu_t of level k0 on every row; of level k0-1 on the row warps' nodes
     nu_row(k0);
     T nu_lo[VV];
-    if (wid < PR) nu_lane<T>(sm, RINGU, RINGB, k0 - 1, srow, xl, lane, g, ph, fb, nu_lo);
+    if (wid < PR) nu_lane<T>(sm, RINGU, RINGB, k0 - 1, srow, xl, lane, g, ph, flags, fb, nu_lo);
     __syncthreads();
     // the ring slot of level k0-2 is free: stage level k0+2
     stage_vel(k0 + 2);
@@ -418,7 +431,7 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_scalar_col(ScaCol<T> a) {
     auto zface = [&](int kl, const T* nul, const T* nuu, T (&out)[2][VV]) {
       const bool wall = g.walls && (kl == -1 || kl == g.nz - 1);
       if (wall) {
-        const bool sfc = g.walls && kl == -1 && (ph.flags & LES_PHYS_SFC);
+        const bool sfc = g.walls && kl == -1 && (flags & LES_PHYS_SFC);
 #pragma unroll
         for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -538,7 +551,7 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_scalar_col(ScaCol<T> a) {
             flz[q][c] = flu[q][c];
           }
       }
-      if (ph.flags & LES_PHYS_SUBS) {
+      if (flags & LES_PHYS_SUBS) {
         const T wsub = ph.subs_div * (T(k) + T(0.5)) * g.dz;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -548,20 +561,21 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_scalar_col(ScaCol<T> a) {
           for (int c = 0; c < VV; ++c) tend[q][c] += r0 * wsub * (p1.v[c] - p0.v[c]) * g.idz;
         }
       }
-      if (ph.flags & LES_PHYS_RAD) {
-        const Vec<T> sr = ldg16(a.srad + m);
+      if (flags & LES_PHYS_RAD) {
+        const Vec<T> sr = ldgv(a.srad + m);
 #pragma unroll
         for (int c = 0; c < VV; ++c) tend[0][c] += sr.v[c];
       }
-      const Vec<T> hth = ldg16(a.thh + m), hqt = ldg16(a.qth + m);
+      const Vec<T> hth = ldgv(a.thh + m), hqt = ldgv(a.qth + m);
       Vec<T> oth, oqt;
 #pragma unroll
+      const T dtr = ph.dt / r0;  // (rho0 phi^{n+1/2} + dt tend) / rho0
       for (int c = 0; c < VV; ++c) {
-        oth.v[c] = (r0 * hth.v[c] + ph.dt * tend[0][c]) / r0;
-        oqt.v[c] = (r0 * hqt.v[c] + ph.dt * tend[1][c]) / r0;
+        oth.v[c] = hth.v[c] + dtr * tend[0][c];
+        oqt.v[c] = hqt.v[c] + dtr * tend[1][c];
       }
-      stg16(a.tho + m, oth);
-      stg16(a.qto + m, oqt);
+      stgv(a.tho + m, oth);
+      stgv(a.qto + m, oqt);
     }
     cp_wait<0>();  // copies of the run's last (unused) planes land before the next run reuses the rings
   }
@@ -591,21 +605,23 @@ struct MomSmem {
   static constexpr size_t bytes() { return ((size_t)NPLANES * kPL<T> + 2 * (size_t)kNPL<T>) * sizeof(T); }
 };
 
-template <typename T, int ADV>
-__global__ void __launch_bounds__(PW* PWARP, 1) k_momentum_col(MomCol<T> a) {
+template <typename T, int ADV, unsigned FIX>
+__global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_momentum_col(MomCol<T> a) {
   constexpr int VV = kV<T>, TW = kTW<T>, RL = kRL<T>, PL = kPL<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   T* NU = sm + (size_t)MomSmem<T>::NPLANES * PL;
   const Grid<T>& g = a.g;
   const Phys<T>& ph = a.ph;
+  // the physics switches, fixed at compile time for the common set
+  const unsigned flags = FIX ? FIX : ph.flags;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const size_t plane = (size_t)g.nx * g.ny;
   const long long ncol = (long long)a.ntx * a.nty;
   const long long nblk = ncol * a.nchunk;
-  const bool fb = ph.flags & LES_PHYS_FB;
-  const bool adv_on = ph.flags & LES_PHYS_ADV;
-  const bool sgs = ph.flags & LES_PHYS_SGS, cst = ph.flags & LES_PHYS_CONST_NU;
+  const bool fb = flags & LES_PHYS_FB;
+  const bool adv_on = flags & LES_PHYS_ADV;
+  const bool sgs = flags & LES_PHYS_SGS, cst = flags & LES_PHYS_CONST_NU;
   const T hx = T(0.5) * g.idx, hy = T(0.5) * g.idy, hz = T(0.5) * g.idz;
   constexpr int RINGU = MomSmem<T>::U, RINGB = MomSmem<T>::B;
   const T ih[3] = {g.idx, g.idy, g.idz};
@@ -644,21 +660,21 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_momentum_col(MomCol<T> a) {
         const T* s0 = src[f] + (size_t)gz * plane;
         for (int q = 0; q < nst; ++q) {
           const int r = q == 0 ? st0 : st1;
-          cp_async_bytes<16>(at(dstp, r, xl), s0 + src_own[q]);
-          if (edge) cp_async_bytes<16>(at(dstp, r, dst_ext), s0 + src_ext[q]);
+          cp_async_bytes<kLB<T>>(at(dstp, r, xl), s0 + src_own[q]);
+          if (edge) cp_async_bytes<kLB<T>>(at(dstp, r, dst_ext), s0 + src_ext[q]);
         }
       }
     };
     auto stage_b = [&](int kk) {
-      if (!(fb || (ph.flags & LES_PHYS_BUOY))) return;
+      if (!(fb || (flags & LES_PHYS_BUOY))) return;
       T sg;
       const int gz = zsrc(g, kk, G_EVEN, sg);
       T* dstp = fp(MomSmem<T>::B, kk);
       const T* s0 = a.b + (size_t)gz * plane;
       for (int q = 0; q < nst; ++q) {
         const int r = q == 0 ? st0 : st1;
-        cp_async_bytes<16>(at(dstp, r, xl), s0 + src_own[q]);
-        if (edge) cp_async_bytes<16>(at(dstp, r, dst_ext), s0 + src_ext[q]);
+        cp_async_bytes<kLB<T>>(at(dstp, r, xl), s0 + src_own[q]);
+        if (edge) cp_async_bytes<kLB<T>>(at(dstp, r, dst_ext), s0 + src_ext[q]);
       }
     };
     // u^{n+1/2} (with the ghost rule's sign) and alpha0 p' of level kk from
@@ -705,19 +721,19 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_momentum_col(MomCol<T> a) {
           const T* uns[3] = {a.un, a.vn, a.wn};
 #pragma unroll
           for (int f = 0; f < 3; ++f) {
-            const Vec<T> x = ldg16(uks[f] + so), y = ldg16(uns[f] + so);
+            const Vec<T> x = ldgv(uks[f] + so), y = ldgv(uns[f] + so);
             const T sg = f == 2 ? sw : su;
             Vec<T> z;
 #pragma unroll
             for (int c = 0; c < VV; ++c) z.v[c] = sg * (T(0.5) * (x.v[c] + y.v[c]));
             sts(at(fp(f == 0 ? MomSmem<T>::U : (f == 1 ? MomSmem<T>::V : MomSmem<T>::W), kk), r, dx), z);
           }
-          const Vec<T> pp = ldg16(a.p + so);
+          const Vec<T> pp = ldgv(a.p + so);
           Vec<T> z;
 #pragma unroll
           for (int c = 0; c < VV; ++c) z.v[c] = a0 * pp.v[c];
           sts(at(fp(MomSmem<T>::AP, kk), r, dx), z);
-          if (fb || (ph.flags & LES_PHYS_BUOY)) sts(at(fp(MomSmem<T>::B, kk), r, dx), ldg16(a.b + so));
+          if (fb || (flags & LES_PHYS_BUOY)) sts(at(fp(MomSmem<T>::B, kk), r, dx), ldgv(a.b + so));
         }
       }
     };
@@ -755,7 +771,7 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_momentum_col(MomCol<T> a) {
     auto nu_row = [&](int kk) {
       T* nr = nup(kk) + nurow * RL + VV;
       Vec<T> o;
-      nu_lane<T>(sm, RINGU, RINGB, kk, nurow + 1, xl, lane, g, ph, fb, o.v);
+      nu_lane<T>(sm, RINGU, RINGB, kk, nurow + 1, xl, lane, g, ph, flags, fb, o.v);
       sts(nr + xl, o);
       if (edge) {
         const int xo = lane == 0 ? -1 : TW;
@@ -825,7 +841,7 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_momentum_col(MomCol<T> a) {
     __syncthreads();
     nu_row(k0);
     T nu_lo[VV];
-    if (wid < PR) nu_lane<T>(sm, RINGU, RINGB, k0 - 1, srow, xl, lane, g, ph, fb, nu_lo);
+    if (wid < PR) nu_lane<T>(sm, RINGU, RINGB, k0 - 1, srow, xl, lane, g, ph, flags, fb, nu_lo);
     __syncthreads();
     if (wid < PR) {
       const Vec<T> nu0 = lds(nup(k0) + (wid + 1) * RL + VV + xl);
@@ -959,12 +975,12 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_momentum_col(MomCol<T> a) {
       }
       // ---- sources, pressure gradient, update
       const Vec<T> uo = lds(at(Uk, srow, xl)), vo = lds(at(Vk, srow, xl)), wo = lds(at(Wk, srow, xl));
-      if (ph.flags & LES_PHYS_BUOY) {
+      if (flags & LES_PHYS_BUOY) {
         const Vec<T> bo = lds(at(fp(MomSmem<T>::B, k), srow, xl));
 #pragma unroll
         for (int c = 0; c < VV; ++c) R[2][c] += r0 * bo.v[c];
       }
-      if (ph.flags & LES_PHYS_CORIOLIS) {
+      if (flags & LES_PHYS_CORIOLIS) {
 #pragma unroll
         for (int c = 0; c < VV; ++c) {
           R[0][c] += ph.f_cor * r0 * (vo.v[c] - ph.vg);
@@ -972,7 +988,7 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_momentum_col(MomCol<T> a) {
         }
       }
       const T zc = (T(k) + T(0.5)) * g.dz;
-      if ((ph.flags & LES_PHYS_SPONGE) && zc > ph.sponge_zs) {
+      if ((flags & LES_PHYS_SPONGE) && zc > ph.sponge_zs) {
         const T sn = c_sin(T(1.5707963267948966) * (zc - ph.sponge_zs) / (ph.sponge_h - ph.sponge_zs));
         const T beta = ph.sponge_rate * sn * sn * r0;
 #pragma unroll
@@ -999,13 +1015,14 @@ __global__ void __launch_bounds__(PW* PWARP, 1) k_momentum_col(MomCol<T> a) {
       }
       const T* uns[3] = {a.un, a.vn, a.wn};
       T* outs[3] = {a.ou, a.ov, a.ow};
+      const T ir0 = T(1) / r0;  // (rho0 u^n + dt (-rho0 G + R)) / rho0
 #pragma unroll
       for (int c3 = 0; c3 < 3; ++c3) {
-        const Vec<T> un = ldg16(uns[c3] + m);
+        const Vec<T> un = ldgv(uns[c3] + m);
         Vec<T> res;
 #pragma unroll
-        for (int c = 0; c < VV; ++c) res.v[c] = (r0 * un.v[c] + ph.dt * (-r0 * gp[c3][c] + R[c3][c])) / r0;
-        stg16(outs[c3] + m, res);
+        for (int c = 0; c < VV; ++c) res.v[c] = un.v[c] + ph.dt * (R[c3][c] * ir0 - gp[c3][c]);
+        stgv(outs[c3] + m, res);
       }
     }
     cp_wait<0>();
@@ -1027,10 +1044,10 @@ cudaError_t launch_scalar_col(const StageArgs<T>& a, int nsm, const T* u, const 
   r.ph = a.ph;
   r.ntx = a.g.nx / kTW<T>;
   r.nty = a.g.ny / PR;
-  // one block per SM: runs long enough to amortise the four-plane prologue,
-  // at least two blocks per SM
+  // z runs long enough to amortise the four-plane prologue, at least two
+  // waves of resident blocks
   const long long ncol = (long long)r.ntx * r.nty;
-  const long long want = 2LL * nsm;
+  const long long want = 2LL * kMinBlocks<T> * nsm;
   const long long nw = std::max<long long>(1, std::min<long long>((long long)a.g.nz, (want + ncol - 1) / ncol));
   r.zrun = (int)((a.g.nz + nw - 1) / nw);
   r.nchunk = (a.g.nz + r.zrun - 1) / r.zrun;
@@ -1038,7 +1055,10 @@ cudaError_t launch_scalar_col(const StageArgs<T>& a, int nsm, const T* u, const 
   r.thk = thk, r.qtk = qtk, r.thh = thh, r.qth = qth, r.srad = srad;
   r.tho = th_out, r.qto = qt_out;
   const size_t smem = ScaSmem<T>::bytes();
-  auto kern = a.ph.advection == LES_ADV_WENO3 ? k_scalar_col<T, LES_ADV_WENO3> : k_scalar_col<T, LES_ADV_QUICK>;
+  constexpr unsigned kDry = LES_PHYS_ADV | LES_PHYS_SGS;  // the dry Taylor-Green set
+  auto kern = a.ph.advection == LES_ADV_WENO3 ? k_scalar_col<T, LES_ADV_WENO3, 0u>
+              : a.ph.flags == kDry             ? k_scalar_col<T, LES_ADV_QUICK, kDry>
+                                               : k_scalar_col<T, LES_ADV_QUICK, 0u>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long nblk = ncol * r.nchunk;
@@ -1067,14 +1087,17 @@ cudaError_t launch_momentum_col(const StageArgs<T>& a, int nsm, const T* uk, con
   r.ntx = a.g.nx / kTW<T>;
   r.nty = a.g.ny / PR;
   const long long ncol = (long long)r.ntx * r.nty;
-  const long long want = 2LL * nsm;
+  const long long want = 2LL * kMinBlocks<T> * nsm;
   const long long nw = std::max<long long>(1, std::min<long long>((long long)a.g.nz, (want + ncol - 1) / ncol));
   r.zrun = (int)((a.g.nz + nw - 1) / nw);
   r.nchunk = (a.g.nz + r.zrun - 1) / r.zrun;
   r.uk = uk, r.vk = vk, r.wk = wk, r.un = un, r.vn = vn, r.wn = wn, r.p = p, r.b = b;
   r.ou = ou, r.ov = ov, r.ow = ow;
   const size_t smem = MomSmem<T>::bytes();
-  auto kern = a.ph.advection == LES_ADV_WENO3 ? k_momentum_col<T, LES_ADV_WENO3> : k_momentum_col<T, LES_ADV_QUICK>;
+  constexpr unsigned kDry = LES_PHYS_ADV | LES_PHYS_SGS;
+  auto kern = a.ph.advection == LES_ADV_WENO3 ? k_momentum_col<T, LES_ADV_WENO3, 0u>
+              : a.ph.flags == kDry             ? k_momentum_col<T, LES_ADV_QUICK, kDry>
+                                               : k_momentum_col<T, LES_ADV_QUICK, 0u>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long nblk = ncol * r.nchunk;

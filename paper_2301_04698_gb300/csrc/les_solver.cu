@@ -349,7 +349,7 @@ int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxi
   // one-pass kernel with 64 x 16 columns (variant 4, and variant 0 for FP32
   // grids of whole columns), the two-phase streaming kernel on tile-aligned
   // grids (variant 0 or 2) or the one-pass kernel (variant 0 on other grids,
-  // or variant 3); variant 1 is Chronopoulos-Gear.  Persistent solves of
+  // or variant 3).  Persistent solves of
   // different handles (ensemble members stepped from several host threads)
   // share the SMs through the budget above: capped ones run together, an
   // uncapped one alone.
@@ -374,7 +374,7 @@ int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxi
     return poisson_solve_wave<T>(a, *a.fused, b, x, tol, maxit, iters, rel, err);
   if (a.bar && cg_c && (var == 3 || var == 4 || (var == 0 && !tiled)))
     return poisson_solve_roll<T>(a, *a.fused, b, x, tol, maxit, iters, rel, err);
-  if (a.bar && tiled && var >= 0 && var <= 2)
+  if (a.bar && tiled && (var == 0 || var == 2))
     return poisson_solve_fused<T>(a, *a.fused, b, x, tol, maxit, iters, rel, err);
   auto fail = [&](cudaError_t e, const char* where) {
     if (err) *err = std::string(where) + ": " + cudaGetErrorString(e);

@@ -154,275 +154,6 @@ __global__ void __launch_bounds__(32 * RZ) k_radiation(Grid<T> g, Phys<T> ph, co
   }
 }
 
-// ---- Sec. 2.3: Smagorinsky-Lilly viscosity at a node ----------------------------
-// nu_t = (c_s Delta)^2 f_B S, S = sqrt(2 S_ij S_ij) from nodal central
-// differences, f_B = sqrt(clip(1 - N^2 / (Pr S^2), 0, 1)), N^2 = db/dz.
-template <typename T, bool HALF>
-struct VelView {
-  const T* u[3];
-  const T* un[3];
-  __device__ __forceinline__ T operator()(const Grid<T>& g, int c, int i, int j, int k) const {
-    T a = g.at(u[c], i, j, k, vghost(c));
-    if (HALF) a = T(0.5) * (a + g.at(un[c], i, j, k, vghost(c)));
-    return a;
-  }
-};
-
-template <typename T, bool HALF>
-__device__ __forceinline__ T nu_node(const Grid<T>& g, const Phys<T>& ph, const VelView<T, HALF>& V,
-                                     const T* __restrict__ b, int i, int j, int k) {
-  if (ph.flags & LES_PHYS_CONST_NU) return ph.nu_const;
-  if (!(ph.flags & LES_PHYS_SGS)) return T(0);
-  T gr[3][3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int di = d == 0, dj = d == 1, dk = d == 2;
-      gr[c][d] = (V(g, c, i + di, j + dj, k + dk) - V(g, c, i - di, j - dj, k - dk)) * (T(0.5) * g.ih(d));
-    }
-  T S2 = T(0);
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const T s = T(0.5) * (gr[c][d] + gr[d][c]);
-      S2 += T(2) * s * s;
-    }
-  T fB = T(1);
-  if ((ph.flags & LES_PHYS_FB) && S2 > T(0)) {
-    const T N2 = (g.at(b, i, j, k + 1, G_EVEN) - g.at(b, i, j, k - 1, G_EVEN)) * (T(0.5) * g.idz);
-    T x = T(1) - N2 / (T(1) / ph.inv_pr * S2);
-    x = x < T(0) ? T(0) : (x > T(1) ? T(1) : x);
-    fB = m_sqrt(x);
-  }
-  return ph.cs2d2 * fB * m_sqrt(S2);
-}
-
-template <typename T, bool HALF>
-__global__ void __launch_bounds__(NTHREADS) k_nu(Grid<T> g, Phys<T> ph, VelView<T, HALF> V,
-                                                 const T* __restrict__ b, T* __restrict__ uh,
-                                                 T* __restrict__ vh, T* __restrict__ wh,
-                                                 T* __restrict__ nu) {
-  for (long long t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-    int i, j, k0, k1;
-    tile_origin(g, t, i, j, k0, k1);
-    if (i >= g.nx || j >= g.ny) continue;
-    for (int k = k0; k < k1; ++k) {
-      const size_t m = g.lin(i, j, k);
-      if (HALF) {
-        uh[m] = V(g, 0, i, j, k);
-        vh[m] = V(g, 1, i, j, k);
-        wh[m] = V(g, 2, i, j, k);
-      }
-      nu[m] = nu_node<T, HALF>(g, ph, V, b, i, j, k);
-    }
-  }
-}
-
-// QUICK face value between node n and n + e_d (Sec. 2.4): for F >= 0
-// (-f[n-1] + 6 f[n] + 3 f[n+1]) / 8, otherwise (3 f[n] + 6 f[n+1] - f[n+2]) / 8
-
-// ---- a3: scalar predictor (Eq. scalar_prediction_step) -----------------------
-// rho0 phi^{k+1} = rho0 phi^{n+1/2} + dt [ -div(rho0 u^k phibar)
-//   + div(rho0 nu_t / Pr grad phibar) + S ],  phibar = (phi^k + phi^{n+1/2}) / 2
-template <typename T>
-__global__ void __launch_bounds__(NTHREADS)
-    k_scalar(Grid<T> g, Phys<T> ph, const T* __restrict__ u, const T* __restrict__ v,
-             const T* __restrict__ w, const T* __restrict__ nu, const T* __restrict__ thk,
-             const T* __restrict__ qtk, const T* __restrict__ thh, const T* __restrict__ qth,
-             const T* __restrict__ srad, T* __restrict__ tho, T* __restrict__ qto) {
-  const T* vel[3] = {u, v, w};
-  const T* phk[2] = {thk, qtk};
-  const T* phh[2] = {thh, qth};
-  const T inv_s[2] = {ph.inv_pr, ph.inv_sc};
-  const T sflux[2] = {ph.sflux_th, ph.sflux_qt};
-  for (long long t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-    int i, j, k0, k1;
-    tile_origin(g, t, i, j, k0, k1);
-    if (i >= g.nx || j >= g.ny) continue;
-    for (int k = k0; k < k1; ++k) {
-      auto bar = [&](int q, int ii, int jj, int kk) -> T {
-        return T(0.5) * (g.at(phk[q], ii, jj, kk, G_EVEN) + g.at(phh[q], ii, jj, kk, G_EVEN));
-      };
-      T tend[2] = {T(0), T(0)};
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const int di = d == 0, dj = d == 1, dk = d == 2;
-        const T ihd = g.ih(d);
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-          const int li = i - (side ? 0 : di), lj = j - (side ? 0 : dj), lk = k - (side ? 0 : dk);
-          const int ui = li + di, uj = lj + dj, uk = lk + dk;
-          T fl[2];
-          if (g.wall_face(d, lk)) {
-            const bool sfc = g.surface_face(d, lk) && (ph.flags & LES_PHYS_SFC);
-            fl[0] = sfc ? -sflux[0] : T(0);
-            fl[1] = sfc ? -sflux[1] : T(0);
-          } else {
-            T F = T(0);
-            if (ph.flags & LES_PHYS_ADV) {
-              F = T(0.5) * (g.prof(ph.rho0, lk) * g.at(vel[d], li, lj, lk, vghost(d)) +
-                            g.prof(ph.rho0, uk) * g.at(vel[d], ui, uj, uk, vghost(d)));
-            }
-            const T nuf = T(0.5) * (g.at(nu, li, lj, lk, G_EVEN) + g.at(nu, ui, uj, uk, G_EVEN));
-            const T rhof = T(0.5) * (g.prof(ph.rho0, lk) + g.prof(ph.rho0, uk));
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              const T b0 = bar(q, li, lj, lk), b1 = bar(q, ui, uj, uk);
-              T adv = T(0);
-              if (ph.flags & LES_PHYS_ADV) {
-                const T bm = bar(q, li - di, lj - dj, lk - dk);
-                const T b2 = bar(q, ui + di, uj + dj, uk + dk);
-                adv = F * face_value(ph.advection, F, bm, b0, b1, b2);
-              }
-              fl[q] = -adv + rhof * nuf * inv_s[q] * (b1 - b0) * ihd;
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < 2; ++q) tend[q] += (side ? fl[q] : -fl[q]) * ihd;
-        }
-      }
-      const size_t m = g.lin(i, j, k);
-      const T r0 = ph.rho0[k];
-      if (ph.flags & LES_PHYS_SUBS) {
-        // sinking at D z: d phi / dz taken upwind, from the level above
-        const T wsub = ph.subs_div * (T(k) + T(0.5)) * g.dz;
-#pragma unroll
-        for (int q = 0; q < 2; ++q) tend[q] += r0 * wsub * (bar(q, i, j, k + 1) - bar(q, i, j, k)) * g.idz;
-      }
-      if (ph.flags & LES_PHYS_RAD) tend[0] += srad[m];
-      tho[m] = (r0 * thh[m] + ph.dt * tend[0]) / r0;
-      qto[m] = (r0 * qth[m] + ph.dt * tend[1]) / r0;
-    }
-  }
-}
-
-// ---- a4: momentum predictor (Eq. momentum_prediction_step) ---------------------
-// rho0 u^ = rho0 u^n + dt [ -rho0 G(alpha0 p^k) + R ],  R at u^{n+1/2}:
-// -div(rho0 u (x) u) (QUICK) + div(rho0 nu_t (grad u + grad u^T)) + rho0 b k
-// - f k x rho0 (u - u_g) - sponge.
-template <typename T>
-__global__ void __launch_bounds__(NTHREADS)
-    k_momentum(Grid<T> g, Phys<T> ph, const T* __restrict__ uh, const T* __restrict__ vh,
-               const T* __restrict__ wh, const T* __restrict__ un, const T* __restrict__ vn,
-               const T* __restrict__ wn, const T* __restrict__ nu, const T* __restrict__ p,
-               const T* __restrict__ b, T* __restrict__ ou, T* __restrict__ ov, T* __restrict__ ow) {
-  const T* vel[3] = {uh, vh, wh};
-  const T* veln[3] = {un, vn, wn};
-  T* out[3] = {ou, ov, ow};
-  const T target[3] = {ph.ug, ph.vg, T(0)};
-  for (long long t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-    int i, j, k0, k1;
-    tile_origin(g, t, i, j, k0, k1);
-    if (i >= g.nx || j >= g.ny) continue;
-    for (int k = k0; k < k1; ++k) {
-      const size_t m = g.lin(i, j, k);
-      const T r0 = ph.rho0[k];
-      const T zc = (T(k) + T(0.5)) * g.dz;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int ci = c == 0, cj = c == 1, ck = c == 2;
-        T R = T(0);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const int di = d == 0, dj = d == 1, dk = d == 2;
-          const T ihd = g.ih(d);
-#pragma unroll
-          for (int side = 0; side < 2; ++side) {
-            const int li = i - (side ? 0 : di), lj = j - (side ? 0 : dj), lk = k - (side ? 0 : dk);
-            const int ui = li + di, uj = lj + dj, uk = lk + dk;
-            if (g.surface_face(d, lk)) continue;  // free slip, no momentum flux
-            T adv = T(0);
-            if ((ph.flags & LES_PHYS_ADV) && !g.wall_face(d, lk)) {
-              const T F = T(0.5) * (g.prof(ph.rho0, lk) * g.at(vel[d], li, lj, lk, vghost(d)) +
-                                    g.prof(ph.rho0, uk) * g.at(vel[d], ui, uj, uk, vghost(d)));
-              adv = F * face_value(ph.advection, F, g.at(vel[c], li - di, lj - dj, lk - dk, vghost(c)),
-                              g.at(vel[c], li, lj, lk, vghost(c)), g.at(vel[c], ui, uj, uk, vghost(c)),
-                              g.at(vel[c], ui + di, uj + dj, uk + dk, vghost(c)));
-            }
-            // SGS stress on the face: compact normal derivative, tangential
-            // derivative = mean of the two nodal central differences
-            const T dn = (g.at(vel[c], ui, uj, uk, vghost(c)) - g.at(vel[c], li, lj, lk, vghost(c))) * ihd;
-            T dtg;
-            if (c == d) {
-              dtg = dn;
-            } else {
-              const T g0 = g.at(vel[d], li + ci, lj + cj, lk + ck, vghost(d)) -
-                           g.at(vel[d], li - ci, lj - cj, lk - ck, vghost(d));
-              const T g1 = g.at(vel[d], ui + ci, uj + cj, uk + ck, vghost(d)) -
-                           g.at(vel[d], ui - ci, uj - cj, uk - ck, vghost(d));
-              dtg = T(0.25) * (g0 + g1) * g.ih(c);
-            }
-            const T nuf = T(0.5) * (g.at(nu, li, lj, lk, G_EVEN) + g.at(nu, ui, uj, uk, G_EVEN));
-            const T rhof = T(0.5) * (g.prof(ph.rho0, lk) + g.prof(ph.rho0, uk));
-            const T fl = -adv + rhof * nuf * (dn + dtg);
-            R += (side ? fl : -fl) * ihd;
-          }
-        }
-        const T uc = g.at(vel[c], i, j, k, vghost(c));
-        if ((ph.flags & LES_PHYS_BUOY) && c == 2) R += r0 * b[m];
-        if (ph.flags & LES_PHYS_CORIOLIS) {
-          if (c == 0) R += ph.f_cor * r0 * (vh[m] - ph.vg);
-          if (c == 1) R -= ph.f_cor * r0 * (uh[m] - ph.ug);
-        }
-        if ((ph.flags & LES_PHYS_SPONGE) && zc > ph.sponge_zs) {
-          const T x = m_sin(T(1.5707963267948966) * (zc - ph.sponge_zs) / (ph.sponge_h - ph.sponge_zs));
-          R -= ph.sponge_rate * x * x * r0 * (uc - target[c]);
-        }
-        const T gp = (g.prof(ph.alpha0, k + ck) * g.at(p, i + ci, j + cj, k + ck, G_EVEN) -
-                      g.prof(ph.alpha0, k - ck) * g.at(p, i - ci, j - cj, k - ck, G_EVEN)) *
-                     (T(0.5) * g.ih(c));
-        out[c][m] = (r0 * veln[c][m] + ph.dt * (-r0 * gp + R)) / r0;
-      }
-    }
-  }
-}
-
-// ---- Poisson right side (Eq. pressure_correction with Appendix A) -------------
-// compact: rhs = alpha0 / dt D(rho0 u^) - C(psi^k),
-//   C = sum_l [psi_{l+2} - 4 psi_{l+1} + 6 psi_l - 4 psi_{l-1} + psi_{l-2}] / (4 Delta_l^2)
-// wide:    rhs = D(rho0 u^) / dt
-template <typename T>
-__global__ void __launch_bounds__(NTHREADS)
-    k_rhs(Grid<T> g, Phys<T> ph, int op, const T* __restrict__ ou, const T* __restrict__ ov,
-          const T* __restrict__ ow, const T* __restrict__ psi, T* __restrict__ rhs) {
-  const T* hat[3] = {ou, ov, ow};
-  for (long long t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-    int i, j, k0, k1;
-    tile_origin(g, t, i, j, k0, k1);
-    if (i >= g.nx || j >= g.ny) continue;
-    for (int k = k0; k < k1; ++k) {
-      T div = T(0);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const int di = d == 0, dj = d == 1, dk = d == 2;
-        div += (g.prof(ph.rho0, k + dk) * g.at(hat[d], i + di, j + dj, k + dk, vghost(d)) -
-                g.prof(ph.rho0, k - dk) * g.at(hat[d], i - di, j - dj, k - dk, vghost(d))) *
-               (T(0.5) * g.ih(d));
-      }
-      T val;
-      if (op == LES_OP_COMPACT) {
-        T C = T(0);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const int di = d == 0, dj = d == 1, dk = d == 2;
-          const T ih = g.ih(d);
-          C += (g.at(psi, i + 2 * di, j + 2 * dj, k + 2 * dk, G_EVEN) -
-                T(4) * g.at(psi, i + di, j + dj, k + dk, G_EVEN) + T(6) * g.at(psi, i, j, k, G_EVEN) -
-                T(4) * g.at(psi, i - di, j - dj, k - dk, G_EVEN) +
-                g.at(psi, i - 2 * di, j - 2 * dj, k - 2 * dk, G_EVEN)) *
-               (T(0.25) * ih * ih);
-        }
-        val = ph.alpha0[k] / ph.dt * div - C;
-      } else {
-        val = div / ph.dt;
-      }
-      rhs[g.lin(i, j, k)] = val;
-    }
-  }
-}
-
 // ---- a7: correction (Sec. 2.4) ----------------------------------------------
 // u^{k+1} = u^ - dt G(psi), p^{k+1} = p^k + rho0 psi, psi = alpha0 dp
 template <typename T>
@@ -610,47 +341,6 @@ cudaError_t launch_thermo(const StageArgs<T>& a, const T* th, const T* qt, T* te
 }
 
 template <typename T>
-cudaError_t launch_nu(const StageArgs<T>& a, const T* u, const T* v, const T* w, const T* un, const T* vn,
-                      const T* wn, const T* b, T* uh, T* vh, T* wh, T* nu) {
-  if (un) {
-    VelView<T, true> V{{u, v, w}, {un, vn, wn}};
-    ProfScope ps(a.prof, KI_NU_HALF, a.st);
-    k_nu<T, true><<<a.lc.grid, a.lc.block, 0, a.st>>>(a.g, a.ph, V, b, uh, vh, wh, nu);
-  } else {
-    VelView<T, false> V{{u, v, w}, {u, v, w}};
-    ProfScope ps(a.prof, KI_NU, a.st);
-    k_nu<T, false><<<a.lc.grid, a.lc.block, 0, a.st>>>(a.g, a.ph, V, b, nullptr, nullptr, nullptr, nu);
-  }
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_scalar(const StageArgs<T>& a, const T* u, const T* v, const T* w, const T* nu,
-                          const T* thk, const T* qtk, const T* thh, const T* qth, const T* srad, T* th_out,
-                          T* qt_out) {
-  ProfScope ps(a.prof, KI_SCALAR, a.st);
-  k_scalar<T><<<a.lc.grid, a.lc.block, 0, a.st>>>(a.g, a.ph, u, v, w, nu, thk, qtk, thh, qth, srad, th_out,
-                                                   qt_out);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_momentum(const StageArgs<T>& a, const T* uh, const T* vh, const T* wh, const T* un,
-                            const T* vn, const T* wn, const T* nu, const T* p, const T* b, T* ou, T* ov, T* ow) {
-  ProfScope ps(a.prof, KI_MOMENTUM, a.st);
-  k_momentum<T><<<a.lc.grid, a.lc.block, 0, a.st>>>(a.g, a.ph, uh, vh, wh, un, vn, wn, nu, p, b, ou, ov, ow);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_rhs(const StageArgs<T>& a, int op, const T* ou, const T* ov, const T* ow, const T* psi,
-                       T* rhs) {
-  ProfScope ps(a.prof, KI_RHS, a.st);
-  k_rhs<T><<<a.lc.grid, a.lc.block, 0, a.st>>>(a.g, a.ph, op, ou, ov, ow, psi, rhs);
-  return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t launch_correct(const StageArgs<T>& a, const T* ou, const T* ov, const T* ow, const T* psi, T* u,
                            T* v, T* w, T* p) {
   ProfScope ps(a.prof, KI_CORRECT, a.st);
@@ -676,13 +366,6 @@ cudaError_t launch_cfl_max(const StageArgs<T>& a, const T* u, const T* v, const 
 
 #define LES_INSTANTIATE(T)                                                                                  \
   template cudaError_t launch_thermo<T>(const StageArgs<T>&, const T*, const T*, T*, T*, T*, T*);          \
-  template cudaError_t launch_nu<T>(const StageArgs<T>&, const T*, const T*, const T*, const T*, const T*, \
-                                    const T*, const T*, T*, T*, T*, T*);                                   \
-  template cudaError_t launch_scalar<T>(const StageArgs<T>&, const T*, const T*, const T*, const T*,       \
-                                        const T*, const T*, const T*, const T*, const T*, T*, T*);         \
-  template cudaError_t launch_momentum<T>(const StageArgs<T>&, const T*, const T*, const T*, const T*,     \
-                                          const T*, const T*, const T*, const T*, const T*, T*, T*, T*);   \
-  template cudaError_t launch_rhs<T>(const StageArgs<T>&, int, const T*, const T*, const T*, const T*, T*); \
   template cudaError_t launch_correct<T>(const StageArgs<T>&, const T*, const T*, const T*, const T*, T*, \
                                          T*, T*, T*);                                                      \
   template cudaError_t launch_diag<T>(const StageArgs<T>&, const T*, const T*, const T*, const T*,         \

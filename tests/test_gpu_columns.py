@@ -1,10 +1,12 @@
-"""The column-march stencil kernels (16-byte lanes, z windows in registers),
-through the C ABI, against the FP64 oracle stage by stage.
+"""The column-march stencil kernels (z windows in registers), through the C
+ABI, against the FP64 oracle stage by stage.
 
-They run by default on grids whose nx is a multiple of 32 lanes x (16 bytes /
-element size) and whose ny is a multiple of 8; the FP64 instantiation (two
-doubles per lane, tiles 64 nodes wide) is held to the same bars as the other
-stencil paths.  Edge cases: one tile across x (the edge lanes wrap onto the
+The correction and the right side run by default on grids whose nx is a
+multiple of 32 lanes x (16 bytes / element size), the predictors on grids
+whose nx is a multiple of 64 (two nodes per lane), both with ny a multiple of
+8; the FP64 instantiation is held to the same bars as the other stencil paths,
+with every physics term on and with the dry set (advection and Smagorinsky
+only), which the predictors compile as a separate specialisation.  Edge cases: one tile across x (the edge lanes wrap onto the
 same tile), one tile across y (the rows j -+ 2 wrap inside the tile), the
 fewest planes (nz = 2 with walls) and both boundary conditions.  The FP32
 instantiation is compared with the rolling kernels on the same inputs.
@@ -56,14 +58,12 @@ def _moist(nx, ny, nz, walls, advection="quick", precision=64):
     return c
 
 
-@pytest.mark.parametrize("path", [0, 4])
 @pytest.mark.parametrize("shape,walls,advection", [
     ((64, 16, 12), True, "quick"), ((128, 8, 10), False, "quick"), ((64, 8, 2), True, "quick"),
     ((64, 24, 9), False, "weno3"), ((192, 8, 6), True, "weno3")])
-def test_column_stages_fp64(les_mod, shape, walls, advection, path):
-    """Stage-by-stage FP64 parity; path 0 (default: column correction, right
-    side and scalar predictor) and path 4 (the momentum predictor as a column
-    march too)."""
+def test_column_stages_fp64(les_mod, shape, walls, advection):
+    """Stage-by-stage FP64 parity of the default path: every stencil stage as
+    a column march."""
     from oracle import Oracle
     case = _moist(*shape, walls, advection)
     st = _state(case)
@@ -71,7 +71,6 @@ def test_column_stages_fp64(les_mod, shape, walls, advection, path):
     sim.set_state(st)
     ref = Oracle(case, st)
     assert sim.tuning()["stencil_path"] == 0
-    sim.set_tuning(stencil_path=path)
     sim.stage("begin")
     ref.begin_step()
     for k in range(case.K):
@@ -96,6 +95,41 @@ def test_column_stages_fp64(les_mod, shape, walls, advection, path):
     ref.end_step()
 
 
+@pytest.mark.parametrize("shape", [(64, 16, 12), (192, 8, 5)])
+def test_column_stages_fp64_dry(les_mod, shape):
+    """The dry Taylor-Green physics (advection and Smagorinsky only, periodic,
+    the predictors' compile-time specialisation) stage by stage against the
+    oracle."""
+    from oracle import Oracle
+    case = inputs.tgv(32, nxyz=shape, precision=64, steps_tol=1e-13)
+    st = _state(case)
+    st["theta_l"] = st["theta_l"] + inputs.uniform(9, 6, case.n, -1, 1).reshape(case.shape)
+    st["q_t"] = 5e-3 + 1e-3 * inputs.uniform(9, 7, case.n, -1, 1).reshape(case.shape)
+    sim = les_mod.Simulation(case)
+    sim.set_state(st)
+    ref = Oracle(case, st)
+    sim.stage("begin")
+    ref.begin_step()
+    assert sim.dt == ref.dt
+    for k in range(case.K):
+        sim.stage("scalar")
+        ref.scalar_stage()
+        for f in ("theta_l", "q_t"):
+            assert rel(sim.get(f), ref.get(f)) < 1e-13, (k, f)
+        sim.stage("momentum")
+        ref.momentum_stage()
+        for f in ("u_hat", "v_hat", "w_hat"):
+            assert rel(sim.get(f), ref.get(f)) < 1e-12, (k, f)
+        sim.stage("solve")
+        ref.solve_stage()
+        sim.stage("correct")
+        ref.correct_stage()
+        for f in ("u", "v", "w"):
+            assert rel(sim.get(f), ref.get(f)) < 1e-9, (k, f)
+    sim.stage("end")
+    ref.end_step()
+
+
 @pytest.mark.parametrize("op", ["compact", "wide"])
 def test_column_rhs_and_correct_fp64_exact_inputs(les_mod, op):
     """The right side node by node against the oracle's, with the compact
@@ -115,15 +149,20 @@ def test_column_rhs_and_correct_fp64_exact_inputs(les_mod, op):
     assert np.max(np.abs(sim.get("rhs") - ref.get("rhs"))) <= 1e-11 * np.max(np.abs(ref.get("rhs")))
 
 
-@pytest.mark.parametrize("path", [0, 4])
-@pytest.mark.parametrize("shape,walls", [((128, 16, 24), True), ((256, 8, 10), False), ((128, 8, 2), True)])
-def test_column_fp32_matches_rolling(les_mod, shape, walls, path):
-    """FP32: the column kernels and the rolling kernels (stencil_path 3) on the
-    same inputs agree to float rounding, stage by stage, for three steps."""
+@pytest.mark.parametrize("shape,walls", [((128, 16, 24), True), ((256, 8, 10), False), ((128, 8, 2), True),
+                                         ((192, 16, 6), False)])
+def test_column_fp32_matches_rolling(les_mod, shape, walls):
+    """FP32: the column kernels and the rolling kernels (stencil_path 1) on the
+    same inputs agree to float rounding, stage by stage, for three steps.  The
+    two round differently (the column predictors scale the tendency by
+    dt / rho0, the rolling ones divide rho0 phi + dt T by rho0; their x faces
+    are summed in other groupings), and nine sub-iterations amplify the
+    differences: 5e-6 relative for u^ (about 40 ulps of float), 1e-4 for the
+    right side (a difference of nearly equal fluxes) and 1e-5 for the fields."""
     case = _moist(*shape, walls, precision=32).replace(dt=0.5)
     st = _state(case)
     sims = []
-    for path in (path, 3):
+    for path in (0, 1):
         s = les_mod.Simulation(case)
         s.set_state(st)
         s.set_tuning(stencil_path=path)
@@ -135,6 +174,6 @@ def test_column_fp32_matches_rolling(les_mod, shape, walls, path):
             if stg == "momentum":
                 for f in ("u_hat", "v_hat", "w_hat", "rhs"):
                     a, b = sims[0].get(f), sims[1].get(f)
-                    assert rel(a, b) < (1e-4 if f == "rhs" else 1e-6), (step, f)
+                    assert rel(a, b) < (1e-4 if f == "rhs" else 5e-6), (step, f)
     for f in ("u", "v", "w", "theta_l", "q_t"):
         assert rel(sims[0].get(f), sims[1].get(f)) < 1e-5, f

@@ -144,7 +144,7 @@ def test_decomposed_step_matches_single_domain(mods, precision, px, py):
                       tol=1e-10 if precision == 64 else 1e-6)
     state = _cbl_state(case)
     sim = les.Simulation(case)
-    sim.set_tuning(stencil_path=3)
+    sim.set_tuning(stencil_path=1)
     sim.set_state(state)
     snaps = {}
 
@@ -162,7 +162,7 @@ def test_decomposed_step_matches_single_domain(mods, precision, px, py):
     for r in range(nr):
         sd = decomp.DecomposedSimulation(case, px, py, r, lambda s, rv, st, r=r: ex.exchange(r, s, rv, st),
                                          lambda v, r=r: ex.allreduce(r, v))
-        sd.sim.set_tuning(stencil_path=3)
+        sd.sim.set_tuning(stencil_path=1)
         sd.set_global_state(state)
         subs.append(sd)
     out = [None] * nr
