@@ -129,9 +129,11 @@ __device__ __forceinline__ double c_sin(double a) { return sin(a); }
 template <typename T>
 __device__ __forceinline__ int zsrc(const Grid<T>& g, int kk, int gh, T& sgn) {
   sgn = T(1);
-  if (!g.walls) {
-    while (kk < 0) kk += g.nz;
-    while (kk >= g.nz) kk -= g.nz;
+  if (!g.walls) {  // kk is within two periods of the range (nz >= 2)
+    kk += kk < 0 ? g.nz : 0;
+    kk += kk < 0 ? g.nz : 0;
+    kk -= kk >= g.nz ? g.nz : 0;
+    kk -= kk >= g.nz ? g.nz : 0;
     return kk;
   }
   if (kk < 0) {
@@ -221,7 +223,10 @@ struct ScaCol {
 template <typename T>
 struct ScaSmem {
   static constexpr int U = 0, V = 4, W = 8, B = 12, PT = 16, PQ = 20, RAW = 24, NPLANES = 28;
-  static constexpr size_t bytes() { return ((size_t)NPLANES * kPL<T> + 2 * (size_t)kNPL<T>) * sizeof(T); }
+  // after the planes: the nu ring [2 nu planes], then the fluxes of both
+  // scalars through the tile's PR + 1 y faces of one level
+  static constexpr size_t yf_offset() { return (size_t)NPLANES * kPL<T> + 2 * (size_t)kNPL<T>; }
+  static constexpr size_t bytes() { return (yf_offset() + (size_t)(PR + 1) * 2 * kTW<T>) * sizeof(T); }
 };
 
 template <typename T, int ADV, unsigned FIX>
@@ -230,6 +235,7 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_scalar_col(ScaCol<
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   T* NU = sm + (size_t)ScaSmem<T>::NPLANES * PL;
+  T* YF = sm + ScaSmem<T>::yf_offset();  // [PR + 1 faces][2 scalars][TW]
   const Grid<T>& g = a.g;
   const Phys<T>& ph = a.ph;
   // the physics switches, fixed at compile time for the common set
@@ -279,7 +285,9 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_scalar_col(ScaCol<
       const int gz = zsrc(g, kk, gh, sg);
       T* dstp = fp(ring, kk);
       const T* s0 = src + (size_t)gz * plane;
-      for (int q = 0; q < nst; ++q) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (q >= nst) break;
         const int r = q == 0 ? st0 : st1;
         if (sg == T(1)) {
           cp_async_bytes<kLB<T>>(at(dstp, r, xl), s0 + src_own[q]);
@@ -313,7 +321,9 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_scalar_col(ScaCol<
       for (int f = 0; f < 4; ++f) {
         T* dstp = sm + (size_t)(ScaSmem<T>::RAW + f) * PL;
         const T* s0 = src[f] + (size_t)gz * plane;
-        for (int q = 0; q < nst; ++q) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (q >= nst) break;
           const int r = q == 0 ? st0 : st1;
           cp_async_bytes<kLB<T>>(at(dstp, r, xl), s0 + src_own[q]);
           if (edge) cp_async_bytes<kLB<T>>(at(dstp, r, dst_ext), s0 + src_ext[q]);
@@ -323,7 +333,11 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_scalar_col(ScaCol<
     // phibar of level kk from the raw plane, all threads over the 12 rows
     auto average_raw = [&](int kk) {
       constexpr int NV = PL / VV;
-      for (int e = threadIdx.x; e < 2 * NV; e += PW * PWARP) {
+      constexpr int NIT = (2 * NV + PW * PWARP - 1) / (PW * PWARP);
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        const int e = threadIdx.x + it * PW * PWARP;
+        if (e >= 2 * NV) break;
         const int s = e / NV, o = (e - s * NV) * VV;
         const T* rk = sm + (size_t)(ScaSmem<T>::RAW + 2 * s) * PL + o;
         const T* rh = rk + PL;
@@ -400,10 +414,14 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_scalar_col(ScaCol<
       Vec<T> o;
       nu_lane<T>(sm, RINGU, RINGB, kk, nurow + 1, xl, lane, g, ph, flags, fb, o.v);
       sts(nr + xl, o);
-      if (edge) {
-        const int xo = lane == 0 ? -1 : TW;
-        nr[xo] = nu_node(kk, nurow + 1, xo);
-      }
+    };
+    // nu_t of level kk at the nodes just beyond the tile's ends on the row
+    // warps' rows (the x faces at the ends read them): halo warp PR, one node
+    // per lane of lanes 0 .. 2 PR - 1
+    auto nu_edges = [&](int kk) {
+      if (wid != PR || lane >= 2 * PR) return;
+      const int r = 1 + (lane >> 1), xo = (lane & 1) ? TW : -1;
+      nup(kk)[r * RL + VV + xo] = nu_node(kk, r + 1, xo);
     };
 
     // ---- the lower z face of the run's first plane (prologue) -------------
@@ -420,6 +438,7 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_scalar_col(ScaCol<
     __syncthreads();
     // nu_t of level k0 on every row; of level k0-1 on the row warps' nodes
     nu_row(k0);
+    nu_edges(k0);
     T nu_lo[VV];
     if (wid < PR) nu_lane<T>(sm, RINGU, RINGB, k0 - 1, srow, xl, lane, g, ph, flags, fb, nu_lo);
     __syncthreads();
@@ -462,6 +481,30 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_scalar_col(ScaCol<
       zface(k0 - 1, nu_lo, nu0.v, flz);
     }
 
+    // fluxes of both scalars through the y face between staged rows sr and
+    // sr + 1 of level kk, for this lane's nodes
+    auto yface = [&](int kk, int sr, T (&out)[2][VV]) {
+      const T r0 = g.prof(ph.rho0, kk);
+      const T* nk = nup(kk) + VV + xl;
+      const Vec<T> nlo = lds(nk + (sr - 1) * RL), nhi = lds(nk + sr * RL);
+      const T* vr = at(fp(ScaSmem<T>::V, kk), sr, xl);
+      const Vec<T> vlo = lds(vr), vhi = lds(vr + RL);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const T* pr = at(fp(q == 0 ? ScaSmem<T>::PT : ScaSmem<T>::PQ, kk), sr, xl);
+        const Vec<T> pm = lds(pr - RL), p0 = lds(pr), p1 = lds(pr + RL), p2 = lds(pr + 2 * RL);
+#pragma unroll
+        for (int c = 0; c < VV; ++c) {
+          T F = T(0);
+          if (adv_on) F = T(0.5) * (r0 * vlo.v[c] + r0 * vhi.v[c]);
+          const T K = r0 * (T(0.5) * (nlo.v[c] + nhi.v[c]));
+          T adv = T(0);
+          if (adv_on) adv = F * face_value(ADV, F, pm.v[c], p0.v[c], p1.v[c], p2.v[c]);
+          out[q][c] = -adv + K * inv_s[q] * (p1.v[c] - p0.v[c]) * g.idy;
+        }
+      }
+    };
+
     // ---- the march ----------------------------------------------------------
     for (int k = k0; k < k1; ++k) {
       cp_wait<0>();
@@ -470,7 +513,23 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_scalar_col(ScaCol<
       stage_vel(k + 3);
       cp_commit();
       nu_row(k + 1);
-      __syncthreads();  // nu_t of level k+1, phibar of level k+2 visible; raw plane free
+      nu_edges(k + 1);
+      // each row warp's upper y face of level k, and (halo warp PR + 1) the
+      // face below the tile's first row: computed once, the lower faces read
+      // back below
+      T yup[2][VV];
+      if (wid != PR) {
+        const int sr = wid < PR ? srow : 1;
+        yface(k, sr, yup);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          Vec<T> o;
+#pragma unroll
+          for (int c = 0; c < VV; ++c) o.v[c] = yup[q][c];
+          sts(YF + ((size_t)(sr - 1) * 2 + q) * TW + xl, o);
+        }
+      }
+      __syncthreads();  // nu_t of level k+1, phibar of level k+2, the y fluxes visible; raw plane free
       stage_raw(k + 3);
       cp_commit();
       if (wid >= PR) continue;
@@ -509,34 +568,13 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_scalar_col(ScaCol<
           for (int c = 0; c < VV; ++c) tend[q][c] += (fl[c + 1] - fl[c]) * g.idx;
         }
       }
-      // y faces: j-1/2 and j+1/2 of every node
-      {
-        const Vec<T> nm = lds(nk + wid * RL), no = lds(nk + (wid + 1) * RL), np = lds(nk + (wid + 2) * RL);
-        const T* vr = at(fp(ScaSmem<T>::V, k), srow, xl);
-        const Vec<T> vm = lds(vr - RL), vo = lds(vr), vp = lds(vr + RL);
+      // y faces: the upper one of this row from yup, the lower one (the upper
+      // face of the row below) from the shared buffer
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const T* pr = at(fp(q == 0 ? ScaSmem<T>::PT : ScaSmem<T>::PQ, k), srow, xl);
-          const Vec<T> p2m = lds(pr - 2 * RL), p1m = lds(pr - RL), p0 = lds(pr), p1p = lds(pr + RL),
-                       p2p = lds(pr + 2 * RL);
+      for (int q = 0; q < 2; ++q) {
+        const Vec<T> lo = lds(YF + ((size_t)wid * 2 + q) * TW + xl);
 #pragma unroll
-          for (int c = 0; c < VV; ++c) {
-            T Fm = T(0), Fp = T(0);
-            if (adv_on) {
-              Fm = T(0.5) * (r0 * vm.v[c] + r0 * vo.v[c]);
-              Fp = T(0.5) * (r0 * vo.v[c] + r0 * vp.v[c]);
-            }
-            const T Km = r0 * (T(0.5) * (nm.v[c] + no.v[c])), Kp = r0 * (T(0.5) * (no.v[c] + np.v[c]));
-            T am = T(0), ap = T(0);
-            if (adv_on) {
-              am = Fm * face_value(ADV, Fm, p2m.v[c], p1m.v[c], p0.v[c], p1p.v[c]);
-              ap = Fp * face_value(ADV, Fp, p1m.v[c], p0.v[c], p1p.v[c], p2p.v[c]);
-            }
-            const T flm = -am + Km * inv_s[q] * (p0.v[c] - p1m.v[c]) * g.idy;
-            const T flp = -ap + Kp * inv_s[q] * (p1p.v[c] - p0.v[c]) * g.idy;
-            tend[q][c] += (flp - flm) * g.idy;
-          }
-        }
+        for (int c = 0; c < VV; ++c) tend[q][c] += (yup[q][c] - lo.v[c]) * g.idy;
       }
       // z faces: the upper face of this level; the lower one was carried up
       {
@@ -658,7 +696,9 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_momentum_col(MomCo
       for (int f = 0; f < 7; ++f) {
         T* dstp = sm + (size_t)(MomSmem<T>::RAW + f) * PL;
         const T* s0 = src[f] + (size_t)gz * plane;
-        for (int q = 0; q < nst; ++q) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (q >= nst) break;
           const int r = q == 0 ? st0 : st1;
           cp_async_bytes<kLB<T>>(at(dstp, r, xl), s0 + src_own[q]);
           if (edge) cp_async_bytes<kLB<T>>(at(dstp, r, dst_ext), s0 + src_ext[q]);
@@ -671,7 +711,9 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_momentum_col(MomCo
       const int gz = zsrc(g, kk, G_EVEN, sg);
       T* dstp = fp(MomSmem<T>::B, kk);
       const T* s0 = a.b + (size_t)gz * plane;
-      for (int q = 0; q < nst; ++q) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (q >= nst) break;
         const int r = q == 0 ? st0 : st1;
         cp_async_bytes<kLB<T>>(at(dstp, r, xl), s0 + src_own[q]);
         if (edge) cp_async_bytes<kLB<T>>(at(dstp, r, dst_ext), s0 + src_ext[q]);
@@ -773,10 +815,12 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_momentum_col(MomCo
       Vec<T> o;
       nu_lane<T>(sm, RINGU, RINGB, kk, nurow + 1, xl, lane, g, ph, flags, fb, o.v);
       sts(nr + xl, o);
-      if (edge) {
-        const int xo = lane == 0 ? -1 : TW;
-        nr[xo] = nu_node(kk, nurow + 1, xo);
-      }
+    };
+    // nu_t just beyond the tile's ends on the row warps' rows: halo warp PR
+    auto nu_edges = [&](int kk) {
+      if (wid != PR || lane >= 2 * PR) return;
+      const int r = 1 + (lane >> 1), xo = (lane & 1) ? TW : -1;
+      nup(kk)[r * RL + VV + xo] = nu_node(kk, r + 1, xo);
     };
     const int j = j0 + wid;
     const int srow = wid + 2;
@@ -840,6 +884,7 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_momentum_col(MomCo
     for (int kk = k0 - 2; kk <= k0 + 1; ++kk) stage_direct(kk);
     __syncthreads();
     nu_row(k0);
+    nu_edges(k0);
     T nu_lo[VV];
     if (wid < PR) nu_lane<T>(sm, RINGU, RINGB, k0 - 1, srow, xl, lane, g, ph, flags, fb, nu_lo);
     __syncthreads();
@@ -860,6 +905,7 @@ __global__ void __launch_bounds__(PW* PWARP, kMinBlocks<T>) k_momentum_col(MomCo
       stage_b(k + 3);
       cp_commit();
       nu_row(k + 1);
+      nu_edges(k + 1);
       __syncthreads();  // nu_t of level k+1 visible
       if (wid >= PR) continue;
       const size_t m = (size_t)k * plane + (size_t)j * g.nx + x0 + xl;
