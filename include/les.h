@@ -220,6 +220,25 @@ int les_get_state(les_handle *h, int32_t field, void *dst, int32_t on_device);
 int les_set_states(les_handle *h, int32_t count, const int32_t *fields, const void *const *srcs,
                    int32_t on_device);
 
+/* Upload a state for a later step without waiting: the count (1 .. 8)
+ * fields are copied from host memory srcs[q] (pinned, for the copies to run
+ * asynchronously) into the caller's device buffer staging (16-byte aligned,
+ * count * nx * ny * nz elements, field q at element q * nx * ny * nz) on
+ * copy_stream, and the call returns.  The next BEGIN stage (les_step or
+ * les_stage) makes the handle's stream wait for those copies and takes the
+ * staged fields as the state (a device-to-device copy), so the upload of a
+ * state overlaps the steps enqueued before that BEGIN.  Up to two prefetches
+ * may be pending, each with its own staging buffer; each is consumed by one
+ * BEGIN, oldest first.  Before copying, copy_stream waits for the BEGIN that
+ * consumed the previous prefetch, so a staging buffer can be reused for the
+ * prefetch after next.  The caller keeps srcs and staging alive until the
+ * consuming BEGIN has run.  LES_ERR_STATE with two prefetches pending;
+ * LES_ERR_INVALID_ARG for a bad or repeated id, a NULL pointer or a
+ * misaligned staging buffer.  The paper has no counterpart: the input
+ * pipeline of callers that step a stream of host-held states. */
+int les_prefetch_states(les_handle *h, int32_t count, const int32_t *fields, const void *const *srcs,
+                        void *staging, void *copy_stream);
+
 /* Byte offset of a field's current buffer inside the workspace (buffers of
  * the scalars and u^n rotate between steps and sub-iterations). */
 int les_field_offset(les_handle *h, int32_t field, size_t *offset);

@@ -140,6 +140,22 @@ struct les_handle {
   std::string err;
   les_step_stats acc{};
   Profiler prof;
+  // states uploaded ahead (les_prefetch_states), consumed in order at BEGIN
+  struct Prefetch {
+    const char* staging = nullptr;
+    int count = 0;
+    int fields[8] = {};
+    cudaEvent_t ready = nullptr;
+  };
+  Prefetch pf[2];
+  int pf_head = 0, pf_n = 0;
+  cudaEvent_t pf_consumed = nullptr;  // recorded after the last consumption
+
+  ~les_handle() {
+    for (auto& p : pf)
+      if (p.ready) cudaEventDestroy(p.ready);
+    if (pf_consumed) cudaEventDestroy(pf_consumed);
+  }
 
   void* field_ptr(int f) {
     switch (f) {
@@ -295,10 +311,25 @@ void reference_profiles(const les_config& c, const double* rho0_z, std::vector<d
   }
 }
 
+// the oldest prefetched state becomes the state (after its copies land)
+int take_prefetch(les_handle* h) {
+  les_handle::Prefetch& p = h->pf[h->pf_head];
+  const size_t bytes = h->n * h->es;
+  cudaError_t e = cudaStreamWaitEvent(h->st, p.ready, 0);
+  for (int q = 0; q < p.count && e == cudaSuccess; ++q)
+    e = cudaMemcpyAsync(h->field_ptr(p.fields[q]), p.staging + (size_t)q * bytes, bytes, cudaMemcpyDeviceToDevice,
+                        h->st);
+  if (e == cudaSuccess) e = cudaEventRecord(h->pf_consumed, h->st);
+  h->pf_head ^= 1;
+  h->pf_n -= 1;
+  return e == cudaSuccess ? LES_OK : h->cuda_fail(e, "prefetched state");
+}
+
 template <typename T>
 int stage_begin(les_handle* h) {
   const size_t bytes = h->n * sizeof(T);
   cudaError_t e;
+  if (h->pf_n > 0 && take_prefetch(h) != LES_OK) return LES_ERR_CUDA;
   auto a = stage_args<T>(h);
   if (h->dt <= 0) {
     if ((e = launch_cfl_max<T>(a, (T*)h->fixed[B_U], (T*)h->fixed[B_V], (T*)h->fixed[B_W], h->partials,
@@ -720,6 +751,36 @@ int les_set_states(les_handle* h, int32_t count, const int32_t* fields, const vo
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->st);
   return e == cudaSuccess ? LES_OK : h->cuda_fail(e, "set_states");
+}
+
+int les_prefetch_states(les_handle* h, int32_t count, const int32_t* fields, const void* const* srcs, void* staging,
+                        void* copy_stream) {
+  if (!h) return LES_ERR_INVALID_ARG;
+  if (count < 1 || count > 8 || !fields || !srcs || !staging || ((uintptr_t)staging % 16) != 0)
+    return h->fail(LES_ERR_INVALID_ARG, "bad prefetch arguments");
+  for (int q = 0; q < count; ++q) {
+    if (!h->field_ptr(fields[q]) || !srcs[q]) return h->fail(LES_ERR_INVALID_ARG, "bad field id or NULL source");
+    for (int r = 0; r < q; ++r)
+      if (fields[r] == fields[q]) return h->fail(LES_ERR_INVALID_ARG, "repeated field");
+  }
+  if (h->pf_n >= 2) return h->fail(LES_ERR_STATE, "two prefetched states are pending");
+  cudaError_t e = cudaSuccess;
+  if (!h->pf_consumed) e = cudaEventCreateWithFlags(&h->pf_consumed, cudaEventDisableTiming);
+  les_handle::Prefetch& p = h->pf[(h->pf_head + h->pf_n) & 1];
+  if (e == cudaSuccess && !p.ready) e = cudaEventCreateWithFlags(&p.ready, cudaEventDisableTiming);
+  cudaStream_t cs = (cudaStream_t)copy_stream;
+  // the staging buffer may be the one the last BEGIN read: wait for that read
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, h->pf_consumed, 0);
+  const size_t bytes = h->n * h->es;
+  for (int q = 0; q < count && e == cudaSuccess; ++q)
+    e = cudaMemcpyAsync((char*)staging + (size_t)q * bytes, srcs[q], bytes, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(p.ready, cs);
+  if (e != cudaSuccess) return h->cuda_fail(e, "prefetch");
+  p.staging = (const char*)staging;
+  p.count = count;
+  for (int q = 0; q < count; ++q) p.fields[q] = fields[q];
+  h->pf_n += 1;
+  return LES_OK;
 }
 
 int les_get_state(les_handle* h, int32_t field, void* dst, int32_t on_device) {

@@ -46,7 +46,7 @@ EXPORTED = ("les_config_default", "les_workspace_bytes", "les_init", "les_destro
             "les_set_warm_model", "les_unet_set_output_scale", "les_unet_get_output_scale", "les_unet_set_loss",
             "les_ensemble_step", "les_set_states", "les_dd_workspace_bytes", "les_dd_create", "les_dd_destroy",
             "les_dd_local_shape", "les_dd_poisson_solve", "les_dd_last_error", "les_dd_step_config",
-            "les_dd_halo_exchange", "les_dd_stage_solve")
+            "les_dd_halo_exchange", "les_dd_stage_solve", "les_prefetch_states")
 
 
 class LesConfig(C.Structure):
@@ -201,6 +201,8 @@ def load_library(path: str = LIB_PATH):
     lib.les_dd_poisson_solve.argtypes = [vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl)]
     lib.les_dd_last_error.restype = C.c_char_p
     lib.les_dd_last_error.argtypes = [vp]
+    lib.les_prefetch_states.restype = C.c_int
+    lib.les_prefetch_states.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(vp), vp, vp]
     lib.les_dd_step_config.restype = C.c_int
     lib.les_dd_step_config.argtypes = [vp, cfgp]
     lib.les_dd_halo_exchange.restype = C.c_int
@@ -331,6 +333,19 @@ class Simulation:
         ptrs = (C.c_void_p * len(names))(*[C.c_void_p(hosts[k].data_ptr()) for k in names])
         rc = self.lib.les_set_states(self.h, len(names), ids, ptrs, 0)
         _check(self.lib, self.h, rc, "set states (host)")
+
+    def prefetch_from_host(self, hosts: dict, staging, stream) -> None:
+        """les_prefetch_states: hosts[name] (pinned torch tensors) into the
+        device buffer `staging` (torch tensor of at least len(hosts) fields)
+        on `stream` (a torch.cuda.Stream); the next BEGIN takes them."""
+        names = list(hosts)
+        if staging.numel() * staging.element_size() < len(names) * self.n * self.esize:
+            raise ValueError("staging buffer too small")
+        ids = (C.c_int32 * len(names))(*[FIELDS[k] for k in names])
+        ptrs = (C.c_void_p * len(names))(*[C.c_void_p(hosts[k].data_ptr()) for k in names])
+        rc = self.lib.les_prefetch_states(self.h, len(names), ids, ptrs, C.c_void_p(staging.data_ptr()),
+                                          C.c_void_p(stream.cuda_stream))
+        _check(self.lib, self.h, rc, "prefetch states")
 
     def get_to_host(self, name: str, host) -> None:
         rc = self.lib.les_get_state(self.h, FIELDS[name], C.c_void_p(host.data_ptr()), 0)
