@@ -234,6 +234,7 @@ class Clocks:
 TRAFFIC_SOURCES = {
     "cg_wave": ("les_cg_wave.cu", "les_gridsync.cuh", "les_common.cuh"),
     "scalar": ("les_predict_col.cu", "les_common.cuh"),
+    "momentum": ("les_predict_col.cu", "les_common.cuh"),
     "rhs": ("les_stencil_col.cu",),
     "correct": ("les_stencil_col.cu",),
 }
