@@ -1,14 +1,14 @@
-// les_stencil.cu -- explicit stencil stages of one LES time step on sm_103a.
+// les_stencil.cu -- the pointwise and column stages of one LES time step on
+// sm_103a: thermodynamics and buoyancy (Sec. 2.1-2.2), the longwave radiation
+// source, the correction of Sec. 2.4 on grids the column kernel does not
+// take, and the FP64 diagnostics.
 //
-// Sec. 2.1-2.3 (thermodynamics, buoyancy, Smagorinsky-Lilly viscosity, sponge)
-// and Sec. 2.4 (QUICK advection, 2nd-order central diffusion, the momentum and
-// scalar predictors of the iterative predictor-corrector scheme, the Poisson
-// right side with the Appendix A fourth-difference term, the correction).
-//
-// Every kernel walks 32x8-thread tiles grid-stride and marches each thread
-// through a run of z-planes; all loads go through the read-only path so that
-// the stencil neighbours of a tile are served from L1 / L2.  Templated on the
-// field precision T (float or double); every sum that leaves a kernel is FP64.
+// The tile kernels walk 32x8-thread tiles grid-stride and march each thread
+// through a run of z-planes; the thermodynamics streams 16-byte chunks where
+// the rows allow.  Templated on the field precision T (float or double);
+// every sum that leaves a kernel is FP64.
+#include <type_traits>
+
 #include "les_gridsync.cuh"
 #include "les_internal.h"
 
@@ -74,7 +74,26 @@ struct Thermo {
   }
 };
 
-// a1: T, q_l and buoyancy b = g (alpha - alpha0) / alpha0, alpha = R_m T / p0
+// a1 at one node of level k: T, q_l and buoyancy b = g (alpha - alpha0) /
+// alpha0, alpha = R_m T / p0
+template <typename T>
+__device__ __forceinline__ void thermo_node(const Phys<T>& ph, int k, T thc, T qtc, T& tc, T& qlc, T& bc) {
+  Thermo<T> td{ph.p0[k], ph.p00};
+  if (ph.flags & LES_PHYS_MOIST) {
+    td.adjust(thc, qtc, ph.sat_tol, ph.sat_maxit, tc, qlc);
+  } else {
+    qlc = T(0);
+    tc = td.exner(qtc, T(0)) * thc;
+  }
+  if (ph.flags & LES_PHYS_BUOY) {
+    const T a0 = ph.alpha0[k];
+    const T alpha = td.rm(qtc, qlc) * tc / td.p0;
+    bc = T(kGrav) * (alpha - a0) / a0;
+  } else {
+    bc = T(0);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS) k_thermo_cells(Grid<T> g, Phys<T> ph, const T* __restrict__ th,
                                                            const T* __restrict__ qt, T* __restrict__ temp,
@@ -86,26 +105,46 @@ __global__ void __launch_bounds__(NTHREADS) k_thermo_cells(Grid<T> g, Phys<T> ph
     if (i >= g.nx || j >= g.ny) continue;
     for (int k = k0; k < k1; ++k) {
       const size_t m = g.lin(i, j, k);
-      Thermo<T> td{ph.p0[k], ph.p00};
-      const T thc = th[m], qtc = qt[m];
-      T tc, qlc;
-      if (ph.flags & LES_PHYS_MOIST) {
-        td.adjust(thc, qtc, ph.sat_tol, ph.sat_maxit, tc, qlc);
-      } else {
-        qlc = T(0);
-        tc = td.exner(qtc, T(0)) * thc;
-      }
+      T tc, qlc, bc;
+      thermo_node(ph, k, th[m], qt[m], tc, qlc, bc);
       temp[m] = tc;
       ql[m] = qlc;
-      if (ph.flags & LES_PHYS_BUOY) {
-        const T a0 = ph.alpha0[k];
-        const T alpha = td.rm(qtc, qlc) * tc / td.p0;
-        b[m] = T(kGrav) * (alpha - a0) / a0;
-      } else {
-        b[m] = T(0);
-      }
+      b[m] = bc;
       srad[m] = T(0);
     }
+  }
+}
+
+// The same as a stream of 16-byte chunks (V nodes of one row; nx a multiple
+// of V): each thread loads its chunks of theta_l and q_t with 16-byte loads,
+// many in flight across the grid, and writes the four outputs likewise.
+template <typename T>
+__global__ void __launch_bounds__(256) k_thermo_vec(Grid<T> g, Phys<T> ph, const T* __restrict__ th,
+                                                    const T* __restrict__ qt, T* __restrict__ temp,
+                                                    T* __restrict__ ql, T* __restrict__ b, T* __restrict__ srad) {
+  constexpr int V = 16 / (int)sizeof(T);
+  using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const long long pc = (long long)g.nx * g.ny / V;  // chunks per plane
+  const long long nc = pc * g.nz;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(c / pc);
+    const V16 tv = __ldcs(reinterpret_cast<const V16*>(th) + c), qv = __ldcs(reinterpret_cast<const V16*>(qt) + c);
+    const T* tp = reinterpret_cast<const T*>(&tv);
+    const T* qp = reinterpret_cast<const T*>(&qv);
+    V16 to, lo, bo, zo;
+    T* top = reinterpret_cast<T*>(&to);
+    T* lop = reinterpret_cast<T*>(&lo);
+    T* bop = reinterpret_cast<T*>(&bo);
+    T* zop = reinterpret_cast<T*>(&zo);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      thermo_node(ph, k, tp[v], qp[v], top[v], lop[v], bop[v]);
+      zop[v] = T(0);
+    }
+    __stcs(reinterpret_cast<V16*>(temp) + c, to);
+    __stcs(reinterpret_cast<V16*>(ql) + c, lo);
+    __stcs(reinterpret_cast<V16*>(b) + c, bo);
+    __stcs(reinterpret_cast<V16*>(srad) + c, zo);
   }
 }
 
@@ -328,7 +367,16 @@ template <typename T>
 cudaError_t launch_thermo(const StageArgs<T>& a, const T* th, const T* qt, T* temp, T* ql, T* b, T* srad) {
   {
     ProfScope ps(a.prof, KI_THERMO, a.st);
-    k_thermo_cells<T><<<a.lc.grid, a.lc.block, 0, a.st>>>(a.g, a.ph, th, qt, temp, ql, b, srad);
+    constexpr int V = 16 / (int)sizeof(T);
+    const bool vec = a.g.nx % V == 0 && ((uintptr_t)th | (uintptr_t)qt | (uintptr_t)temp | (uintptr_t)ql |
+                                          (uintptr_t)b | (uintptr_t)srad) % 16 == 0;
+    if (vec) {
+      const long long nc = (long long)a.g.nx * a.g.ny * a.g.nz / V;
+      const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>((nc + 255) / 256, 1LL << 20));
+      k_thermo_vec<T><<<grid, 256, 0, a.st>>>(a.g, a.ph, th, qt, temp, ql, b, srad);
+    } else {
+      k_thermo_cells<T><<<a.lc.grid, a.lc.block, 0, a.st>>>(a.g, a.ph, th, qt, temp, ql, b, srad);
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !(a.ph.flags & LES_PHYS_RAD)) return e;
