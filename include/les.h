@@ -287,8 +287,8 @@ int les_diagnostics(les_handle *h, double *out);
  * rejected with LES_ERR_INVALID_ARG and a message in err.  No cudaMalloc,
  * cudaFree or allocating library routine is called.
  * The first call on a device looks up the array's device address with that
- * device current (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture.  The cached address belongs to the device's
+ * device current (cudaGetSymbolAddress) and caches it.  The cached address
+ * belongs to the device's
  * current context: after cudaDeviceReset() on that device, further calls in
  * the same process are invalid.  Every call on a device shares the one array,
  * which keeps the previous call's contents (the call clears the control
