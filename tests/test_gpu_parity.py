@@ -702,3 +702,59 @@ def test_largest_workload_full_size_invariants(les_mod):
     psi = sim.view("psi")
     assert abs(float(psi.double().mean())) < 1e-6 * float(psi.abs().max())
     sim.close()
+
+
+def test_largest_workload_sampled_stage_outputs(les_mod):
+    """The 1536 x 1536 x 256 Taylor-Green box in the bench's configuration
+    (FP32, the column kernels), node by node at sampled nodes against the
+    FP64 oracle: after the first thermodynamics, scalar and momentum stages
+    (before any solve), a node's theta_l, q_t, u^ and Poisson right side
+    depend on the initial state within three nodes, so the oracle run on the
+    periodic 9 x 9 x 9 box around the node (the wrap reaches only nodes
+    beyond that distance) gives them exactly.  The samples include the
+    grid's corners and the column kernels' tile and lane edges."""
+    from oracle import Oracle
+    if torch.cuda.get_device_properties(0).total_memory < 100e9:
+        pytest.skip("needs the GB300's memory")
+    case = inputs.tgv(32, nxyz=(1536, 1536, 256), precision=32, steps_tol=1e-6)
+    st = inputs.initial_state(case)
+    st["theta_l"] = st["theta_l"] + inputs.uniform(9, 6, case.n, -1, 1).reshape(case.shape)
+    sim = les_mod.Simulation(case)
+    sim.set_state(st)
+    for stg in ("begin", "scalar", "momentum"):
+        sim.stage(stg)
+    nz, ny, nx = case.shape
+    r = np.random.default_rng(7)
+    samples = [(0, 0, 0), (nz - 1, ny - 1, nx - 1), (128, 7, 63), (1, 8, 64), (255, 767, 1), (17, 1535, 1534)]
+    samples += [tuple(int(v) for v in (r.integers(nz), r.integers(ny), r.integers(nx))) for _ in range(26)]
+    names = ("theta_l", "q_t", "u_hat", "v_hat", "w_hat", "rhs")
+    kk = torch.tensor([s[0] for s in samples], device="cuda")
+    jj = torch.tensor([s[1] for s in samples], device="cuda")
+    ii = torch.tensor([s[2] for s in samples], device="cuda")
+    got = {n: sim.view(n)[kk, jj, ii].double().cpu().numpy() for n in names}
+    dt = sim.dt
+    sim.close()
+    H = 4
+    small = case.replace(nx=2 * H + 1, ny=2 * H + 1, nz=2 * H + 1, dt=dt)
+    worst = {n: 0.0 for n in names}
+    for q, (k, j, i) in enumerate(samples):
+        zk = (k - H + np.arange(2 * H + 1)) % nz
+        yj = (j - H + np.arange(2 * H + 1)) % ny
+        xi = (i - H + np.arange(2 * H + 1)) % nx
+        ref = Oracle(small, {f: st[f][zk][:, yj][:, :, xi] for f in ("u", "v", "w", "p", "theta_l", "q_t")})
+        ref.dt = dt
+        ref.begin_step()
+        ref.scalar_stage()
+        ref.momentum_stage()
+        for n in names:
+            box = ref.get(n)
+            want = box[H, H, H]
+            scale = {"theta_l": 300.0, "q_t": 1.0}.get(n, float(np.abs(box).max()))
+            worst[n] = max(worst[n], abs(got[n][q] - want) / scale)
+    print("largest worst relative error at the samples:", worst)
+    # FP32 rounding (2^-24 = 6e-8) of a few operations per term: measured
+    # 1e-7 for theta_l, 3e-8 .. 6e-8 for u^ and the right side
+    assert worst["theta_l"] < 1e-6 and worst["q_t"] < 1e-6
+    for n in ("u_hat", "v_hat", "w_hat"):
+        assert worst[n] < 1e-6, n
+    assert worst["rhs"] < 1e-5
