@@ -43,6 +43,8 @@
 #include <mutex>
 #include <string>
 
+#include <type_traits>
+
 #include "les_gridsync.cuh"
 #include "les_internal.h"
 
@@ -219,25 +221,57 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(const __
   const long long gstride = (long long)gridDim.x * NT;
   const long long gtid = (long long)blockIdx.x * NT + tid;
 
-  // the 7-point operator straight from global memory (set-up sweeps only)
-  auto lap_global = [&](const T* v, int i, int j, int k) -> T {
-    const size_t row = (size_t)k * plane + (size_t)j * f.nx;
-    const T c2 = T(2) * __ldcg(v + row + i);
-    const T xm = __ldcg(v + row + wrapw(i - 1, f.nx)), xp = __ldcg(v + row + wrapw(i + 1, f.nx));
-    const T ym = __ldcg(v + (size_t)k * plane + (size_t)wrapw(j - 1, f.ny) * f.nx + i);
-    const T yp = __ldcg(v + (size_t)k * plane + (size_t)wrapw(j + 1, f.ny) * f.nx + i);
-    const T zm = __ldcg(v + (size_t)zmapw(k - 1, f.nz, f.walls) * plane + (size_t)j * f.nx + i);
-    const T zp = __ldcg(v + (size_t)zmapw(k + 1, f.nz, f.walls) * plane + (size_t)j * f.nx + i);
-    return (xm + xp - c2) * cx + (ym + yp - c2) * cy + (zm + zp - c2) * cz;
+  // the set-up and gauge sweeps in 16-byte chunks of VC nodes along x (nx is
+  // a multiple of 32 and every vector 16-byte aligned here), chunks dealt to
+  // the grid's threads in order
+  constexpr int VC = 16 / (int)sizeof(T);
+  using VQ = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  struct Ch {
+    T e[VC];
   };
-  // every node once, rows of x dealt to the blocks (one division per row, not
-  // three 64-bit ones per node)
-  auto each_node = [&](auto&& body) {
-    const long long nrow = (long long)f.ny * f.nz;
-    for (long long rw = blockIdx.x; rw < nrow; rw += gridDim.x) {
-      const int j = (int)(rw % f.ny), k = (int)(rw / f.ny);
-      const long long m0 = rw * f.nx;
-      for (int i = tid; i < f.nx; i += NT) body(m0 + i, i, j, k);
+  auto ldch = [](const T* ptr) -> Ch {
+    const VQ q = __ldcg(reinterpret_cast<const VQ*>(ptr));
+    Ch c;
+    if constexpr (sizeof(T) == 4) {
+      c.e[0] = q.x, c.e[1] = q.y, c.e[2] = q.z, c.e[3] = q.w;
+    } else {
+      c.e[0] = q.x, c.e[1] = q.y;
+    }
+    return c;
+  };
+  auto stch = [](T* ptr, const Ch& c) {
+    VQ q;
+    if constexpr (sizeof(T) == 4) {
+      q.x = c.e[0], q.y = c.e[1], q.z = c.e[2], q.w = c.e[3];
+    } else {
+      q.x = c.e[0], q.y = c.e[1];
+    }
+    __stcg(reinterpret_cast<VQ*>(ptr), q);
+  };
+  const int cpr = f.nx / VC;  // chunks per row
+  const long long nch = f.n / VC;
+  auto each_chunk = [&](auto&& body) {
+    for (long long c = gtid; c < nch; c += gstride) {
+      const long long rw = c / cpr;
+      const int i0 = (int)(c - rw * cpr) * VC;
+      body((size_t)c * VC, i0, (int)(rw % f.ny), (int)(rw / f.ny));
+    }
+  };
+  // the 7-point operator at a chunk's nodes straight from global memory
+  // (set-up sweeps only), and the chunk's own values
+  auto lap_chunk = [&](const T* v, size_t m, int i0, int j, int k, Ch& lap, Ch& own) {
+    const size_t row = (size_t)k * plane + (size_t)j * f.nx;
+    own = ldch(v + m);
+    const T xl = __ldcg(v + row + wrapw(i0 - 1, f.nx)), xr = __ldcg(v + row + wrapw(i0 + VC, f.nx));
+    const Ch ym = ldch(v + (size_t)k * plane + (size_t)wrapw(j - 1, f.ny) * f.nx + i0);
+    const Ch yp = ldch(v + (size_t)k * plane + (size_t)wrapw(j + 1, f.ny) * f.nx + i0);
+    const Ch zm = ldch(v + (size_t)zmapw(k - 1, f.nz, f.walls) * plane + (size_t)j * f.nx + i0);
+    const Ch zp = ldch(v + (size_t)zmapw(k + 1, f.nz, f.walls) * plane + (size_t)j * f.nx + i0);
+#pragma unroll
+    for (int q = 0; q < VC; ++q) {
+      const T c2 = T(2) * own.e[q];
+      const T xm = q == 0 ? xl : own.e[q - 1], xp = q == VC - 1 ? xr : own.e[q + 1];
+      lap.e[q] = (xm + xp - c2) * cx + (ym.e[q] + yp.e[q] - c2) * cy + (zm.e[q] + zp.e[q] - c2) * cz;
     }
   };
 
@@ -248,9 +282,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(const __
   {
     WaveSum<T> s[1];
     int cnt = 0;
-    for (long long m = gtid; m < f.n; m += gstride) {
-      s[0].add(__ldcg(f.b + m));
-      if ((++cnt & 15) == 0) s[0].flush();
+    for (long long c = gtid; c < nch; c += gstride) {
+      const Ch bq = ldch(f.b + (size_t)c * VC);
+#pragma unroll
+      for (int q = 0; q < VC; ++q) s[0].add(bq.e[q]);
+      if ((++cnt & 3) == 0) s[0].flush();
     }
     double t[1];
     const bool ok = wave_sum_t0<1>(s, gs, t);
@@ -266,13 +302,21 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(const __
   if (!status) {
     WaveSum<T> s[2];
     int cnt = 0;
-    each_node([&](long long m, int i, int j, int k) {
-      const T bm = __ldcg(f.b + m) - mean;
-      const T rv = bm - lap_global(f.x, i, j, k);
-      __stcg(f.r[0] + m, rv);
-      s[0].add(rv * rv);
-      s[1].add(bm * bm);
-      if ((++cnt & 15) == 0) {
+    each_chunk([&](size_t m, int i0, int j, int k) {
+      Ch lap, xo;
+      lap_chunk(f.x, m, i0, j, k, lap, xo);
+      const Ch bq = ldch(f.b + m);
+      Ch rq;
+#pragma unroll
+      for (int q = 0; q < VC; ++q) {
+        const T bm = bq.e[q] - mean;
+        const T rv = bm - lap.e[q];
+        rq.e[q] = rv;
+        s[0].add(rv * rv);
+        s[1].add(bm * bm);
+      }
+      stch(f.r[0] + m, rq);
+      if ((++cnt & 3) == 0) {
         s[0].flush();
         s[1].flush();
       }
@@ -319,9 +363,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(const __
   if (!status) {
     WaveSum<T> s[1];
     int cnt = 0;
-    each_node([&](long long m, int i, int j, int k) {
-      s[0].add(__ldcg(f.r[0] + m) * lap_global(f.r[0], i, j, k));
-      if ((++cnt & 15) == 0) s[0].flush();
+    each_chunk([&](size_t m, int i0, int j, int k) {
+      Ch lap, ro;
+      lap_chunk(f.r[0], m, i0, j, k, lap, ro);
+#pragma unroll
+      for (int q = 0; q < VC; ++q) s[0].add(ro.e[q] * lap.e[q]);
+      if ((++cnt & 3) == 0) s[0].flush();
     });
     double t[1];
     const bool ok = wave_sum_t0<1>(s, gs, t);
@@ -589,9 +636,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(const __
   if (status != 5) {
     WaveSum<T> s[1];
     int cnt = 0;
-    for (long long m = gtid; m < f.n; m += gstride) {
-      s[0].add(__ldcg(f.x + m));
-      if ((++cnt & 15) == 0) s[0].flush();
+    for (long long c = gtid; c < nch; c += gstride) {
+      const Ch xq = ldch(f.x + (size_t)c * VC);
+#pragma unroll
+      for (int q = 0; q < VC; ++q) s[0].add(xq.e[q]);
+      if ((++cnt & 3) == 0) s[0].flush();
     }
     double t[1];
     const bool ok = wave_sum_t0<1>(s, gs, t);
@@ -604,7 +653,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_cg_wave(const __
     status = sc.status;
     if (status != 5) {
       const T mx = sc.mean;
-      for (long long m = gtid; m < f.n; m += gstride) __stcg(f.x + m, status == 4 ? T(0) : __ldcg(f.x + m) - mx);
+      for (long long c = gtid; c < nch; c += gstride) {
+        Ch xq = ldch(f.x + (size_t)c * VC);
+#pragma unroll
+        for (int q = 0; q < VC; ++q) xq.e[q] = status == 4 ? T(0) : xq.e[q] - mx;
+        stch(f.x + (size_t)c * VC, xq);
+      }
     }
   }
   if (blockIdx.x == 0 && tid == 0) {
