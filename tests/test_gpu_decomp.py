@@ -130,18 +130,21 @@ class _Whole:
         return self.sim.stage("solve")
 
 
-@pytest.mark.parametrize("precision,px,py", [(64, 2, 2), (64, 2, 1), (64, 1, 2), (32, 2, 2)])
-def test_decomposed_step_matches_single_domain(mods, precision, px, py):
+@pytest.mark.parametrize("precision,px,py,warm", [(64, 2, 2, "zero"), (64, 2, 1, "zero"), (64, 1, 2, "zero"),
+                                                  (32, 2, 2, "zero"), (64, 2, 2, "prev")])
+def test_decomposed_step_matches_single_domain(mods, precision, px, py, warm):
     """Sub-domains of one GPU, each stepped by its own thread through
     decomp.decomposed_step with the library's halo exchange (two-node halos,
     LocalExchange) and decomposed solve, against the single-domain step on
     the same kernels (the rolling predictors on both): after the step's
     thermodynamics every node of each widened sub-domain, halos included,
     and after the first predictors every owned node equal bit for bit; after
-    two steps the fields equal to the solver tolerance."""
+    two steps the fields equal to the solver tolerance.  With the previous
+    solution as first guess ("prev") both sides start each solve from their
+    own previous psi."""
     les, decomp = mods
     case = inputs.cbl(nx=32, ny=24, nz=24, dx=35.0, dz=40.0, precision=precision,
-                      tol=1e-10 if precision == 64 else 1e-6)
+                      tol=1e-10 if precision == 64 else 1e-6, warm=warm)
     state = _cbl_state(case)
     sim = les.Simulation(case)
     sim.set_tuning(stencil_path=1)
