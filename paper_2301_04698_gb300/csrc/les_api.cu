@@ -22,7 +22,7 @@ enum Buf : int {
   B_U = 0, B_V, B_W, B_UN, B_VN, B_WN, B_P,
   B_THA, B_QTA, B_THB, B_QTB, B_THH, B_QTH,
   B_UHAT, B_VHAT, B_WHAT, B_RHS, B_PSI,
-  B_B, B_QL, B_T, B_SRAD, B_NU, B_UHALF, B_VHALF, B_WHALF,
+  B_B, B_QL, B_T, B_SRAD, B_E0, B_E1,  // B_E*: spare vectors of the flexible CG
   B_R, B_PA, B_PB, B_Q,
   B_NFIXED
 };
@@ -261,11 +261,8 @@ SolverArgs<T> solver_args(les_handle* h) {
   s.prof = &h->prof;
   s.bar = h->bar;
   s.fused = h->cfg.solver_path == 0 ? &h->fused : nullptr;
-  // the nu / u^{n+1/2} fields of the direct-load predictors are free during
-  // a solve and serve as the extra vectors of the one-barrier CG
-  s.e0 = (T*)h->fixed[B_NU];
-  s.e1 = (T*)h->fixed[B_UHALF];
-  s.e2 = (T*)h->fixed[B_VHALF];
+  s.e0 = (T*)h->fixed[B_E0];
+  s.e1 = (T*)h->fixed[B_E1];
   return s;
 }
 

@@ -283,9 +283,8 @@ struct SolverArgs {
   FusedBar* bar = nullptr;          // persistent-solver barrier (workspace)
   int nsm = 0;                      // SMs of the device (the persistent solves' budget)
   int guard = 0;                    // restart from x = 0 if ||b - A x0|| > ||b|| (learned guesses)
-  T* e0 = nullptr;                  // extra vectors for the one-barrier variant
+  T* e0 = nullptr;                  // two spare vectors (the flexible CG's z and b)
   T* e1 = nullptr;
-  T* e2 = nullptr;
   const FusedCfg* fused = nullptr;  // enables the persistent CG when eligible
 };
 
