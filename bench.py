@@ -118,6 +118,9 @@ def parse():
                     help="--poisson-only: les_tuning.cg_max_blocks (0: the library's choice, all SMs)")
     ap.add_argument("--stencil-path", type=int, default=-1,
                     help="les_tuning.stencil_path of the timed workload (-1: the library's default)")
+    ap.add_argument("--oracle-one-thread", type=int, default=0, metavar="SIDE",
+                    help="internal: time one oracle step of a SIDE x SIDE full-column sample in this process and "
+                         "print {value, secs} (the single-thread leg of cpu_baseline runs it with OMP_NUM_THREADS=1)")
     return ap.parse_args()
 
 
@@ -299,6 +302,19 @@ def time_oracle(case, steps: int, warm: int):
     o.step(steps)
     dt = time.perf_counter() - t0
     return case.n * steps / dt, dt
+
+
+def oracle_one_thread(args, side: int):
+    """The oracle on one host core: a child process with OMP_NUM_THREADS=1
+    times one step of a side x side full-column sample; (value, secs, desc)."""
+    import subprocess
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", args.workload, "--oracle-one-thread", str(side)]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        return None
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return r["value"], r["secs"], r["sample"]
 
 
 def cores():
@@ -531,6 +547,12 @@ def main():
     args = parse()
     if args.poisson_only:
         return poisson_only(args)
+    if args.oracle_one_thread:
+        case = workload(args.workload, 1)
+        sample, desc = oracle_sample(case, args, side=args.oracle_one_thread)
+        val, secs = time_oracle(sample, 1, 0)
+        print(json.dumps({"value": val, "secs": secs, "sample": desc}), flush=True)
+        return 0
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         rc = reference_arm(args, rank, world)
@@ -753,6 +775,11 @@ def main():
         val, secs = time_oracle(sample, 1, 0)
         cpu = {"value": val, "unit": UNIT, "cores": cores(), "kind": "oracle",
                "sample": f"1 step of the {desc} (FP64, {secs:.1f} s)"}
+        # and on one core (a smaller sample of about the same time)
+        one = oracle_one_thread(args, 32 if big else 16)
+        if one is not None:
+            cpu["one_core"] = {"value": one[0], "cores": 1,
+                               "sample": f"1 step of the {one[2]} (FP64, {one[1]:.1f} s)"}
 
     if rank == 0:
         line = {
