@@ -763,7 +763,10 @@ int solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, dou
   // z-runs: enough columns x runs to give every block work, runs as long as
   // possible (each run re-forms two planes of p and r' below it)
   const long long ncol = (long long)f.ntx * f.nty;
-  const long long want = std::max<long long>(1, std::min<long long>((long long)f.nz, (G + ncol - 1) / ncol));
+  // the (column, run) units are dealt to the G persistent blocks in turns:
+  // with fewer columns than blocks take at most G units, one turn (the
+  // G-th + 1 unit would double the iteration for the rest)
+  const long long want = ncol >= G ? 1 : std::max<long long>(1, std::min<long long>((long long)f.nz, G / ncol));
   f.zrun = (int)((f.nz + want - 1) / want);
   f.nchunk = (f.nz + f.zrun - 1) / f.zrun;
   G = std::max<long long>(1, std::min<long long>(G, ncol * f.nchunk));
