@@ -576,7 +576,9 @@ def test_rolling_cg_matches_oracle(les_mod, precision, walls, shape):
     (32, False, (160, 160, 20), 64),    # 32 x 32 columns, blocks looping
     (32, True, (320, 64, 12), 0),       # six interior 64 x 16 columns: TMA-staged planes
     (64, False, (160, 96, 10), 0),      # interior 32 x 32 columns, FP64 boxes
-    (32, False, (384, 64, 16), 64)])    # TMA and per-thread columns mixed in each block
+    (32, False, (384, 64, 16), 64),     # TMA and per-thread columns mixed in each block
+    (32, True, (384, 64, 16), 7),       # 24 columns, 7 blocks: 3 turns, then 3 columns in plane shares
+    (64, False, (192, 48, 9), 5)])      # 9 columns, 5 blocks: 1 turn, then 4 columns in plane shares
 def test_wave_cg_matches_oracle(les_mod, precision, walls, shape, max_blocks):
     """The one-pass CG with 64 x 16 or 32 x 32 columns and register windows
     (variant 4; interior columns staged by TMA boxes, edge columns by
