@@ -341,6 +341,115 @@ __global__ void __launch_bounds__(NTHREADS)
   }
 }
 
+// a8 for FP32 fields as a stream of 16-byte chunks (four nodes of a row),
+// with the per-node arithmetic of k_diag: the fields at the chunk's nodes by
+// 16-byte loads, the divergence's neighbours along y as the chunks of the
+// rows beside it and along z as the chunks of the planes above and below
+// (their ghost rule resolved once per chunk), along x from the chunk and
+// its two edge nodes.  nx a multiple of 4, every field 16-byte aligned.
+__global__ void __launch_bounds__(NTHREADS)
+    k_diag_vec(Grid<float> g, Phys<float> ph, const float* __restrict__ u, const float* __restrict__ v,
+               const float* __restrict__ w, const float* __restrict__ p, const float* __restrict__ th,
+               const float* __restrict__ qt, const float* __restrict__ ql, double* partials, SolverCtl* ctl,
+               double* out) {
+  constexpr int NS = 7;  // the sums: 0 theta, 1 q_t, 2-4 u, 5 2 x kinetic energy, 6 q_l
+  F2 sum[NS];
+  float run[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    sum[q] = F2{0.f, 0.f};
+    run[q] = 0.f;
+  }
+  float cmax = 0.f, dmax = 0.f, bad = 0.f;
+  int cnt = 0;
+  const int cpr = g.nx / 4;
+  const long long pc = (long long)cpr * g.ny, nc = pc * g.nz;
+  const int nthr = blockDim.x * blockDim.y;
+  const long long t0 = (long long)blockIdx.x * nthr + threadIdx.x + blockDim.x * threadIdx.y;
+  auto ld4 = [](const float* q) { return __ldg(reinterpret_cast<const float4*>(q)); };
+  auto el = [](const float4& a, int n) { return n == 0 ? a.x : (n == 1 ? a.y : (n == 2 ? a.z : a.w)); };
+  for (long long c = t0; c < nc; c += (long long)gridDim.x * nthr) {
+    const int k = (int)(c / pc);
+    const int rem = (int)(c - (long long)k * pc);
+    const int j = rem / cpr, i0 = (rem - j * cpr) * 4;
+    const size_t m = (size_t)c * 4;
+    const size_t plane = (size_t)g.nx * g.ny;
+    const float4 u4 = ld4(u + m), v4 = ld4(v + m), w4 = ld4(w + m);
+    const float4 p4 = ld4(p + m), t4 = ld4(th + m), q4 = ld4(qt + m), l4 = ld4(ql + m);
+    const float ul = g.at(u, i0 - 1, j, k, G_UV), ur = g.at(u, i0 + 4, j, k, G_UV);
+    const size_t row = (size_t)k * plane + (size_t)i0;
+    const float4 vm = ld4(v + row + (size_t)g.wrap(j - 1, g.ny) * g.nx);
+    const float4 vp = ld4(v + row + (size_t)g.wrap(j + 1, g.ny) * g.nx);
+    // w on the planes k -+ 1 under the antisymmetric ghost rule
+    int kzm = k - 1, kzp = k + 1;
+    float szm = 1.f, szp = 1.f;
+    if (g.walls) {
+      if (kzm < 0) kzm = 0, szm = -1.f;
+      if (kzp >= g.nz) kzp = g.nz - 1, szp = -1.f;
+    } else {
+      kzm = g.wrap(kzm, g.nz);
+      kzp = g.wrap(kzp, g.nz);
+    }
+    const size_t col = (size_t)j * g.nx + i0;
+    const float4 wm = ld4(w + (size_t)kzm * plane + col), wp = ld4(w + (size_t)kzp * plane + col);
+    const float r0 = ph.rho0[k];
+    const float rzm = g.prof(ph.rho0, k - 1), rzp = g.prof(ph.rho0, k + 1);
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const float uc[3] = {el(u4, n), el(v4, n), el(w4, n)};
+      const float thn = el(t4, n), qtn = el(q4, n);
+      run[0] += r0 * thn;
+      run[1] += r0 * qtn;
+      float ke = 0.f, cfl = 0.f;
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        run[2 + cc] += r0 * uc[cc];
+        ke += uc[cc] * uc[cc];
+        cfl += fabsf(uc[cc]) * g.ih(cc);
+      }
+      const float xp = n == 3 ? ur : el(u4, n + 1), xm = n == 0 ? ul : el(u4, n - 1);
+      float div = (r0 * xp - r0 * xm) * (0.5f * g.ih(0));
+      div += (r0 * el(vp, n) - r0 * el(vm, n)) * (0.5f * g.ih(1));
+      div += (rzp * (szp * el(wp, n)) - rzm * (szm * el(wm, n))) * (0.5f * g.ih(2));
+      run[5] += r0 * ke;
+      run[6] += r0 * el(l4, n);
+      cmax = fmaxf(cmax, cfl * ph.dt);
+      dmax = fmaxf(dmax, fabsf(div));
+      const float vals[6] = {uc[0], uc[1], uc[2], el(p4, n), thn, qtn};
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        if (!isfinite(vals[q])) bad += 1.f;
+    }
+    if ((++cnt & 3) == 0)
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        f2_acc(sum[q], run[q]);
+        run[q] = 0.f;
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < NS; ++q) f2_acc(sum[q], run[q]);
+  double acc[LES_NDIAG];
+  acc[0] = f2_value(sum[0]);
+  acc[1] = f2_value(sum[1]);
+  acc[2] = f2_value(sum[2]);
+  acc[3] = f2_value(sum[3]);
+  acc[4] = f2_value(sum[4]);
+  acc[5] = 0.5 * f2_value(sum[5]);
+  acc[6] = cmax;
+  acc[7] = dmax;
+  acc[8] = bad;
+  acc[9] = f2_value(sum[6]);
+  const double dV = (double)g.dx * (double)g.dy * (double)g.dz;
+#pragma unroll
+  for (int q : {0, 1, 2, 3, 4, 5, 9}) acc[q] *= dV;
+  double res[LES_NDIAG];
+  if (grid_reduce<LES_NDIAG>(acc, (1u << 6) | (1u << 7), partials, &ctl->tickets[TK_DIAG], res)) {
+#pragma unroll
+    for (int q = 0; q < LES_NDIAG; ++q) out[q] = res[q];
+  }
+}
+
 // max over cells of |u|/dx + |v|/dy + |w|/dz (Courant-number step)
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
@@ -400,6 +509,14 @@ template <typename T>
 cudaError_t launch_diag(const StageArgs<T>& a, const T* u, const T* v, const T* w, const T* p, const T* th,
                         const T* qt, const T* ql, double* partials, SolverCtl* ctl, double* out_dev) {
   ProfScope ps(a.prof, KI_DIAG, a.st);
+  if constexpr (sizeof(T) == 4) {
+    const bool vec = a.g.nx % 4 == 0 && ((uintptr_t)u | (uintptr_t)v | (uintptr_t)w | (uintptr_t)p |
+                                          (uintptr_t)th | (uintptr_t)qt | (uintptr_t)ql) % 16 == 0;
+    if (vec) {
+      k_diag_vec<<<a.lc.grid, a.lc.block, 0, a.st>>>(a.g, a.ph, u, v, w, p, th, qt, ql, partials, ctl, out_dev);
+      return cudaGetLastError();
+    }
+  }
   k_diag<T><<<a.lc.grid, a.lc.block, 0, a.st>>>(a.g, a.ph, u, v, w, p, th, qt, ql, partials, ctl, out_dev);
   return cudaGetLastError();
 }
