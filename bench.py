@@ -269,6 +269,17 @@ def traffic_for(kernel: str, units: float):
         return None
 
 
+def traffic_capture(kernel: str) -> str:
+    """Where the per-unit DRAM figure of `kernel` comes from (the captured grid)."""
+    try:
+        ent = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        grid = "x".join(str(v) for v in ent["capture"]["grid"])
+        return (f"profiles/traffic.json: DRAM bytes per {ent['per']} of an ncu capture on {grid}, scaled to this "
+                "launch's units")
+    except Exception:
+        return "no record"
+
+
 # ---------------------------------------------------------------------------
 def oracle_sample(case, args, budget=2.0e6, side=None):
     """A bounded sample of the workload for the FP64 oracle: the same physics
@@ -650,8 +661,7 @@ def main():
                 "bytes_per_launch": top["bytes_per_launch"], "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "frac_of_8tbs": achieved / 8000.0, "profiled_steps": aux_prof,
-                "traffic_source": "profiles/traffic.json: DRAM bytes per unit of an ncu capture on 512x512x64, "
-                                  "scaled to this launch's units"}
+                "traffic_source": traffic_capture(top["name"])}
     kernels = {}
     for k in kstats:
         mean = k["total_ms"] / max(k["timed"], 1)
