@@ -47,6 +47,9 @@ struct RollArgs {
   int nx, ny, nz, walls;
   T cx, cy, cz;  // 1/dx^2, 1/dy^2, 1/dz^2
   int ntx, nty, zrun, nchunk;
+  // runs of a block as in the column CG: units u = blockIdx.x, + gridDim.x,
+  // ... below nunits, then an equal share of the planes of the columns left
+  int nunits, tail_planes, tail_per;
   long long n;
   const T* b;
   T* x;
@@ -126,7 +129,6 @@ __global__ void __launch_bounds__(CX* CY, 3) k_cg_roll(RollArgs<T> f) {
   } sc;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + CX * ty;
   const long long ncol = (long long)f.ntx * f.nty;
-  const long long nblk = ncol * f.nchunk;
   const size_t plane = (size_t)f.nx * f.ny;
   const T cx = f.cx, cy = f.cy, cz = f.cz;
   GridSync gs{f.bar, f.partials, f.spin_cycles, f.expected, 0u};
@@ -269,10 +271,24 @@ __global__ void __launch_bounds__(CX* CY, 3) k_cg_roll(RollArgs<T> f) {
     const T* pold = f.p[(iter + 1) & 1];  // p_{i-1}
     T* pw = f.p[iter & 1];
     LongSum<T> s[4];  // r'.r', r'.w, r'.q, p.q
-    for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-      const int col = (int)(blk % ncol), chunk = (int)(blk / ncol);
+    int u = blockIdx.x;
+    int ts = (int)blockIdx.x * f.tail_per, te = min(ts + f.tail_per, f.tail_planes);
+    for (;;) {
+      int col, k0, k1;
+      if (u < f.nunits) {
+        col = u % (int)ncol;
+        k0 = (u / (int)ncol) * f.zrun;
+        k1 = min(k0 + f.zrun, f.nz);
+        u += gridDim.x;
+      } else if (ts < te) {  // the units are whole columns here
+        col = f.nunits + ts / f.nz;
+        k0 = ts % f.nz;
+        k1 = min(f.nz, k0 + (te - ts));
+        ts += k1 - k0;
+      } else {
+        break;
+      }
       const int x0 = (col % f.ntx) * CX, y0 = (col / f.ntx) * CY;
-      const int k0 = chunk * f.zrun, k1 = min(k0 + f.zrun, f.nz);
       const int i = x0 + tx, j = y0 + ty;
       const bool own = i < f.nx && j < f.ny;
       const int eo = sidx(tx, ty);
@@ -477,16 +493,26 @@ int poisson_solve_roll(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T
   long long G = (long long)std::max(1, per_sm) * nsm;
   G = std::min<long long>(G, fc.max_blocks);
   G = std::min<long long>(G, 8LL * nsm);  // the partials hold 2 x 4 x 8 slots per SM
-  // z-runs: enough columns x runs to give every block work, runs as long as
-  // possible (each run re-forms two planes of p and one of q, r' below it)
+  // z-runs as long as possible (each run re-forms two planes of p and one of
+  // q, r' below it), dealt to the G persistent blocks as in the column CG:
+  // fewer columns than blocks, at most G units (one turn); more, whole
+  // columns in full turns and the columns left in equal plane shares
   const long long ncol = (long long)f.ntx * f.nty;
-  // the (column, run) units are dealt to the G persistent blocks in turns:
-  // with fewer columns than blocks take at most G units, one turn (the
-  // G-th + 1 unit would double the iteration for the rest)
-  const long long want = ncol >= G ? 1 : std::max<long long>(1, std::min<long long>((long long)f.nz, G / ncol));
-  f.zrun = (int)((f.nz + want - 1) / want);
-  f.nchunk = (f.nz + f.zrun - 1) / f.zrun;
-  G = std::max<long long>(1, std::min<long long>(G, ncol * f.nchunk));
+  if (ncol >= G) {
+    f.zrun = f.nz;
+    f.nchunk = 1;
+    f.nunits = (int)((ncol / G) * G);
+    f.tail_planes = (int)((ncol - f.nunits) * f.nz);
+    f.tail_per = (int)((f.tail_planes + G - 1) / G);
+  } else {
+    const long long want = std::max<long long>(1, std::min<long long>((long long)f.nz, G / ncol));
+    f.zrun = (int)((f.nz + want - 1) / want);
+    f.nchunk = (f.nz + f.zrun - 1) / f.zrun;
+    f.nunits = (int)(ncol * f.nchunk);
+    f.tail_planes = 0;
+    f.tail_per = 0;
+    G = std::max<long long>(1, std::min<long long>(G, f.nunits));
+  }
   f.expected = (unsigned)G + (unsigned)std::max(0, fc.missing);
   if ((e = cudaMemsetAsync(a.bar, 0, sizeof(FusedBar), a.st)) != cudaSuccess) {
     if (err) *err = std::string("rolling CG barrier reset: ") + cudaGetErrorString(e);
