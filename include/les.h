@@ -341,8 +341,9 @@ typedef struct les_dd_ops {
    * on success. */
   int (*allreduce)(void *ctx, double *values, int32_t n);
 } les_dd_ops;
-/* Device workspace of one sub-domain (its vectors with a one-node halo, the
- * face strips and the partial sums).  LES_ERR_INVALID_ARG unless px divides
+/* Device workspace of one sub-domain (its CG vectors with a one-node halo,
+ * their face strips, the partial sums, and the strips of the decomposed
+ * step's field halos: LES_DD_MAX_FIELDS fields, LES_DD_HALO deep).  LES_ERR_INVALID_ARG unless px divides
  * nx, py divides ny, nz >= 2 and the precision is 32 or 64. */
 int les_dd_workspace_bytes(const les_config *cfg, int32_t px, int32_t py, size_t *bytes);
 /* Sub-domain (rx, ry) of a px x py partition of *cfg's grid; the workspace
