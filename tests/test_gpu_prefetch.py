@@ -56,3 +56,30 @@ def test_prefetched_states_step_like_uploaded_ones(les_mod, shape):
             assert np.array_equal(sim.get(k), want[q][k]), (q, k)
     ref.close()
     sim.close()
+
+
+def test_prefetch_refuses_bad_arguments(les_mod):
+    """A misaligned staging buffer, a repeated field, a bad field id and no
+    fields are refused before anything is copied."""
+    import ctypes as C
+    case = inputs.tgv(32, nxyz=(64, 16, 12), precision=32, steps_tol=1e-6)
+    sim = les_mod.Simulation(case)
+    host = _host_state(case, 1)
+    copy = torch.cuda.Stream()
+    staging = torch.empty(len(NAMES) * case.n + 4, dtype=torch.float32, device="cuda")
+    ids = (C.c_int32 * 2)(les_mod.FIELDS["u"], les_mod.FIELDS["u"])
+    ptrs = (C.c_void_p * 2)(host["u"].data_ptr(), host["v"].data_ptr())
+    stream = C.c_void_p(copy.cuda_stream)
+    lib = sim.lib
+    misaligned = C.c_void_p(staging.data_ptr() + 4)
+    good = C.c_void_p(staging.data_ptr())
+    one = (C.c_int32 * 1)(les_mod.FIELDS["u"])
+    assert lib.les_prefetch_states(sim.h, 1, one, ptrs, misaligned, stream) == les_mod.LES_ERR_INVALID_ARG
+    assert lib.les_prefetch_states(sim.h, 2, ids, ptrs, good, stream) == les_mod.LES_ERR_INVALID_ARG
+    bad = (C.c_int32 * 1)(999)
+    assert lib.les_prefetch_states(sim.h, 1, bad, ptrs, good, stream) == les_mod.LES_ERR_INVALID_ARG
+    assert lib.les_prefetch_states(sim.h, 0, one, ptrs, good, stream) == les_mod.LES_ERR_INVALID_ARG
+    # nothing is pending: a step runs from the state set before
+    sim.set_state({k: v.numpy() for k, v in host.items()})
+    sim.step(1)
+    sim.close()
