@@ -59,7 +59,9 @@ def neighbours(px: int, py: int, rank: int) -> dict:
 class TorchExchange:
     """Halo exchange and all-reduce over a torch.distributed process group.
     ``exchange(send, recv)`` takes the four face strips of this rank and
-    fills the four halo strips (torch tensors on the group's device)."""
+    fills the four halo strips (torch tensors on the group's device).  With
+    the gloo backend, device strips travel through host copies (gloo moves
+    host memory); with NCCL they go device to device."""
 
     def __init__(self, px: int, py: int, rank: int, group=None):
         self.px, self.py, self.rank, self.group = px, py, rank, group
@@ -72,8 +74,10 @@ class TorchExchange:
         import torch.distributed as dist
         if stream is not None:
             stream.synchronize()
+        staged = dist.get_backend(self.group) == "gloo"
         ops = []
         local = []
+        back = []
         for face, side, halo in TRAVEL:
             if send[face] is None:              # this axis is not exchanged now
                 continue
@@ -82,11 +86,18 @@ class TorchExchange:
             if dst == self.rank and src == self.rank:
                 local.append((halo, face))
                 continue
-            ops.append(dist.P2POp(dist.isend, send[face], dst, self.group))
-            ops.append(dist.P2POp(dist.irecv, recv[halo], src, self.group))
+            s, r = send[face], recv[halo]
+            if staged and s.is_cuda:
+                s = s.cpu()
+                r = torch.empty(recv[halo].shape, dtype=recv[halo].dtype)
+                back.append((recv[halo], r))
+            ops.append(dist.P2POp(dist.isend, s, dst, self.group))
+            ops.append(dist.P2POp(dist.irecv, r, src, self.group))
         if ops:
             for w in dist.batch_isend_irecv(ops):
                 w.wait()
+        for dev, host in back:
+            dev.copy_(host)
         for halo, face in local:                # periodic with itself
             recv[halo].copy_(send[face])
         if stream is not None:
