@@ -71,7 +71,7 @@ struct FusedArgs {
   T* p0;
   T* p1;
   T* q;
-  double* partials;  // [4][gridDim.x]
+  double* partials;  // two slots of kSumSlot words per block
   FusedBar* bar;
   SolverCtl* ctl;
   double tol;
@@ -412,7 +412,7 @@ int poisson_solve_fused(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, 
   long long G = (long long)per_sm * nsm;
   G = std::min<long long>(G, fc.max_blocks);
   G = std::max<long long>(1, std::min<long long>(G, std::max<long long>(f.ntiles, nsm)));
-  G = std::min<long long>(G, 8LL * nsm);  // the partials hold 2 x 2 x 8 slots per SM
+  G = std::min<long long>(G, 8LL * nsm);  // the partials hold 2 x kSumSlot words of 8 blocks per SM
   f.expected = (unsigned)G + (unsigned)std::max(0, fc.missing);
   f.guard = a.guard;
   if ((e = cudaMemsetAsync(a.bar, 0, sizeof(FusedBar), a.st)) != cudaSuccess) {

@@ -492,7 +492,7 @@ int poisson_solve_roll(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T
   }
   long long G = (long long)std::max(1, per_sm) * nsm;
   G = std::min<long long>(G, fc.max_blocks);
-  G = std::min<long long>(G, 8LL * nsm);  // the partials hold 2 x 4 x 8 slots per SM
+  G = std::min<long long>(G, 8LL * nsm);  // the partials hold 2 x kSumSlot words of 8 blocks per SM
   // z-runs as long as possible (each run re-forms two planes of p and one of
   // q, r' below it), dealt to the G persistent blocks as in the column CG:
   // fewer columns than blocks, at most G units (one turn); more, whole

@@ -776,7 +776,7 @@ int solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, dou
   }
   long long G = (long long)per_sm * nsm;
   G = std::min<long long>(G, fc.max_blocks);
-  G = std::min<long long>(G, 8LL * nsm);  // the partials hold 2 x 4 x 8 slots per SM
+  G = std::min<long long>(G, 8LL * nsm);  // the partials hold 2 x kSumSlot words of 8 blocks per SM
   // z-runs as long as possible (each run re-forms two planes of p and r'
   // below it)
   const long long ncol = (long long)f.ntx * f.nty;

@@ -9,7 +9,9 @@
 // (deterministic for a fixed grid) and no block has to publish them.  Two
 // slots suffice: a block writes slot e mod 2 again only at sum e + 2, which
 // it can reach only after every block has arrived at sum e + 1, i.e. after
-// every block has finished reading the slot of sum e.
+// every block has finished reading the slot of sum e.  The slots have a
+// fixed size (kSumSlot values of every block) whatever the number of values
+// of a sum, so that consecutive sums of different sizes never share memory.
 //
 // Every wait is bounded in time: on expiry the fail flag is raised and the
 // call returns false in every thread of the block, leaving the device usable.
@@ -152,10 +154,18 @@ __device__ __forceinline__ void block_sum_bcast(double (&v)[NV]) {
 }
 
 // ---- the grid sum ---------------------------------------------------------------
+// Values per block in one slot of the partials array: the partials array
+// holds at least 2 x kSumSlot x gridDim.x 8-byte words.
+constexpr int kSumSlot = 8;
+template <typename A>
+__device__ __forceinline__ A* sum_slot(void* partials, unsigned epoch) {
+  return reinterpret_cast<A*>(partials) + (size_t)(epoch & 1u) * kSumSlot * gridDim.x;
+}
+
 // Per-block state of the grid sums of one launch (held in registers).
 struct GridSync {
   FusedBar* bar;
-  void* partials;     // >= 2 x NV x gridDim.x 8-byte slots
+  void* partials;     // >= 2 x kSumSlot x gridDim.x 8-byte words
   long long spin;     // wait limit in clock cycles
   unsigned expected;  // arrivals per sum: gridDim.x (+ the test hook's missing ones)
   unsigned epoch;     // sums completed by this block
@@ -191,7 +201,8 @@ __device__ bool grid_sum(F2 (&v)[NV], GridSync& gs, double (&tot)[NV]) {
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
   const unsigned G = gridDim.x;
-  float2* slot = reinterpret_cast<float2*>(gs.partials) + (size_t)(gs.epoch & 1u) * NV * G;
+  static_assert(NV <= kSumSlot, "too many values for one slot");
+  float2* slot = sum_slot<float2>(gs.partials, gs.epoch);
   block_sum_bcast<NV>(v);
   if (tid == 0)
 #pragma unroll
@@ -220,7 +231,8 @@ __device__ bool grid_sum(double (&v)[NV], GridSync& gs) {
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
   const unsigned G = gridDim.x;
-  double* slot = reinterpret_cast<double*>(gs.partials) + (size_t)(gs.epoch & 1u) * NV * G;
+  static_assert(NV <= kSumSlot, "too many values for one slot");
+  double* slot = sum_slot<double>(gs.partials, gs.epoch);
   block_sum_bcast<NV>(v);
   if (tid == 0)
 #pragma unroll
@@ -298,7 +310,8 @@ __device__ bool grid_sum_t0_acc(A (&v)[NV], GridSync& gs, A (&tot)[NV], W&& work
   const int lane = tid & 31, warp = tid >> 5;
   const int nw = (blockDim.x * blockDim.y + 31) >> 5;
   const unsigned G = gridDim.x;
-  A* slot = reinterpret_cast<A*>(gs.partials) + (size_t)(gs.epoch & 1u) * NV * G;
+  static_assert(NV <= kSumSlot, "too many values for one slot");
+  A* slot = sum_slot<A>(gs.partials, gs.epoch);
 #pragma unroll
   for (int q = 0; q < NV; ++q) v[q] = acc_warp(v[q]);
   if (lane == 0)
