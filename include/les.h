@@ -451,10 +451,12 @@ int les_ensemble_step(les_handle *const *hs, int32_t m, int32_t nsteps, les_step
  * / 64 doubles), the scalar and momentum predictors over two-node lanes (nx
  * a multiple of 64), ny a multiple of 8 -- and rolling z-marches elsewhere;
  * 1 rolling z-marches through shared-memory plane rings everywhere.  With
- * cg_resident = 0 the standard CG solve first tries a decomposition of the
- * grid into one brick per thread block (x extent 32, 64 or 128 dividing nx,
- * y and z extents dividing ny and nz, at most one block per SM, x, r and p
- * of a brick within the per-block shared memory); the blocks then exchange
+ * cg_resident = 0 or 2 the standard CG solve first tries a decomposition of
+ * the grid into one brick per thread block (x extent 32, 64 or 128 dividing
+ * nx, y and z extents dividing ny and nz, at most one block per SM, x, r and
+ * p of a brick within the per-block shared memory; with cg_resident = 0 and
+ * an FP32 grid 128 nodes wide, bricks of the whole x extent with at most six
+ * planes per thread and p, r and q in registers); the blocks then exchange
  * only brick faces through global memory, and cg_tile_rows and
  * cg_tile_planes do not apply.  A zero field in a set call keeps the
  * current value (except fault_missing_arrivals, stencil_path, cg_variant and
@@ -486,9 +488,13 @@ typedef struct les_tuning {
                                       and ny of cg_tile_rows, else the
                                       per-phase launches run               */
   int32_t  cg_resident;            /* 0 (default): standard CG keeps its
-                                      vectors in shared memory when the grid
-                                      fits there; 1: always streams them
-                                      through global memory                */
+                                      vectors on chip when the grid fits
+                                      there (FP32 grids with nx = 128: p, r
+                                      and q in registers, x and a copy of p
+                                      in shared memory; else all in shared
+                                      memory); 1: always streams them
+                                      through global memory; 2: on chip with
+                                      every vector in shared memory        */
 } les_tuning;
 int les_get_tuning(les_handle *h, les_tuning *out);
 int les_set_tuning(les_handle *h, const les_tuning *in);

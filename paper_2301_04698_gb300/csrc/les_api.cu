@@ -566,7 +566,7 @@ namespace les {
 const char* const kKernelNames[KI_COUNT] = {
     "thermo", "radiation", "scalar", "momentum", "rhs", "correct", "diag",
     "cfl", "apply", "sum", "cg_init", "cg_matvec", "cg_update", "jacobi", "finish", "ctl", "cg_fused",
-    "unet_conv", "unet_wgrad", "unet_adam", "cg_resident", "cg_roll", "cg_wave"};
+    "unet_conv", "unet_wgrad", "unet_adam", "cg_resident", "cg_roll", "cg_wave", "cg_regs"};
 
 template <typename T>
 Grid<T> make_grid(const les_config& c, int zc) {
@@ -1000,7 +1000,7 @@ int les_set_tuning(les_handle* h, const les_tuning* in) {
   if (in->cg_variant < 0 || in->cg_variant > 4 || in->cg_variant == 1)
     return h->fail(LES_ERR_INVALID_ARG, "cg_variant must be 0, 2, 3 or 4");
   h->fused.variant = in->cg_variant;
-  if (in->cg_resident != 0 && in->cg_resident != 1) return h->fail(LES_ERR_INVALID_ARG, "cg_resident must be 0 or 1");
+  if (in->cg_resident < 0 || in->cg_resident > 2) return h->fail(LES_ERR_INVALID_ARG, "cg_resident must be 0, 1 or 2");
   h->fused.resident = in->cg_resident;
   return LES_OK;
 }

@@ -44,7 +44,7 @@ struct ResArgs {
   T* rg;             // published faces of the first residual
   T* qg0;            // published faces of q = L_c p, even iterations
   T* qg1;            // ... odd iterations
-  double* partials;  // [2][4][gridDim.x]
+  double* partials;  // two slots of kSumSlot words per block
   FusedBar* bar;
   SolverCtl* ctl;
   double tol;
@@ -598,6 +598,13 @@ int poisson_solve_resident(const SolverArgs<T>& a, const FusedCfg& fc, const T* 
   *used = false;
   if (!(a.op == LES_OP_COMPACT && a.solver == LES_SOLVER_CG && a.g.nz >= 2 && a.bar && a.r && a.p0 && a.p1))
     return LES_OK;
+  // FP32 grids 128 nodes wide: p, r and q in registers (les_cg_regs.cu)
+  if constexpr (sizeof(T) == 4) {
+    if (fc.resident == 0) {
+      const int rc = poisson_solve_regs(a, fc, b, x, tol, maxit, iters, rel, err, used);
+      if (*used || rc != LES_OK) return rc;
+    }
+  }
   int dev = 0, nsm = 0, smem_optin = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess ||

@@ -105,7 +105,9 @@ struct FusedCfg {
   int variant = 0;                      // 0 standard iterates (resident, else FP32 columns, else
                                         // two-phase streaming when tile-aligned, else one-pass),
                                         // 2 two-phase streaming, 3 one-pass one-reduction, 4 columns
-  int resident = 0;                     // 0 shared-memory-resident CG when the grid fits, 1 never
+  int resident = 0;                     // 0 on-chip CG when the grid fits (p, r, q in registers where
+                                        // the grid allows), 1 never, 2 on chip with every vector in
+                                        // shared memory
 };
 
 struct LaunchCfg {
@@ -116,7 +118,7 @@ struct LaunchCfg {
 enum KernelId : int {
   KI_THERMO = 0, KI_RADIATION, KI_SCALAR, KI_MOMENTUM, KI_RHS, KI_CORRECT,
   KI_DIAG, KI_CFL, KI_APPLY, KI_SUM, KI_CG_INIT, KI_CG_MATVEC, KI_CG_UPDATE, KI_JACOBI, KI_FINISH,
-  KI_CTL, KI_CG_FUSED, KI_UNET_CONV, KI_UNET_WGRAD, KI_UNET_ADAM, KI_CG_RESIDENT, KI_CG_ROLL, KI_CG_WAVE, KI_COUNT
+  KI_CTL, KI_CG_FUSED, KI_UNET_CONV, KI_UNET_WGRAD, KI_UNET_ADAM, KI_CG_RESIDENT, KI_CG_ROLL, KI_CG_WAVE, KI_CG_REGS, KI_COUNT
 };
 extern const char* const kKernelNames[KI_COUNT];
 
@@ -316,6 +318,10 @@ int poisson_solve_wave(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T
 template <typename T>
 int poisson_solve_resident(const SolverArgs<T>& a, const FusedCfg& fc, const T* b, T* x, double tol, int maxit,
                            int* iters, double* rel, std::string* err, bool* used);
+// The same iterates with p, r and q in registers (les_cg_regs.cu): FP32
+// grids with nx = 128; *used as above.
+int poisson_solve_regs(const SolverArgs<float>& a, const FusedCfg& fc, const float* b, float* x, double tol,
+                       int maxit, int* iters, double* rel, std::string* err, bool* used);
 
 }  // namespace les
 struct les_unet;

@@ -363,7 +363,7 @@ int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxi
   }
   const int var = a.fused ? a.fused->variant : -1;
   const bool tiled = a.fused && fused_cg_eligible(a.g, a.op, a.solver, a.fused->ty);
-  if (a.bar && cg_c && var == 0 && a.fused->resident == 0) {
+  if (a.bar && cg_c && var == 0 && a.fused->resident != 1) {
     bool used = false;
     const int rc = poisson_solve_resident<T>(a, *a.fused, b, x, tol, maxit, iters, rel, err, &used);
     if (used || rc != LES_OK) return rc;

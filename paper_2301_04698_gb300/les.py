@@ -587,6 +587,7 @@ AUTOTUNE_CANDIDATES = (
     {"stencil_path": 0},
     {"stencil_path": 1},
     {"stencil_path": 0, "cg_max_blocks": 64},
+    {"stencil_path": 0, "cg_resident": 2},
     {"stencil_path": 0, "cg_resident": 1, "cg_variant": 2, "cg_tile_rows": 4, "cg_tile_planes": 4},
     {"stencil_path": 0, "cg_resident": 1, "cg_variant": 2, "cg_tile_rows": 2, "cg_tile_planes": 8},
     {"stencil_path": 0, "cg_resident": 1, "cg_variant": 3},

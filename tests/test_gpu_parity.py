@@ -396,7 +396,7 @@ def test_ragged_and_minimum_grids(les_mod, shape):
 # persistent single-launch CG (fast path for nx a multiple of the tile width)
 
 
-def _fused_launches(sim, names=("cg_fused", "cg_resident", "cg_roll", "cg_wave")):
+def _fused_launches(sim, names=("cg_fused", "cg_resident", "cg_regs", "cg_roll", "cg_wave")):
     return sum(k["launches"] for k in sim.profile_read() if k["name"] in names)
 
 
@@ -427,8 +427,8 @@ def test_fused_cg_matches_oracle(les_mod, precision, walls, shape):
         x = torch.zeros_like(bt)
         rc, it, res = sim.poisson_solve(bt, x, tol, 20000)
         assert rc == 0 and res <= tol
-        kern = {2: "cg_fused", 3: "cg_roll"}.get(variant, "cg_resident")
-        assert _fused_launches(sim, (kern,)) == 1, (variant, stream)
+        kern = {2: ("cg_fused",), 3: ("cg_roll",)}.get(variant, ("cg_resident", "cg_regs"))
+        assert _fused_launches(sim, kern) == 1, (variant, stream)
         xn = x.cpu().double().numpy()
         # zero-mean gauge, to rounding of the field's magnitude
         assert abs(xn.mean()) < (1e-14 if precision == 64 else 1e-6) * np.abs(xn).max()
@@ -446,8 +446,9 @@ def test_fused_cg_matches_oracle(les_mod, precision, walls, shape):
         assert rel(xn, x1.cpu().double().numpy()) < (1e-9 if precision == 64 else 5e-4)
 
 
-@pytest.mark.parametrize("variant,stream,kern,ny", [(0, 0, "cg_resident", 8), (3, 1, "cg_roll", 8),
-                                                    (2, 1, "cg_fused", 8), (4, 1, "cg_wave", 16)])
+@pytest.mark.parametrize("variant,stream,kern,ny", [(0, 0, "cg_regs", 8), (0, 2, "cg_resident", 8),
+                                                    (3, 1, "cg_roll", 8), (2, 1, "cg_fused", 8),
+                                                    (4, 1, "cg_wave", 16)])
 def test_fused_cg_barrier_timeout_is_reported(les_mod, variant, stream, kern, ny):
     case = inputs.Case(name="fused", nx=128, ny=ny, nz=4, dx=1.0, dy=1.0, dz=1.0, precision=32,
                        init="zero", physics=())
@@ -476,7 +477,12 @@ def test_fused_cg_barrier_timeout_is_reported(les_mod, variant, stream, kern, ny
     (64, False, (32, 32, 32), 0),     # the learned-guess grid
     (64, True, (64, 7, 11), 0),       # odd brick extents in y and z
     (32, False, (32, 3, 2), 0),       # one-node bricks in y and z
-    (32, True, (32, 256, 4), 4)])     # more ghost rows than one batch of loads
+    (32, True, (32, 256, 4), 4),      # more ghost rows than one batch of loads
+    # p, r and q in registers (FP32, nx = 128):
+    (32, False, (128, 24, 13), 6),    # runs of 4 and 3 planes, bricks of 7 and 6 planes
+    (32, True, (128, 32, 23), 8),     # runs of 6 and 5 planes, bricks of 12 and 11 planes
+    (32, True, (128, 8, 12), 1),      # one block, two runs of six planes
+    (32, False, (128, 32, 23), 0)])   # one plane per thread and per brick
 def test_resident_cg_matches_oracle(les_mod, precision, walls, shape, max_blocks):
     """The shared-memory-resident CG against the FP64 oracle and against the
     one-reduction rolling CG, which follows the same iterates."""
@@ -500,7 +506,7 @@ def test_resident_cg_matches_oracle(les_mod, precision, walls, shape, max_blocks
         x = torch.from_numpy(0.1 * inputs.uniform(24, 0, case.n, -1, 1).reshape(case.shape)).to("cuda", dt)
         rc, it, res = sim.poisson_solve(bt, x, tol, 20000)
         assert rc == 0 and res <= tol
-        assert _fused_launches(sim, ("cg_resident",) if stream == 0 else ("cg_roll",)) == 1
+        assert _fused_launches(sim, ("cg_resident", "cg_regs") if stream == 0 else ("cg_roll",)) == 1
         xn = x.cpu().double().numpy()
         assert abs(xn.mean()) < (1e-14 if precision == 64 else 1e-6) * np.abs(xn).max()
         assert rel(xn, xr) < (1e-8 if precision == 64 else 5e-4), stream
@@ -516,6 +522,43 @@ def test_resident_cg_matches_oracle(les_mod, precision, walls, shape, max_blocks
     x = torch.ones_like(bt)
     rc, it, res = sim.poisson_solve(torch.zeros_like(bt), x, tol, 100)
     assert rc == 0 and it == 0 and float(x.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("walls,shape", [(True, (128, 128, 96)), (False, (128, 64, 48))])
+def test_register_cg_matches_shared_memory_cg(les_mod, walls, shape):
+    """The on-chip CG with p, r and q in registers and the one with every
+    vector in shared memory, on the capped boundary layer's 128 x 128 x 96
+    grid and a periodic one: both against the FP64 oracle's solution, the
+    same iteration count within 3, and a true residual |b - L_c x| (the
+    oracle's operator, FP64) below 5e-5 |b|.  The bound is FP32's: rounding x
+    alone (|x| ~ 700, ||L_c|| ~ 4/dx^2 + 4/dz^2) leaves ~2e-6 |b|, and the
+    recurrence residual that stops the solve drifts from the true one over
+    the ~900 iterations (1.3e-5 |b| measured for the register kernel)."""
+    from oracle import Oracle
+    nx, ny, nz = shape
+    case = inputs.Case(name="regs", nx=nx, ny=ny, nz=nz, dx=35.0, dy=35.0, dz=10.0, walls=walls,
+                       precision=32, init="zero", physics=())
+    ref = Oracle(case.replace(precision=64))
+    b = inputs.uniform(25, 0, case.n, -1, 1).reshape(case.shape) + 0.25
+    xr, st, itr, _ = ref.poisson(b, tol=1e-10, maxit=20000)
+    bm = b - b.mean()
+    sim = les_mod.Simulation(case)
+    bt = torch.from_numpy(b).to("cuda", torch.float32)
+    its, true_res = {}, {}
+    for mode, kern in ((0, "cg_regs"), (2, "cg_resident")):
+        sim.set_tuning(cg_resident=mode, cg_variant=0)
+        sim.profile_reset()
+        x = torch.zeros_like(bt)
+        rc, it, res = sim.poisson_solve(bt, x, 1e-6, 20000)
+        assert rc == 0 and res <= 1e-6
+        assert _fused_launches(sim, (kern,)) == 1, kern
+        xn = x.cpu().double().numpy()
+        assert rel(xn, xr) < 5e-4, kern
+        true_res[kern] = np.linalg.norm(bm - ref.apply_poisson(xn)) / np.linalg.norm(bm)
+        its[kern] = it
+    assert max(true_res.values()) < 5e-5, true_res
+    assert abs(its["cg_regs"] - its["cg_resident"]) <= 3, its
+    sim.close()
 
 
 @pytest.mark.parametrize("precision,walls,shape", [
