@@ -24,7 +24,7 @@
 // An iteration (one grid-wide sum, the recurrences of the shared-memory
 // solver in les_cg_resident.cu):
 //   matvec   q = L_c p; the q faces a neighbour reads are published;
-//            p.q, r.r, r.q and q.q
+//            p.q, r.q and q.q (r.r was formed with r, in the update)
 //   sum      each warp reduces its four values in FP32 (a transposing
 //            butterfly: six shuffles for all four); warp 0 combines the
 //            warps' values as compensated FP32 pairs, writes them into
@@ -34,8 +34,8 @@
 //            its arrivals and reads spread over as many L2 lines); then
 //            warps 0 .. 3 fold one value each from the block's copy, in
 //            block order, while the other warps copy the neighbours' q
-//            faces into shared memory asynchronously, and every thread
-//            forms alpha and beta = |r - alpha q|^2 / r.r from the totals
+//            faces into shared memory asynchronously; thread 0 forms
+//            alpha and beta = |r - alpha q|^2 / r.r from the totals
 //   update   r -= alpha q, p = r + beta p (registers and the shared copy of
 //            p); at the ghost nodes r -= alpha q_ghost and p = r + beta p;
 //            x += alpha p in warp 0, while the other warps keep p and add
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kRegMaxWarps * 32, 1) k_cg_regs(RegArgs f) {
   GridSync gs{f.bar, f.partials, f.spin_cycles, f.expected, 0u};
   // set-up results of thread 0, broadcast through shared memory
   __shared__ struct {
-    float mean;
+    float mean, ta, tb;
     int status;
   } sc;
   __shared__ float shv[4][kRegMaxWarps];
@@ -177,6 +177,9 @@ __global__ void __launch_bounds__(kRegMaxWarps * 32, 1) k_cg_regs(RegArgs f) {
   __shared__ int s_fail;
   double rr = 0.0, bb = 0.0, rel = 0.0;  // meaningful in thread 0
   int status = 0;  // 0 running, 1 converged, 2 maxit, 3 breakdown, 4 zero rhs, 5 timeout
+  // this thread's share of r.r for the next sum, formed where r is (the
+  // initial residual, then each update), in the order the sums expect
+  float rr_own = 0.f;
 
   // mean of b (b held in r)
   {
@@ -230,6 +233,7 @@ __global__ void __launch_bounds__(kRegMaxWarps * 32, 1) k_cg_regs(RegArgs f) {
         a2[1].add(bm.z * bm.z);
         a2[1].add(bm.w * bm.w);
       }
+    rr_own = a2[0].s;
     double s2[2];
     const bool ok = grid_dot_t0<2>(a2, gs, s2);
     if (tid == 0) {
@@ -292,10 +296,6 @@ __global__ void __launch_bounds__(kRegMaxWarps * 32, 1) k_cg_regs(RegArgs f) {
           d[0].add(p[j].y * q[j].y);
           d[0].add(p[j].z * q[j].z);
           d[0].add(p[j].w * q[j].w);
-          d[1].add(r[j].x * r[j].x);
-          d[1].add(r[j].y * r[j].y);
-          d[1].add(r[j].z * r[j].z);
-          d[1].add(r[j].w * r[j].w);
           d[2].add(r[j].x * q[j].x);
           d[2].add(r[j].y * q[j].y);
           d[2].add(r[j].z * q[j].z);
@@ -305,6 +305,7 @@ __global__ void __launch_bounds__(kRegMaxWarps * 32, 1) k_cg_regs(RegArgs f) {
           d[3].add(q[j].z * q[j].z);
           d[3].add(q[j].w * q[j].w);
         }
+      d[1].s = rr_own;
       // the grid sum.  Each warp's four values in FP32 by a transposing
       // butterfly: after it lanes 8k .. 8k + 7 hold the warp's value k.
       {
@@ -414,6 +415,31 @@ __global__ void __launch_bounds__(kRegMaxWarps * 32, 1) k_cg_regs(RegArgs f) {
           t = warp_sum_f2(t);
           if (lane == 0) tot[k] = t;
         }
+        // the folds are complete: thread 0 forms the status, alpha and beta
+        asm volatile("bar.sync 3, %0;" ::"r"(32 * min(nwarp, 4)) : "memory");
+        if (tid == 0) {
+          int st = 0;
+          if (s_fail) {
+            st = 5;
+          } else {
+            const F2 t1 = tot[1];
+            rr_last = t1;
+            if (acc_le(t1, rr_stop)) st = 1;
+            else if (iter >= f.maxit) st = 2;
+            else {
+              const float pq = tot[0].hi, r2 = t1.hi, rq = tot[2].hi, q2 = tot[3].hi;
+              if (!(pq != 0.f) || !isfinite(pq) || !isfinite(r2)) {
+                st = 3;
+              } else {
+                const float alpha = r2 / pq;
+                const float rn = fmaf(alpha * alpha, q2, fmaf(-2.f * alpha, rq, r2));  // |r - alpha q|^2
+                sc.ta = alpha;
+                sc.tb = rn / r2;
+              }
+            }
+          }
+          sc.status = st;
+        }
       }
       if (!l0) {
         for (int row = warp; row < nr; row += nwarp) {
@@ -426,26 +452,11 @@ __global__ void __launch_bounds__(kRegMaxWarps * 32, 1) k_cg_regs(RegArgs f) {
       cp_wait<0>();
       it_sum += 1u;
       __syncthreads();
-      // every thread forms the status, alpha and beta from the same totals
-      if (s_fail) {
-        status = 5;
-      } else {
-        const F2 t1 = tot[1];
-        if (tid == 0) rr_last = t1;
-        if (acc_le(t1, rr_stop)) status = 1;
-        else if (iter >= f.maxit) status = 2;
-        else {
-          const float pq = tot[0].hi, r2 = t1.hi, rq = tot[2].hi, q2 = tot[3].hi;
-          if (!(pq != 0.f) || !isfinite(pq) || !isfinite(r2)) {
-            status = 3;
-          } else {
-            ta = r2 / pq;
-            const float rn = fmaf(ta * ta, q2, fmaf(-2.f * ta, rq, r2));  // |r - alpha q|^2
-            tb = rn / r2;
-          }
-        }
-      }
+      status = sc.status;
       if (status) break;
+      ta = sc.ta;
+      tb = sc.tb;
+      float rr_new = 0.f;
 #pragma unroll
       for (int j = 0; j < ZP; ++j)
         if (j < nzp) {
@@ -463,6 +474,10 @@ __global__ void __launch_bounds__(kRegMaxWarps * 32, 1) k_cg_regs(RegArgs f) {
           r[j].y -= ta * q[j].y;
           r[j].z -= ta * q[j].z;
           r[j].w -= ta * q[j].w;
+          rr_new += r[j].x * r[j].x;
+          rr_new += r[j].y * r[j].y;
+          rr_new += r[j].z * r[j].z;
+          rr_new += r[j].w * r[j].w;
           p[j].x = r[j].x + tb * p[j].x;
           p[j].y = r[j].y + tb * p[j].y;
           p[j].z = r[j].z + tb * p[j].z;
@@ -487,6 +502,7 @@ __global__ void __launch_bounds__(kRegMaxWarps * 32, 1) k_cg_regs(RegArgs f) {
         pv.w = rv.w + tb * pv.w;
         sts4(pg, pv);
       }
+      rr_own = rr_new;
       iter += 1;
       __syncthreads();
     }
