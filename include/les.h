@@ -286,11 +286,10 @@ int les_diagnostics(les_handle *h, double *out);
  * precision 32 (four work vectors of 16 MiB in total); larger grids are
  * rejected with LES_ERR_INVALID_ARG and a message in err.  No cudaMalloc,
  * cudaFree or allocating library routine is called.
- * The first call on a device looks up the array's device address with that
- * device current (cudaGetSymbolAddress) and caches it.  The cached address
- * belongs to the device's
- * current context: after cudaDeviceReset() on that device, further calls in
- * the same process are invalid.  Every call on a device shares the one array,
+ * Every call looks up the array's address in the current device's context
+ * (cudaGetSymbolAddress, no allocation), so a context torn down and created
+ * again in the same process gets its own copy.  Every call on a device
+ * shares the one array,
  * which keeps the previous call's contents (the call clears the control
  * block it needs zeroed): calls that overlap on the GPU race, so issue them
  * on one stream or serialise them.

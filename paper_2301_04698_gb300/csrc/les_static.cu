@@ -16,7 +16,6 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "les_internal.h"
@@ -33,33 +32,17 @@ static_assert(sizeof(les::SolverCtl) <= kCtlBytes, "control block does not fit")
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// device address of g_scratch per device, looked up once with that device current
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
+// device address of g_scratch in the current device's context, looked up on
+// every call (no allocation): a cached address would go stale if the
+// context were torn down and created again in the same process
 int scratch_address(void** out, std::string* err) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    *err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess || !p) {
+    *err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
     return LES_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) {
-    *err = "device ordinal beyond the static table";
-    return LES_ERR_INVALID_ARG;
-  }
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || !p) {
-      *err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-      return LES_ERR_CUDA;
-    }
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  *out = p;
   return LES_OK;
 }
 
