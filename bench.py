@@ -401,8 +401,9 @@ def poisson_only(args):
 
 # ---------------------------------------------------------------------------
 def bench_ensemble(args, rank, world, local):
-    """The uneven ensemble: every member tuned by the autotuner, then all
-    stepped together through les_ensemble_step; whole-job cell-steps/s over
+    """The uneven ensemble: every member tuned by the autotuner, the
+    ensemble's mode (members stepped together through les_ensemble_step, or
+    one after another) chosen by timing both; whole-job cell-steps/s over
     wall time bracketed by device synchronisation (the members run on their
     own streams)."""
     import torch
@@ -420,9 +421,15 @@ def bench_ensemble(args, rank, world, local):
         if args.ensemble_share > 1:   # the share's cap wins over a tuned one
             nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
             m.set_tuning(cg_max_blocks=max(1, nsm // args.ensemble_share))
+    # stepped together or one member after another, whichever is faster
+    mode = None if args.no_autotune else ens.tune()
     for _ in range(args.warmup):
         ens.step(1, allow_not_converged=True)
     torch.cuda.synchronize()
+    # the members' states at the start of the timed steps, so that the steps
+    # one member after another below start from the same states
+    fields = ("u", "v", "w", "p", "theta_l", "q_t")
+    snaps = [({k: m.view(k).clone() for k in fields}, m.dt) for m in ens.members]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     clocks = Clocks(local)
     launches0 = sum(m.launch_count() for m in ens.members)
@@ -443,7 +450,15 @@ def bench_ensemble(args, rank, world, local):
     clk = clocks.stop()
     total_s = allmax(world, total_s)
     launches = sum(m.launch_count() for m in ens.members) - launches0
-    # the same steps member after member, for the gain of stepping them together
+    # the same steps member after member from the same states, for the gain of
+    # stepping them together
+    torch.cuda.synchronize()
+    for m, (snap, dt) in zip(ens.members, snaps):
+        for k in fields:
+            m.view(k).copy_(snap[k])
+        if dt:
+            m.dt = dt
+    torch.cuda.synchronize()
     seq_s = 0.0
     for s in range(args.steps):
         flush.zero_()
@@ -463,10 +478,13 @@ def bench_ensemble(args, rank, world, local):
                        "cells": ens.cells, "K": cases[0].K, "tol": cases[0].tol,
                        "timing": "wall clock between device synchronisations (members on their own streams)",
                        "l2": "flushed (256 MiB write) before every timed step", "autotuned": tuned,
+                       "mode": "together" if ens.together else "one after another",
                        "share": args.ensemble_share},
             "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk,
             "poisson": {"iters_per_step": iters / args.steps},
             "one_after_another_ms_per_step": 1e3 * seq_s / args.steps,
+            "ensemble_mode": ("together" if ens.together else "one after another"),
+            "mode_choice": mode,
         }
         print(json.dumps(line), flush=True)
     ens.close()

@@ -542,18 +542,22 @@ def attach_model(sim: "Simulation", model) -> None:
 
 class Ensemble:
     """Independent members (each its own Simulation and stream) stepped
-    together through les_ensemble_step."""
+    together through les_ensemble_step, or one member after another."""
 
-    def __init__(self, cases, device=None, share: int = 1):
+    def __init__(self, cases, device=None, share: int = 1, together: bool = True):
         """share > 1 caps every member's persistent CG solve at 1/share of the
         SMs (les_tuning.cg_max_blocks), so that up to `share` members solve
-        at once; 1 leaves the solves uncapped (one at a time)."""
+        at once; 1 leaves the solves uncapped (one at a time).  together:
+        step the members concurrently (les_ensemble_step: a host thread per
+        member, the members' kernels overlapping); False steps them one after
+        another (tune() chooses by timing both)."""
         import torch
         self.torch = torch
         self.members = [Simulation(c, device=device, stream=torch.cuda.Stream(device=device)) for c in cases]
         self.lib = self.members[0].lib
         self.cells = sum(m.n for m in self.members)
         self.share = share
+        self.together = together
         if share > 1:
             nsm = torch.cuda.get_device_properties(device if device is not None else
                                                    torch.cuda.current_device()).multi_processor_count
@@ -565,6 +569,8 @@ class Ensemble:
             m.set_state(st)
 
     def step(self, nsteps: int = 1, allow_not_converged: bool = False) -> list:
+        if not self.together:
+            return [x.step(nsteps, allow_not_converged=allow_not_converged) for x in self.members]
         m = len(self.members)
         hs = (C.c_void_p * m)(*[x.h.value for x in self.members])
         stats = (LesStepStats * m)()
@@ -575,6 +581,44 @@ class Ensemble:
             h = self.members[failed.value].h if failed.value >= 0 else None
             _check(self.lib, h, rc, f"les_ensemble_step (member {failed.value})", allow)
         return [st.as_dict() for st in stats]
+
+    def tune(self, steps: int = 2) -> dict:
+        """Time `steps` ensemble steps stepped together and one member after
+        another (after one untimed step each, L2 not flushed), from the same
+        member states, keep the faster mode and put the states back.  On-chip
+        solves are bound by the latency of their grid sums through L2, which
+        the other members' streaming kernels raise when they run beside them;
+        which mode wins depends on the members.  Returns {"together": chosen
+        mode, "ms_per_step": {"together": ms, "one_after_another": ms}}."""
+        import time
+        torch = self.torch
+        names = ("u", "v", "w", "p", "theta_l", "q_t")
+        torch.cuda.synchronize()
+        snaps = [{k: x.view(k).clone() for k in names} for x in self.members]
+        dts = [x.dt for x in self.members]
+
+        def restore():
+            torch.cuda.synchronize()
+            for x, snap, dt in zip(self.members, snaps, dts):
+                for k in names:
+                    x.view(k).copy_(snap[k])
+                if dt:
+                    x.dt = dt
+            torch.cuda.synchronize()
+
+        ms = {}
+        for mode in (True, False):
+            self.together = mode
+            restore()
+            self.step(1, allow_not_converged=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            self.step(steps, allow_not_converged=True)
+            torch.cuda.synchronize()
+            ms["together" if mode else "one_after_another"] = 1e3 * (time.perf_counter() - t0) / steps
+        self.together = ms["together"] <= ms["one_after_another"]
+        restore()
+        return {"together": self.together, "ms_per_step": ms}
 
     def close(self) -> None:
         for x in self.members:

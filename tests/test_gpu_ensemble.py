@@ -44,6 +44,37 @@ def test_ensemble_matches_solo_runs(les_mod):
     ens.close()
 
 
+def test_ensemble_tune_restores_states(les_mod):
+    """tune() times the members stepped together and one after another from
+    the same states and puts the states back: stepping in the mode it chose,
+    and in the other mode from a fresh ensemble, ends bit-identical to each
+    member run alone."""
+    cases = _members()
+    ens = les_mod.Ensemble(cases)
+    ens.set_states([inputs.initial_state(c) for c in cases])
+    res = ens.tune(steps=1)
+    assert set(res["ms_per_step"]) == {"together", "one_after_another"}
+    assert res["together"] == ens.together
+    chosen = ens.together
+    other = les_mod.Ensemble(cases, together=not chosen)
+    other.set_states([inputs.initial_state(c) for c in cases])
+    for e in (ens, other):
+        stats = e.step(2)
+        assert all(st["not_converged"] == 0 for st in stats)
+    torch.cuda.synchronize()
+    for i, c in enumerate(cases):
+        solo = les_mod.Simulation(c)
+        solo.set_state(inputs.initial_state(c))
+        solo.step(2)
+        for f in ("u", "v", "w", "p", "theta_l", "q_t"):
+            ref = solo.get(f)
+            assert np.array_equal(ens.members[i].get(f), ref), (c.name, f, chosen)
+            assert np.array_equal(other.members[i].get(f), ref), (c.name, f, not chosen)
+        solo.close()
+    ens.close()
+    other.close()
+
+
 @pytest.mark.parametrize("share", [2, 4])
 def test_ensemble_shared_sms_matches_solo_runs(les_mod, share):
     """Members capped at 1/share of the SMs solve concurrently; each member
