@@ -1081,6 +1081,20 @@ bool pcol_eligible(const Grid<T>& g) {
   return g.nx % kTW<T> == 0 && g.ny % PR == 0 && g.nz >= 2;
 }
 
+// runs of z-planes per column.  With fewer columns than half a wave of
+// resident blocks (kMinBlocks per SM), as many runs as one wave holds: a
+// partial second wave would leave most SMs idle for a whole run (on a
+// 128 x 128 grid, 9 runs of 11 planes ran both predictors 1.2x faster than
+// 16 runs of 6).  With more, at least two waves, which keeps the last,
+// partial wave short (512 x 512: two runs per column 5 % faster than one).
+template <typename T>
+long long pcol_runs(int nz, long long ncol, int nsm) {
+  const long long slots = (long long)kMinBlocks<T> * std::max(1, nsm);
+  const long long c = std::max<long long>(1, ncol);
+  const long long nw = 2 * c < slots ? slots / c : (2 * slots + c - 1) / c;
+  return std::max<long long>(1, std::min<long long>((long long)nz, nw));
+}
+
 template <typename T>
 cudaError_t launch_scalar_col(const StageArgs<T>& a, int nsm, const T* u, const T* v, const T* w, const T* b,
                               const T* thk, const T* qtk, const T* thh, const T* qth, const T* srad, T* th_out,
@@ -1090,11 +1104,8 @@ cudaError_t launch_scalar_col(const StageArgs<T>& a, int nsm, const T* u, const 
   r.ph = a.ph;
   r.ntx = a.g.nx / kTW<T>;
   r.nty = a.g.ny / PR;
-  // z runs long enough to amortise the four-plane prologue, at least two
-  // waves of resident blocks
   const long long ncol = (long long)r.ntx * r.nty;
-  const long long want = 2LL * kMinBlocks<T> * nsm;
-  const long long nw = std::max<long long>(1, std::min<long long>((long long)a.g.nz, (want + ncol - 1) / ncol));
+  const long long nw = pcol_runs<T>(a.g.nz, ncol, nsm);
   r.zrun = (int)((a.g.nz + nw - 1) / nw);
   r.nchunk = (a.g.nz + r.zrun - 1) / r.zrun;
   r.u = u, r.v = v, r.w = w, r.b = b;
@@ -1133,8 +1144,7 @@ cudaError_t launch_momentum_col(const StageArgs<T>& a, int nsm, const T* uk, con
   r.ntx = a.g.nx / kTW<T>;
   r.nty = a.g.ny / PR;
   const long long ncol = (long long)r.ntx * r.nty;
-  const long long want = 2LL * kMinBlocks<T> * nsm;
-  const long long nw = std::max<long long>(1, std::min<long long>((long long)a.g.nz, (want + ncol - 1) / ncol));
+  const long long nw = pcol_runs<T>(a.g.nz, ncol, nsm);
   r.zrun = (int)((a.g.nz + nw - 1) / nw);
   r.nchunk = (a.g.nz + r.zrun - 1) / r.zrun;
   r.uk = uk, r.vk = vk, r.wk = wk, r.un = un, r.vn = vn, r.wn = wn, r.p = p, r.b = b;
