@@ -110,7 +110,8 @@ def parse():
                          "--workload tgv_large (profiling a smaller tiling of the same box)")
     ap.add_argument("--variant", type=int, default=0, help="--poisson-only: les_tuning.cg_variant")
     ap.add_argument("--resident", type=int, default=1,
-                    help="--poisson-only: les_tuning.cg_resident (0: on chip when the grid fits)")
+                    help="--poisson-only: les_tuning.cg_resident (0: on chip when the grid fits, 1: streams, "
+                         "2: on chip with every vector in shared memory)")
     ap.add_argument("--iters", type=int, default=20, help="--poisson-only: CG iterations (tolerance unreachable)")
     ap.add_argument("--repeat", type=int, default=2, help="--poisson-only: solves")
     ap.add_argument("--fp64", action="store_true", help="--poisson-only: FP64 fields")

@@ -345,7 +345,9 @@ class SmHold {
 template <typename T>
 int poisson_solve(const SolverArgs<T>& a, const T* b, T* x, double tol, int maxit, int* iters, double* rel,
                   std::string* err) {
-  // persistent CG: in shared memory when the grid fits there; else the
+  // persistent CG: on chip when the grid fits there (p, r and q in
+  // registers on FP32 grids 128 nodes wide, else every vector in shared
+  // memory); else the
   // one-pass kernel with 64 x 16 columns (variant 4, and variant 0 for FP32
   // grids of whole columns), the two-phase streaming kernel on tile-aligned
   // grids (variant 0 or 2) or the one-pass kernel (variant 0 on other grids,
