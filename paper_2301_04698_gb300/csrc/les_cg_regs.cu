@@ -53,6 +53,7 @@ constexpr int kRegNx = 128;       // grid width: 32 lanes x 4 nodes
 constexpr int kRegMaxWarps = 16;  // 512 threads of at most 128 registers
 constexpr int kSpread = 8;        // arrival counters and copies of the partials per sum
 constexpr int kLineWords = 32;    // counters 128 bytes apart
+static_assert(kSpread * 4 == 32, "one lane of warp 0 per (copy, value) of the partials");
 
 struct RegArgs {
   int ny, nz, walls;
