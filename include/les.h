@@ -443,7 +443,8 @@ int les_ensemble_step(les_handle *const *hs, int32_t m, int32_t nsteps, les_step
  * after barrier_timeout_ms; the solve then returns LES_ERR_TIMEOUT and the
  * device stays usable.  fault_missing_arrivals is a failure-detection test
  * hook: the barrier then waits for that many blocks that never arrive, so
- * every wait runs out; it must be 0 otherwise.  stencil_path selects the
+ * every wait runs out (in the register CG, every wait of its iterations; its
+ * set-up sums wait for the launched blocks only); it must be 0 otherwise.  stencil_path selects the
  * stencil kernels (same results to rounding; both compute nu_t in place):
  * 0 (default) column marches where the grid allows them -- the correction
  * and the Poisson right side over 16-byte lanes (nx a multiple of 128 floats

@@ -689,6 +689,8 @@ def test_wave_cg_alignment_and_variant_range(les_mod):
     assert rel(out[0][1], out[1][1]) < 5e-4
     with pytest.raises(les_mod.LesError):
         sim.set_tuning(cg_variant=5)
+    with pytest.raises(les_mod.LesError):
+        sim.set_tuning(cg_resident=3)
     sim.close()
 
 
