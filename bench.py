@@ -102,6 +102,8 @@ def parse():
     ap.add_argument("--aux-steps", type=int, default=-1,
                     help="steps of the stage-breakdown, profiled and end-to-end legs (default: --steps, at most 3 / "
                          "3 / 5 on grids above 100 M cells)")
+    ap.add_argument("--fp32-peak", action="store_true",
+                    help="measure the device's FP32 FMA rate (the ALU bound of the issue-bound kernels)")
     # single Poisson solves (profiling a CG kernel)
     ap.add_argument("--poisson-only", action="store_true",
                     help="time single Poisson solves of a seeded right side instead of steps")
@@ -364,6 +366,31 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def fp32_peak(args):
+    """The FP32 FMA rate of the device (les_measure_fp32_fma), three times,
+    with the issue rate it implies: one warp instruction retires 32 FMAs."""
+    import torch
+
+    from paper_2301_04698_gb300 import build as B
+    from paper_2301_04698_gb300 import les
+    B.build()
+    les.load_library()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    nsm = props.multi_processor_count
+    clk = (json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz")
+           if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None) or 2070.0
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.mark(0)
+    runs = [les.measure_fp32_fma(10000) for _ in range(3)]
+    clocks.mark(1)
+    best = max(r["tflops"] for r in runs)
+    print(json.dumps({"fp32_fma_tflops": best, "runs": runs, "sms": nsm, "sm_max_mhz": clk,
+                      "fma_per_sm_per_clk_at_max": best * 1e12 / 2 / nsm / (clk * 1e6),
+                      "warp_instr_per_sm_per_clk_at_max": best * 1e12 / 2 / 32 / nsm / (clk * 1e6),
+                      "clocks": clocks.stop()}), flush=True)
+    return 0
+
+
 def poisson_only(args):
     """Single Poisson solves of a seeded uniform right side through the public
     API (Sec. 2.4: L_c psi = b, CG), one JSON line per solve: iterations, the
@@ -578,6 +605,8 @@ def main():
     args = parse()
     if args.poisson_only:
         return poisson_only(args)
+    if args.fp32_peak:
+        return fp32_peak(args)
     if args.oracle_one_thread:
         case = workload(args.workload, 1)
         sample, desc = oracle_sample(case, args, side=args.oracle_one_thread)

@@ -21,7 +21,7 @@ def lib():
 def _declared_functions():
     src = open(os.path.join(ROOT, "include", "les.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"\b(les_[a-z_]+)\s*\(", src)
+    names = re.findall(r"\b(les_[a-z0-9_]+)\s*\(", src)
     return sorted(set(names))
 
 
