@@ -569,7 +569,7 @@ const char *les_unet_last_error(const les_unet *u);
 /* Attach a model to a solver handle for LES_WARM_LEARNED (NULL detaches).
  * The model's grid must equal the handle's (nx = ny = nz = n); the handle
  * borrows the model until detached or destroyed.  The plain solver is the
- * fallback and the judge: if the model fails, or its guess leaves a larger
+ * fallback and the arbiter: if the model fails, or its guess leaves a larger
  * residual than a zero guess (||b - A psi_0|| > ||b||), the solve starts
  * from zero; every solve still iterates to the same relative residual. */
 int les_set_warm_model(les_handle *h, les_unet *u);

@@ -11,7 +11,7 @@
 //   z_{k+1} = M(r_{k+1}),  beta_k = z_{k+1}.(r_{k+1} - r_k) / r_k.z_k,
 //   p_{k+1} = z_{k+1} + beta_k p_k.
 // L_c is negative semi-definite, so a preconditioner close to L_c^-1 gives
-// r.M(r) < 0.  The plain iteration is the fallback and the judge: where
+// r.M(r) < 0.  The plain iteration is the fallback and the arbiter: where
 // r.M(r) is not negative (an untrained network answers 0) z = -r is used,
 // which with every z so chosen gives the plain CG iterates; every solve stops
 // at the same relative residual ||r|| <= tol ||b|| as the plain CG.

@@ -248,7 +248,7 @@ def test_learned_preconditioner_flexible_cg(les_mod):
     An untrained network answers 0, so every iteration takes the fallback
     z = -r: the solve is then the plain CG -- the same iteration count within
     two and the same solution.  With a network trained on solver pairs every
-    solve still reaches the tolerance (the plain iteration is the judge);
+    solve still reaches the tolerance (the plain iteration is the arbiter);
     its iterations and time are reported next to the plain solve's."""
     import time
 
