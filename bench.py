@@ -102,8 +102,8 @@ def parse():
     ap.add_argument("--aux-steps", type=int, default=-1,
                     help="steps of the stage-breakdown, profiled and end-to-end legs (default: --steps, at most 3 / "
                          "3 / 5 on grids above 100 M cells)")
-    ap.add_argument("--fp32-peak", action="store_true",
-                    help="measure the device's FP32 FMA rate (the ALU bound of the issue-bound kernels)")
+    ap.add_argument("--fma-peak", action="store_true",
+                    help="measure the device's FP32 and FP64 FMA rates (the ALU bounds)")
     # single Poisson solves (profiling a CG kernel)
     ap.add_argument("--poisson-only", action="store_true",
                     help="time single Poisson solves of a seeded right side instead of steps")
@@ -366,9 +366,10 @@ def reference_arm(args, rank, world):
     return 0
 
 
-def fp32_peak(args):
-    """The FP32 FMA rate of the device (les_measure_fp32_fma), three times,
-    with the issue rate it implies: one warp instruction retires 32 FMAs."""
+def fma_peak(args):
+    """The FP32 and FP64 FMA rates of the device (les_measure_fma), three
+    times each, with the FP32 issue rate they imply: one warp instruction
+    retires 32 FMAs."""
     import torch
 
     from paper_2301_04698_gb300 import build as B
@@ -381,12 +382,16 @@ def fp32_peak(args):
            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None) or 2070.0
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.mark(0)
-    runs = [les.measure_fp32_fma(10000) for _ in range(3)]
+    fp32 = [les.measure_fma(32, 10000) for _ in range(3)]
+    fp64 = [les.measure_fma(64, 200) for _ in range(3)]
     clocks.mark(1)
-    best = max(r["tflops"] for r in runs)
-    print(json.dumps({"fp32_fma_tflops": best, "runs": runs, "sms": nsm, "sm_max_mhz": clk,
-                      "fma_per_sm_per_clk_at_max": best * 1e12 / 2 / nsm / (clk * 1e6),
-                      "warp_instr_per_sm_per_clk_at_max": best * 1e12 / 2 / 32 / nsm / (clk * 1e6),
+    b32 = max(r["tflops"] for r in fp32)
+    b64 = max(r["tflops"] for r in fp64)
+    print(json.dumps({"fp32_fma_tflops": b32, "fp64_fma_tflops": b64, "fp32_runs": fp32, "fp64_runs": fp64,
+                      "sms": nsm, "sm_max_mhz": clk,
+                      "fp32_fma_per_sm_per_clk_at_max": b32 * 1e12 / 2 / nsm / (clk * 1e6),
+                      "fp32_warp_instr_per_sm_per_clk_at_max": b32 * 1e12 / 2 / 32 / nsm / (clk * 1e6),
+                      "fp64_fma_per_sm_per_clk_at_max": b64 * 1e12 / 2 / nsm / (clk * 1e6),
                       "clocks": clocks.stop()}), flush=True)
     return 0
 
@@ -605,8 +610,8 @@ def main():
     args = parse()
     if args.poisson_only:
         return poisson_only(args)
-    if args.fp32_peak:
-        return fp32_peak(args)
+    if args.fma_peak:
+        return fma_peak(args)
     if args.oracle_one_thread:
         case = workload(args.workload, 1)
         sample, desc = oracle_sample(case, args, side=args.oracle_one_thread)

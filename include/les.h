@@ -304,16 +304,18 @@ int les_poisson_solve_static(const les_config *cfg, const void *d_rho0, const vo
                              double *rel_res, char *err, size_t err_len);
 
 /* ---- device measurement ---------------------------------------------------------
- * The FP32 FMA rate of the current device: every thread of four waves of
- * resident 1024-thread blocks runs eight independent FMA chains for
- * trips x 16 steps (one warm-up launch, then one launch timed with CUDA
- * events on stream).  It is the ALU bound against which the kernels bound by
- * instruction issue (the predictors) are judged; the method does not use it.
+ * The FMA rate of the current device in precision 32 or 64: every thread of
+ * four waves of resident 1024-thread blocks runs eight independent FMA
+ * chains for trips x 16 steps (one warm-up launch, then one launch timed with
+ * CUDA events on stream).  The FP32 rate is the ALU bound against which the
+ * kernels bound by instruction issue (the predictors) are judged, the FP64
+ * rate the bound of the FP64 configurations; the method does not use them.
  * trips > 0; *tflops receives 2 x FMAs / time in TFLOP/s, *ms the timed
  * launch's duration.  Allocates and frees a few kilobytes on the stream
  * (cudaMallocAsync) and synchronises it.  Returns LES_OK, LES_ERR_INVALID_ARG
- * or LES_ERR_CUDA. */
-int les_measure_fp32_fma(void *stream, int32_t trips, double *tflops, double *ms);
+ * (trips <= 0, a precision other than 32 or 64, a null output) or
+ * LES_ERR_CUDA. */
+int les_measure_fma(void *stream, int32_t precision, int32_t trips, double *tflops, double *ms);
 
 /* ---- domain decomposition of the Poisson solve --------------------------------
  * The paper runs its LES on many TPU cores by cutting the domain into

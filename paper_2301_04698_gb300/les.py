@@ -46,7 +46,7 @@ EXPORTED = ("les_config_default", "les_workspace_bytes", "les_init", "les_destro
             "les_set_warm_model", "les_unet_set_output_scale", "les_unet_get_output_scale", "les_unet_set_loss",
             "les_ensemble_step", "les_set_states", "les_dd_workspace_bytes", "les_dd_create", "les_dd_destroy",
             "les_dd_local_shape", "les_dd_poisson_solve", "les_dd_last_error", "les_dd_step_config",
-            "les_dd_halo_exchange", "les_dd_stage_solve", "les_prefetch_states", "les_measure_fp32_fma")
+            "les_dd_halo_exchange", "les_dd_stage_solve", "les_prefetch_states", "les_measure_fma")
 
 
 class LesConfig(C.Structure):
@@ -214,20 +214,20 @@ def load_library(path: str = LIB_PATH):
     lib.les_poisson_solve_static.restype = C.c_int
     lib.les_poisson_solve_static.argtypes = [cfgp, vp, vp, vp, dbl, i32, vp, C.POINTER(i32), C.POINTER(dbl),
                                              C.c_char_p, sz]
-    lib.les_measure_fp32_fma.restype = C.c_int
-    lib.les_measure_fp32_fma.argtypes = [vp, i32, C.POINTER(dbl), C.POINTER(dbl)]
+    lib.les_measure_fma.restype = C.c_int
+    lib.les_measure_fma.argtypes = [vp, i32, i32, C.POINTER(dbl), C.POINTER(dbl)]
     _lib = lib
     return lib
 
 
-def measure_fp32_fma(trips: int = 10000, stream=None) -> dict:
-    """The device's FP32 FMA rate (les_measure_fp32_fma): {"tflops", "ms"}."""
+def measure_fma(precision: int = 32, trips: int = 10000, stream=None) -> dict:
+    """The device's FMA rate in FP32 or FP64 (les_measure_fma): {"tflops", "ms"}."""
     lib = load_library()
     tf, ms = C.c_double(0.0), C.c_double(0.0)
-    rc = lib.les_measure_fp32_fma(C.c_void_p(stream.cuda_stream if stream is not None else 0), int(trips),
-                                  C.byref(tf), C.byref(ms))
+    rc = lib.les_measure_fma(C.c_void_p(stream.cuda_stream if stream is not None else 0), int(precision), int(trips),
+                             C.byref(tf), C.byref(ms))
     if rc != LES_OK:
-        raise LesError(rc, f"les_measure_fp32_fma: status {rc}")
+        raise LesError(rc, f"les_measure_fma: status {rc}")
     return {"tflops": tf.value, "ms": ms.value}
 
 
